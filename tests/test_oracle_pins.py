@@ -1,0 +1,380 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, exact discrete invariants, brute force, or numbers the paper prints
+(tests/golden/paper_values.txt).
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def golden_rows(kind):
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, src, a, b, v = line.split()
+            if k == kind:
+                rows.append((src, float(a), float(b), float(v)))
+    assert rows, kind
+    return rows
+
+
+# ---------------------------------------------------------------------------
+# (a7) Poisson initialisation, Eq. 4
+# ---------------------------------------------------------------------------
+
+def test_poisson_matches_closed_form_second_order():
+    """Constant rho_GJ: phi(z) = -4 pi rho [1 - cosh(L - z)/cosh(L)] (R = 1)."""
+    L, rho = 8.0, -1.3
+    errs = []
+    for nz in (128, 256, 512):
+        dz = L / nz
+        z = np.arange(nz + 1) * dz
+        phi = orc.poisson_potential(np.full(nz + 1, rho), dz)
+        exact = -4.0 * math.pi * rho * (1.0 - np.cosh(L - z) / np.cosh(L))
+        errs.append(np.max(np.abs(phi - exact)) / np.max(np.abs(exact)))
+    assert errs[-1] < 2e-5
+    # second order: halving dz divides the error by ~4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_initial_fields_follow_the_potential():
+    """E_z = -phi' -> -4 pi rho sinh(L-z)/cosh(L); E_r = phi/R; B = 0."""
+    L, nz, rho = 8.0, 1024, -1.0
+    dz = L / nz
+    ez, er, b, phi = orc.initial_fields(np.full(nz + 1, rho), dz)
+    zc = (np.arange(nz) + 0.5) * dz
+    ez_exact = 4.0 * math.pi * rho * np.sinh(L - zc) / np.cosh(L)
+    assert np.max(np.abs(ez - ez_exact)) < 1e-4 * np.max(np.abs(ez_exact))
+    assert np.array_equal(er, phi) and er[0] == 0.0
+    assert np.all(b == 0.0)
+    # vacuum field at the base pulls electrons up: E_z < 0 for rho_GJ < 0
+    assert ez[0] < 0.0
+
+
+# ---------------------------------------------------------------------------
+# (a6) leap-frog of Eq. 3
+# ---------------------------------------------------------------------------
+
+def _leapfrog_closed_form(n, theta):
+    """x_n of x' = x + h y, y' = y - h x' with x_0 = 1, y_{1/2} = 0:
+    x_n = cos(n theta) + tan(theta/2) sin(n theta), cos theta = 1 - h^2/2."""
+    return np.cos(n * theta) + np.tan(theta / 2.0) * np.sin(n * theta)
+
+
+def test_uniform_transverse_mode_oscillates_at_c_over_R():
+    """A z-uniform E_z, B_phi perturbation obeys dE/dt = B, dB/dt = -E:
+    omega = c/R, discrete sin(omega dt / 2) = dt / 2."""
+    nz, L = 64, 8.0
+    dz = L / nz
+    dt = 0.4 * dz
+    ez = np.full(nz, 1e-3)
+    er = np.zeros(nz + 1)
+    b = np.zeros(nz)
+    j = np.zeros(nz)
+    theta = math.acos(1.0 - dt * dt / 2.0)
+    got = []
+    for n in range(4000):
+        got.append(ez[0])
+        ez, er, b = orc.field_update(ez, er, b, j, dt, dz)
+        assert np.ptp(ez) == 0.0            # stays uniform
+    want = 1e-3 * _leapfrog_closed_form(np.arange(4000), theta)
+    assert np.max(np.abs(np.array(got) - want)) < 1e-13
+    # the period approaches 2 pi R / c
+    assert abs(2 * math.pi / theta * dt - 2 * math.pi) < 1e-2
+
+
+@pytest.mark.parametrize("mode", [1, 3, 7])
+def test_standing_wave_obeys_waveguide_dispersion(mode):
+    """Eq. 3 without current has modes E_z ~ cos(kz), E_r ~ sin(kz), k = m pi/L
+    (they meet E_r(0) = 0 and phi'(L) = 0). With K = (2/dz) sin(k dz/2):
+    W = e + K r oscillates with Omega^2 = 1 + K^2 and V = K e - r is constant."""
+    nz, L = 128, 4.0
+    dz = L / nz
+    dt = 0.45 * dz
+    k = mode * math.pi / L
+    K = 2.0 / dz * math.sin(k * dz / 2.0)
+    zc = (np.arange(nz) + 0.5) * dz
+    zn = np.arange(nz + 1) * dz
+    e0, r0 = 0.7, -0.4
+    ez, er, b = e0 * np.cos(k * zc), r0 * np.sin(k * zn), np.zeros(nz)
+    j = np.zeros(nz)
+    omega = math.sqrt(1.0 + K * K)
+    theta = math.acos(1.0 - (omega * dt) ** 2 / 2.0)
+    w0, v0 = e0 + K * r0, K * e0 - r0
+    for n in range(1, 1501):
+        ez, er, b = orc.field_update(ez, er, b, j, dt, dz)
+        w = w0 * _leapfrog_closed_form(n, theta)
+        e = (w + K * v0) / (1.0 + K * K)
+        r = (K * w - v0) / (1.0 + K * K)
+        assert np.max(np.abs(ez - e * np.cos(k * zc))) < 1e-11
+        assert np.max(np.abs(er - r * np.sin(k * zn))) < 1e-11
+
+
+def test_empty_tube_is_stationary():
+    """Poisson state with no particles is a fixed point of Eq. 3 (P2).
+    rho_GJ > 0 so that the surface field pushes electrons back (no injection)."""
+    nz, L = 256, 8.0
+    dz = L / nz
+    rho = np.linspace(0.5, 1.5, nz + 1)
+    t = orc.Tube(nz, L, 0.4 * dz, rho, -1e-3)
+    ez0, er0 = t.ez.copy(), t.er.copy()
+    t.run(3000)
+    assert t.xi.size == 0 and t.total_injected == 0
+    assert np.max(np.abs(t.ez - ez0)) < 1e-12 * np.max(np.abs(ez0))
+    assert np.max(np.abs(t.er - er0)) < 1e-12 * np.max(np.abs(er0))
+    assert np.max(np.abs(t.b)) < 1e-12 * np.max(np.abs(ez0))
+
+
+# ---------------------------------------------------------------------------
+# (a2) + (a3) gather and push, Eq. 1
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rt", [np.float64, np.float32])
+def test_gather_is_exact_for_linear_fields_and_clamped_at_ends(rt):
+    nz, L = 32, 4.0
+    dz = L / nz
+    zc = (np.arange(nz) + 0.5) * dz
+    ez = 2.0 - 0.75 * zc
+    xi = np.linspace(0.5, nz - 0.5, 301).astype(rt)
+    ep = orc.gather(ez, xi, rt)
+    tol = 1e-13 if rt is np.float64 else 2e-6
+    assert np.max(np.abs(ep - (2.0 - 0.75 * xi.astype(np.float64) * dz))) < tol
+    lo = orc.gather(ez, np.array([0.0, 0.2, 0.49], rt), rt)
+    hi = orc.gather(ez, np.array([nz - 0.4, nz - 0.01], rt), rt)
+    assert np.all(lo == rt(ez[0])) and np.all(hi == rt(ez[-1]))
+
+
+def test_uniform_field_single_particle_matches_relativistic_solution():
+    """du/dt = q E / m (Eq. 1): u is linear in time, gamma = sqrt(1 + u^2), and
+    z(t) = (gamma(t) - gamma(0)) / |E| within O(dt^2) (P4)."""
+    nz, L, E0 = 64, 100.0, -0.8
+    dz = L / nz
+    for dt in (0.4 * dz, 0.2 * dz, 0.1 * dz):
+        xi = np.zeros(1)
+        u = np.zeros(1)
+        ez = np.full(nz, E0)
+        nsteps = int(round(20.0 / dt))
+        for n in range(nsteps):
+            ep = orc.gather(ez, xi, np.float64)
+            xi, u = orc.push(xi, u, ep, dt, dz, np.float64)
+        # u^{N-1/2} = -E0 * N * dt (q/m = -1) up to rounding of the sum
+        assert abs(u[0] - (-E0) * nsteps * dt) < nsteps * 1e-15 * abs(u[0])
+        # a leap-frog particle started at rest at t = 0 with u^{-1/2} = 0 has
+        # u(t) = |E0| (t + dt/2); integrate v = u / gamma exactly:
+        T = nsteps * dt
+        a = abs(E0)
+        z_exact = (math.sqrt(1 + (a * (T + dt / 2)) ** 2)
+                   - math.sqrt(1 + (a * dt / 2) ** 2)) / a
+        err = abs(xi[0] * dz - z_exact)
+        assert err < 0.05 * dt * dt * T + 1e-12, (dt, err)
+
+
+# ---------------------------------------------------------------------------
+# (a4) deposit: continuity, Gauss, brute force
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rt,tol", [(np.float64, 1e-12), (np.float32, 2e-5)])
+def test_deposit_satisfies_discrete_continuity(rt, tol):
+    """rho^{n+1}_j - rho^n_j + dt (J_{j+1/2} - J_{j-1/2}) / dz = 0 on interior
+    nodes, with cloud-in-cell rho computed independently of the deposit (P5)."""
+    rng = np.random.default_rng(5)
+    nz, L, s = 40, 5.0, -0.01
+    dz = L / nz
+    dt = 0.5 * dz
+    xi0 = rng.uniform(0.0, nz, 3000).astype(rt)
+    dxi = rng.uniform(-0.5, 0.5, xi0.size).astype(rt)
+    xi1 = (xi0 + dxi).astype(rt)
+    acc = orc.deposit_fractions(nz, xi0, xi1, rt, "sum")
+    j = orc.current_from(acc, s, dt, "sum")
+    keep = (xi1 >= 0) & (xi1 < nz)
+    r0 = orc.rho_nodes(xi0, s, dz, nz)
+    r1 = orc.rho_nodes(xi1[keep], s, dz, nz)
+    res = r1[1:-1] - r0[1:-1] + dt * (j[1:] - j[:-1]) / dz
+    assert np.max(np.abs(res)) < tol * np.max(np.abs(r0))
+
+
+@pytest.mark.parametrize("nz,npart", [(4, 6), (8, 20), (16, 13)])
+def test_brute_force_equals_fast_deposit_on_tiny_tubes(nz, npart):
+    """The whole step with the all-pairs deposit equals the two-cell deposit:
+    exactly in 'fixed' accumulation, to 1e-14 in 'sum' (P7)."""
+    rng = np.random.default_rng(nz)
+    L = 1.0
+    dz = L / nz
+    rho = -np.linspace(1.0, 2.0, nz + 1)
+    z = rng.uniform(0.0, L, npart)
+    u = rng.normal(0.0, 0.5, npart)
+    for prec in ("f64", "f32"):
+        for acc in ("fixed", "sum"):
+            ts = [orc.Tube(nz, L, 0.45 * dz, rho, -0.05, precision=prec,
+                           accumulate=acc, deposit=d) for d in ("fast", "brute")]
+            for t in ts:
+                t.add_particles(z, u)
+            for _ in range(200):
+                for t in ts:
+                    t.step()
+                a, b = ts
+                assert np.array_equal(a.ids, b.ids)
+                assert a.total_injected == b.total_injected
+                if acc == "fixed":
+                    assert np.array_equal(a.xi, b.xi) and np.array_equal(a.u, b.u)
+                    assert np.array_equal(a.ez, b.ez) and np.array_equal(a.b, b.b)
+                else:
+                    assert np.max(np.abs(a.ez - b.ez)) <= 1e-14 * np.max(np.abs(a.ez))
+            assert ts[0].total_injected > npart   # injection was exercised
+
+
+def test_gauss_law_is_conserved_by_the_full_step():
+    """G_j stays at its Poisson value (~0) on interior nodes while particles are
+    injected, pushed, deposited and removed (P6)."""
+    nz, L = 256, 4.0
+    dz = L / nz
+    rho = -np.ones(nz + 1)
+    t = orc.Tube(nz, L, 0.4 * dz, rho, orc.macro_charge_for(-1.0, L, 8000))
+    g0 = np.max(np.abs(t.gauss_residual()))
+    t.run(1500)
+    assert t.xi.size > 1000 and t.last_removed >= 0
+    assert g0 < 1e-9 and np.max(np.abs(t.gauss_residual())) < 1e-9
+
+
+def test_removal_at_both_ends_and_id_order():
+    nz, L = 16, 1.0
+    dz = L / nz
+    t = orc.Tube(nz, L, 0.5 * dz, np.full(nz + 1, 1.0), -0.01)  # no injection
+    t.add_particles([0.001, 0.5, 0.999], [-5.0, 0.0, 5.0])
+    t.step()
+    assert list(t.ids) == [1] and t.last_removed == 2
+
+
+# ---------------------------------------------------------------------------
+# (a1) injection and the whole loop against the paper's physics
+# ---------------------------------------------------------------------------
+
+def test_injection_zeroes_the_surface_field():
+    """Each new electron lifts E_s by 4 pi |s|; after injection |E_s| <= 2 pi |s|."""
+    nz, L = 128, 8.0
+    dz = L / nz
+    s = -1e-3
+    t = orc.Tube(nz, L, 0.4 * dz, -np.ones(nz + 1), s)
+    n = t.inject()
+    es_before = t.surface_field
+    assert n == round(-es_before / (4 * math.pi * abs(s)))
+    _, es_after = orc.injection_count(t.ez[0], t.w0, s, dz, t.rho_gj[0])
+    assert abs(es_after) <= 2 * math.pi * abs(s) + 1e-12
+
+
+def _cfg1_tube(prec="f64", acc="sum"):
+    nz, L = 1024, 8.0
+    dz = L / nz
+    return orc.Tube(nz, L, 0.4 * dz, -np.ones(nz + 1),
+                    orc.macro_charge_for(-1.0, L, 50000),
+                    precision=prec, accumulate=acc)
+
+
+def test_flat_sclf_reaches_sqrt2_lambda_and_screens_the_surface():
+    """Flat space, rho_GJ = -1 (Lambda = sqrt(4 pi)): behind the front the beam
+    reaches gamma_max ~ sqrt(2) omega_p R / c (Table 1, Table 2) and E_z at the
+    surface vanishes with a cloud of electrons at the base (Sec. 2, Fig. 4)."""
+    t = _cfg1_tube("f32", "fixed")
+    lam = math.sqrt(4 * math.pi)
+    ez_vac = abs(t.ez[0])
+    while t.z().max(initial=0.0) < 0.9 * t.L:
+        t.run(200)
+    g = t.gamma()
+    assert 0.7 * math.sqrt(2) * lam < g.max() < 1.3 * math.sqrt(2) * lam
+    assert abs(t.ez[0]) < 0.1 * ez_vac                    # SCLF condition
+    base = np.count_nonzero(t.z() < t.dz)
+    beam = np.count_nonzero((t.z() > 2.0) & (t.z() < 2.0 + t.dz))
+    assert base > 5 * beam                                 # the base cloud
+
+
+def _gr_tube(incl, lam=40.0, nz=4096, L=8.0):
+    dz = L / nz
+    z = np.arange(nz + 1) * dz
+    rho = orc.rho_gj_profile(orc.RHO_GR, z, lam, incl, 0.67 * 0.02, 0.125, 0.1654)
+    t = orc.Tube(nz, L, orc.default_dt(dz, lam), rho,
+                 orc.macro_charge_for(rho[0], L, 20000),
+                 precision="f32", accumulate="fixed")
+    phi = orc.poisson_potential(rho - rho[0], dz)
+    return t, z, phi
+
+
+def test_frame_dragging_acceleration_and_inclination_order():
+    """Behind the front gamma follows the analytic frame-dragging acceleration
+    (Eq. 8, gamma = 1 + e Phi / m c^2) with Phi from Eq. 4 driven by
+    rho_GJ(0) - rho_GJ(z) (Eq. 6-7) and the surface condition of Sec. 2; a
+    smaller inclination accelerates harder (Sec. 3, Fig. 6)."""
+    means = {}
+    for incl in (0.5, 0.1):
+        t, z, phi = _gr_tube(incl)
+        t.run(10500)
+        g, zz = t.gamma(), t.z()
+        for lo in (1.0, 2.0):
+            sel = (zz >= lo) & (zz < lo + 1.0)
+            ana = 1.0 + np.mean(phi[(z >= lo) & (z < lo + 1.0)])
+            sim = np.mean(g[sel])
+            assert abs(sim / ana - 1.0) < 0.15, (incl, lo, sim, ana)
+            means[(incl, lo)] = sim
+    assert means[(0.1, 1.0)] > means[(0.5, 1.0)]
+    assert means[(0.1, 2.0)] > means[(0.5, 2.0)]
+
+
+# ---------------------------------------------------------------------------
+# Units and calibration against the numbers the paper prints
+# ---------------------------------------------------------------------------
+
+def test_gamma_max_formula_matches_tables_1_and_2():
+    # The paper rounds both columns ("~15", "R ~ 5.0e6", "~7,000"): 12 %.
+    for src, R, wp, gmax in golden_rows("gmax"):
+        got = math.sqrt(2.0) * wp * R
+        assert abs(got / gmax - 1.0) < 0.12, (src, R, wp, got, gmax)
+    for src, R, wp, gmax in golden_rows("gmax_cgs"):
+        got = math.sqrt(2.0) * wp * R / orc.C_LIGHT
+        assert abs(got / gmax - 1.0) < 0.05
+
+
+def test_standard_pulsar_units_match_section_3():
+    cu = orc.code_units(1e12, 1.0, 1e6, 0.0, 1.4 * orc.M_SUN)
+    (_, P, Rs, th), = golden_rows("theta_p")
+    assert abs(cu["theta_p"] / th - 1.0) < 0.05
+    (_, P, B, n), = golden_rows("n_gj")
+    assert abs(cu["n0"] / n - 1.0) < 0.06
+    (_, P, B, wp), = golden_rows("omega_p")
+    assert abs(cu["omega_p0"] / wp - 1.0) < 0.03
+    assert abs(cu["rg_over_Rstar"] - 0.41) < 0.01        # "r_g / R_* ~ 0.4"
+
+
+def test_figure5_calibration_and_step_duration():
+    """Fig. 5: the program pairs (R, omega_p) carry the pulsar's
+    Lambda = omega_p R / c at i = 0.5 rad, and one step of dt = dz / 2 lasts
+    R_p / (R_program c) / 2 seconds with R_p = R_* theta_p."""
+    cu = orc.code_units(1e12, 1.0, 1e6, 0.5, 1.4 * orc.M_SUN)
+    lam_i = cu["Lambda0"] * math.sqrt(math.cos(0.5))
+    for src, R, wp, _ in golden_rows("lambda_gr"):
+        assert abs(R * wp / lam_i - 1.0) < 0.05
+    for src, R, _, secs in golden_rows("step_s"):
+        got = 0.5 * cu["R_cm"] / R / orc.C_LIGHT
+        assert abs(got / secs - 1.0) < 0.05, (R, got, secs)
+
+
+def test_gr_profile_reduces_to_flat_without_frame_dragging():
+    z = np.linspace(0.0, 50.0, 11)
+    a = orc.rho_gj_profile(orc.RHO_GR, z, 3.0, 0.4, 0.01, 0.02, 0.0)
+    b = orc.rho_gj_profile(orc.RHO_FLAT, z, 3.0, 0.4, 0.01, 0.02, 0.1654)
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+    g = orc.rho_gj_profile(orc.RHO_GR, z, 3.0, 0.0, 0.01, 0.02, 0.1654)
+    eta = 1.0 + z * 0.02
+    assert np.allclose(g, -(9.0 / (4 * math.pi)) * (1 - 0.1654 / eta ** 3), rtol=1e-15)
+    # |rho_GJ| grows with height under frame dragging (omega falls off as eta^-3)
+    assert np.all(np.diff(np.abs(g)) > 0)
