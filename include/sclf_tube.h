@@ -1,0 +1,253 @@
+/*
+ * sclf_tube.h -- C ABI of the GB300 (sm_103a) library for the 1D
+ * particle-in-cell tube of Barzilay, "Full simulation of the open field
+ * lines above pulsar's polar cap - Part I" (arXiv:1011.6330).
+ *
+ * One tube is a conducting cylinder of radius R above the polar cap (Sec. 2).
+ * Each step (Sec. 2, Figure A) injects electrons at the base while the
+ * Goldreich-Julian charge there is not compensated, weights E_z to every
+ * particle (cloud-in-cell), pushes it with Eq. 1, deposits a
+ * charge-conserving current and advances Eq. 3 (Maxwell with d/dr -> 1/R)
+ * by leap-frog, against the flat (Eq. 5) or frame-dragging (Eq. 6-7)
+ * rho_GJ(z). Fields start from Eq. 4 with an empty tube.
+ *
+ * Units (Sec. 3): c = 1, lengths in R, time in R/c, electron q/m = -1,
+ * density in units where omega_p^2 = 4 pi |rho|, i.e. |rho_GJ| =
+ * Lambda^2 / 4 pi with Lambda = omega_p R / c.
+ *
+ * Conventions for every call:
+ *   - Return 0 (SCLF_OK) on success or a negative SCLF_E* code; no C++
+ *     exception crosses the ABI. tube_strerror() names a code.
+ *   - Pointers documented "host" are caller-owned host memory (pageable or
+ *     pinned); the library never keeps them after the call returns.
+ *   - Device memory is owned by the tube: either a caller-provided device
+ *     workspace (tube_create with dev_workspace != NULL; the caller keeps it
+ *     alive until tube_destroy) or memory the library allocates itself.
+ *   - Work is queued on the CUDA stream given to tube_create and is
+ *     asynchronous unless the call says it synchronises. Calls on one tube
+ *     must not run concurrently from several host threads.
+ */
+#ifndef SCLF_TUBE_H
+#define SCLF_TUBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define SCLF_OK          0
+#define SCLF_EINVAL     -1   /* a parameter or argument is out of range      */
+#define SCLF_ENOMEM     -2   /* device or host allocation failed, or the
+                                caller's workspace is too small               */
+#define SCLF_ECUDA      -3   /* a CUDA runtime call failed                    */
+#define SCLF_ECAPACITY  -4   /* particle slots exhausted (injection clipped)  */
+#define SCLF_ENONFINITE -5   /* a particle produced NaN/Inf and was dropped   */
+#define SCLF_ETIMEOUT   -6   /* a bounded device-side wait gave up            */
+#define SCLF_ESTATE     -7   /* call not valid in the tube's current state    */
+
+/* ---- sticky device status flags (tube_stats.flags) ---------------------- */
+#define SCLF_FLAG_CAPACITY  0x1u
+#define SCLF_FLAG_NONFINITE 0x2u
+#define SCLF_FLAG_TIMEOUT   0x4u
+
+/* ---- enumerations -------------------------------------------------------- */
+#define SCLF_RHO_FLAT 0      /* Eq. 5 with the (R_* / r)^3 factor dropped       */
+#define SCLF_RHO_GR   1      /* Eq. 6 with omega from Eq. 7, f = H = alpha = 1 */
+#define SCLF_RHO_USER 2      /* caller-supplied rho_GJ at the Nz+1 nodes      */
+
+#define SCLF_FP32 0          /* particle arithmetic in IEEE float32           */
+#define SCLF_FP64 1          /* particle arithmetic in IEEE float64           */
+
+#define SCLF_ACC_FIXED64 0   /* current fractions summed exactly in int64
+                                multiples of 2^-32 (order independent)        */
+#define SCLF_ACC_FP64    1   /* current fractions summed with FP64 atomics    */
+
+typedef struct sclf_tube* tube_t;   /* opaque, library-owned */
+
+/*
+ * Parameters of one tube, as the paper states them (Sec. 3: B, P, R_*, i,
+ * M; Sec. 2: R, the rho_GJ profile; plus the grid Nz and the step dt).
+ * tube_params_default() fills the "standard pulsar" of Sec. 3.
+ */
+typedef struct tube_params {
+    double B_G;            /* surface magnetic field B_* [G]                  */
+    double P_s;            /* rotation period P [s]                           */
+    double Rstar_cm;       /* stellar radius R_* [cm]                         */
+    double incl_rad;       /* inclination i [rad]                             */
+    double mass_g;         /* stellar mass M_* [g]                            */
+    double R_cm;           /* tube radius R [cm]; <= 0 -> R_* theta_p,
+                              theta_p = sqrt(Omega R_* / c) (Sec. 3)          */
+    double L_over_R;       /* tube length in units of R                       */
+    int64_t Nz;            /* grid cells, 2 <= Nz <= 2^24                     */
+    double dt;             /* time step in R/c; <= 0 -> min(0.4 dz, 0.2/Lambda0);
+                              must satisfy 0 < dt < dz                        */
+    int32_t rho_gj_mode;   /* SCLF_RHO_*                                      */
+    int32_t precision;     /* SCLF_FP32 or SCLF_FP64 (grids are always FP64)  */
+    const double* rho_gj_user; /* host, Nz+1 node values in code units, read
+                                  by tube_create when mode is SCLF_RHO_USER   */
+    double lambda_override;/* > 0: use this Lambda0 = omega_p0 R / c instead of
+                              deriving it from B, P, R (the calibration of
+                              Sec. 3 picks (R, omega_p) with the pulsar's
+                              omega_p R / c)                                  */
+    double macro_charge;   /* macro-particle charge s < 0 in code units;
+                              0 -> -|rho_GJ(0)| L / target_particles          */
+    int64_t target_particles; /* used only to derive macro_charge            */
+    int64_t capacity;      /* particle slots (live particles plus holes left
+                              by removals until the next compaction)          */
+    int32_t accumulate;    /* SCLF_ACC_FIXED64 or SCLF_ACC_FP64               */
+    int32_t track_ids;     /* 1: keep an int64 ID per particle                */
+    int32_t compact_interval; /* steps between compactions; 0 -> 64          */
+    int32_t use_graphs;    /* 1: tube_run replays captured CUDA graphs        */
+} tube_params;
+
+/* Code-unit quantities derived from tube_params (all FP64). */
+typedef struct tube_derived {
+    double Omega;          /* 2 pi / P [1/s]                                  */
+    double theta_p;        /* sqrt(Omega R_* / c)                             */
+    double R_cm;           /* tube radius actually used [cm]                  */
+    double n0;             /* Omega B / (2 pi c e) [cm^-3] (n_GJ / cos i)     */
+    double omega_p0;       /* sqrt(4 pi n0 e^2 / m) [1/s]                     */
+    double Lambda0;        /* omega_p0 R / c (or lambda_override)             */
+    double kappa;          /* (2/5) r_g / R_*  (Eq. 7)                        */
+    double theta_star;     /* 0.67 theta_p (Eq. 5 text)                       */
+    double R_over_Rstar;   /* R / R_*                                         */
+    double L;              /* tube length in R                                */
+    double dz;             /* L / Nz                                          */
+    double dt;             /* time step in R/c                                */
+    double s;              /* macro-particle charge (< 0)                     */
+    double rho0;           /* rho_GJ at node 0, code units                    */
+} tube_derived;
+
+/* Per-tube counters, read back by tube_status (synchronises the stream). */
+typedef struct tube_stats {
+    int64_t step;              /* completed steps                            */
+    int64_t n_particles;       /* live particles                             */
+    int64_t n_slots;           /* occupied slots (live + holes)              */
+    int64_t total_injected;    /* IDs handed out so far                      */
+    int64_t last_injected;     /* injected in the last step                  */
+    int64_t last_removed;      /* removed in the last step                   */
+    int64_t pending_injection; /* electrons the next step will inject        */
+    double surface_field;      /* E_s at the base before that injection      */
+    uint32_t flags;            /* SCLF_FLAG_* (sticky)                       */
+    uint32_t reserved;
+} tube_stats;
+
+/* Kernel timings accumulated while timing is enabled. */
+typedef struct tube_timing {
+    double push_ms;            /* summed device time of the particle kernel  */
+    double field_ms;           /* summed device time of the field kernel     */
+    double compact_ms;         /* summed device time of compactions          */
+    int64_t n_steps;           /* steps timed                                */
+    int64_t n_compactions;     /* compactions timed                          */
+    int64_t particle_slots;    /* sum over timed steps of slots processed    */
+} tube_timing;
+
+/* Fill p with the standard pulsar of Sec. 3 (P = 1 s, B = 1e12 G,
+ * R_* = 1e6 cm, M = 1.4 M_sun, i = 0, flat rho_GJ), L = 8 R, Nz = 1024,
+ * FP32 particles, fixed-point current, capacity 2^20. */
+int tube_params_default(tube_params* p);
+
+/* Validate p and compute the derived code-unit quantities (host only, no
+ * CUDA). Units: Sec. 3 normalisation; rho_GJ(0) from Eq. 5 or Eq. 6. */
+int tube_derive(const tube_params* p, tube_derived* d);
+
+/* Bytes of device memory a tube with these parameters needs. */
+int tube_workspace_bytes(const tube_params* p, int64_t* bytes);
+
+/* Create a tube: validate p, build rho_GJ (Eq. 5/6 or user), solve Eq. 4
+ * for the empty tube (phi = 0 at the base, phi' = 0 at the top), set
+ * E_z = -phi', E_r = phi / R, B_phi = 0 (Sec. 2), and upload to the device.
+ * dev_workspace: device memory of at least tube_workspace_bytes() bytes,
+ *   aligned to 256 bytes, or NULL to let the library allocate.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Synchronises the stream before returning. */
+int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes,
+                void* stream, tube_t* out);
+
+/* Release the tube (and its own device memory if it allocated any). */
+int tube_destroy(tube_t t);
+
+/* Copy the derived quantities of a live tube. */
+int tube_get_derived(tube_t t, tube_derived* d);
+
+/* One base injection (step (a1) alone, Sec. 2): append the pending number
+ * of electrons at z = 0 with u = 0. *n_injected (host, may be NULL)
+ * receives the count. Synchronises. */
+int tube_inject(tube_t t, int64_t* n_injected);
+
+/* Append n particles at heights z[i] (host, in R, 0 <= z < L) with
+ * u[i] = gamma beta (host); IDs continue the tube's count. Used for
+ * synthetic prefilled states and tests. Synchronises. */
+int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u);
+
+/* One time step (a1..a6 of Sec. 2, Figure A). Asynchronous. */
+int tube_step(tube_t t);
+
+/* nsteps time steps; replays captured CUDA graphs when use_graphs is set
+ * and timing is off. Asynchronous. */
+int tube_run(tube_t t, int64_t nsteps);
+
+/* Copy fields to host arrays (any may be NULL): Ez, Bphi, J at the Nz cell
+ * centres (Ez at step n, Bphi at n+1/2, J of the last step, code units);
+ * Er and rho (cloud-in-cell charge density) at the Nz+1 nodes.
+ * Synchronises. */
+int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi,
+                     double* J, double* rho);
+
+/* Copy live particles in ID order to host arrays of capacity cap: z in R,
+ * u = gamma beta, id (any of z, u, id may be NULL). *n receives the number
+ * of live particles; min(cap, *n) are written. Synchronises. */
+int tube_read_particles(tube_t t, int64_t cap, int64_t* n, double* z,
+                        double* u, int64_t* id);
+
+/* Raw particle state in the tube's precision: xi = z / dz (cell units) and
+ * u as float (SCLF_FP32) or double (SCLF_FP64), live particles only, ID
+ * order. Host buffers of capacity cap; *n receives the live count.
+ * Synchronises. (Checkpointing.) */
+int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u,
+                        int64_t* id);
+
+/* Replace all particles by n raw particles (host, layout as
+ * tube_save_particles; id may be NULL to number them 0..n-1). Holes are
+ * not allowed (every xi in [0, Nz)). Synchronises. */
+int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u,
+                        const int64_t* id);
+
+/* Re-solve Eq. 4 with the tube's current charge: phi'' - phi / R^2 =
+ * -4 pi (rho - rho_GJ) with rho the cloud-in-cell density of the live
+ * particles at the nodes, phi = 0 at the base and phi' = 0 at the top;
+ * then E_z = -phi', E_r = phi / R and B_phi = 0 (Sec. 2 initialisation,
+ * generalised from the empty tube to a prefilled one). The next injection
+ * count is recomputed. Synchronises. */
+int tube_solve_fields(tube_t t);
+
+/* Counters and sticky flags. Synchronises. Returns SCLF_OK even when flags
+ * are set; tube_check() turns flags into an error code. */
+int tube_status(tube_t t, tube_stats* out);
+
+/* SCLF_OK, or the error code of the most severe sticky flag. Synchronises. */
+int tube_check(tube_t t);
+
+/* Compact the particle slots now (removes holes, keeps ID order). Async. */
+int tube_compact(tube_t t);
+
+/* Enable (1) or disable (0) per-kernel CUDA-event timing of steps; enabling
+ * clears the accumulated numbers. While enabled, tube_run launches kernels
+ * directly (no graph replay). */
+int tube_set_timing(tube_t t, int enable);
+
+/* Accumulated timings since timing was enabled. Synchronises. */
+int tube_get_timing(tube_t t, tube_timing* out);
+
+/* Human-readable name of a return code (static storage). */
+const char* tube_strerror(int code);
+
+/* Library version string, e.g. "sclf_tube 0.1.0 sm_103a". */
+const char* tube_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCLF_TUBE_H */

@@ -401,6 +401,17 @@ class Tube:
         self.total_injected += n
         self.w0 = base_weight_fixed(self.xi, self.rt)
 
+    def solve_fields(self):
+        """Eq. 4 with the tube's current charge: phi'' - phi = -4 pi (rho - rho_GJ)
+        with rho the cloud-in-cell density of the particles at the nodes,
+        phi(0) = 0, phi'(L) = 0; E_z = -phi', E_r = phi, B_phi = 0 (the
+        Sec. 2 initialisation applied to a prefilled tube)."""
+        rho = self.rho_nodes()
+        phi = poisson_potential(self.rho_gj - rho, self.dz)
+        self.ez = -(phi[1:] - phi[:-1]) / self.dz
+        self.er = phi.copy()
+        self.b = np.zeros(self.nz)
+
     def injection_count(self):
         """N_inj for the current state (see :func:`injection_count`)."""
         n, es = injection_count(self.ez[0], self.w0, self.s, self.dz,

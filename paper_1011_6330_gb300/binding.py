@@ -1,0 +1,296 @@
+"""Thin Python binding of the sclf_tube C ABI (include/sclf_tube.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library. PyTorch provides the device workspace (its caching allocator) and
+the stream (``torch.cuda.current_stream()``). Loading fails loudly when the
+in-tree library has not been built; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "libsclf_tube.so")
+HEADER = os.path.join(ROOT, "include", "sclf_tube.h")
+
+SCLF_RHO_FLAT, SCLF_RHO_GR, SCLF_RHO_USER = 0, 1, 2
+SCLF_FP32, SCLF_FP64 = 0, 1
+SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
+FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
+
+
+class TubeParams(C.Structure):
+    _fields_ = [
+        ("B_G", C.c_double), ("P_s", C.c_double), ("Rstar_cm", C.c_double),
+        ("incl_rad", C.c_double), ("mass_g", C.c_double), ("R_cm", C.c_double),
+        ("L_over_R", C.c_double), ("Nz", C.c_int64), ("dt", C.c_double),
+        ("rho_gj_mode", C.c_int32), ("precision", C.c_int32),
+        ("rho_gj_user", C.POINTER(C.c_double)),
+        ("lambda_override", C.c_double), ("macro_charge", C.c_double),
+        ("target_particles", C.c_int64), ("capacity", C.c_int64),
+        ("accumulate", C.c_int32), ("track_ids", C.c_int32),
+        ("compact_interval", C.c_int32), ("use_graphs", C.c_int32),
+    ]
+
+
+class TubeDerived(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "Omega", "theta_p", "R_cm", "n0", "omega_p0", "Lambda0", "kappa",
+        "theta_star", "R_over_Rstar", "L", "dz", "dt", "s", "rho0")]
+
+
+class TubeStats(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("n_particles", C.c_int64), ("n_slots", C.c_int64),
+        ("total_injected", C.c_int64), ("last_injected", C.c_int64),
+        ("last_removed", C.c_int64), ("pending_injection", C.c_int64),
+        ("surface_field", C.c_double), ("flags", C.c_uint32), ("reserved", C.c_uint32),
+    ]
+
+
+class TubeTiming(C.Structure):
+    _fields_ = [
+        ("push_ms", C.c_double), ("field_ms", C.c_double), ("compact_ms", C.c_double),
+        ("n_steps", C.c_int64), ("n_compactions", C.c_int64),
+        ("particle_slots", C.c_int64),
+    ]
+
+
+_vp, _i64, _i32 = C.c_void_p, C.c_int64, C.c_int
+_pd = C.POINTER(C.c_double)
+_pi64 = C.POINTER(C.c_int64)
+
+SIGNATURES = {
+    "tube_params_default": (_i32, [C.POINTER(TubeParams)]),
+    "tube_derive": (_i32, [C.POINTER(TubeParams), C.POINTER(TubeDerived)]),
+    "tube_workspace_bytes": (_i32, [C.POINTER(TubeParams), _pi64]),
+    "tube_create": (_i32, [C.POINTER(TubeParams), _vp, _i64, _vp, C.POINTER(_vp)]),
+    "tube_destroy": (_i32, [_vp]),
+    "tube_get_derived": (_i32, [_vp, C.POINTER(TubeDerived)]),
+    "tube_inject": (_i32, [_vp, _pi64]),
+    "tube_add_particles": (_i32, [_vp, _i64, _pd, _pd]),
+    "tube_step": (_i32, [_vp]),
+    "tube_run": (_i32, [_vp, _i64]),
+    "tube_read_fields": (_i32, [_vp, _pd, _pd, _pd, _pd, _pd]),
+    "tube_read_particles": (_i32, [_vp, _i64, _pi64, _pd, _pd, _pi64]),
+    "tube_save_particles": (_i32, [_vp, _i64, _pi64, _vp, _vp, _pi64]),
+    "tube_load_particles": (_i32, [_vp, _i64, _vp, _vp, _pi64]),
+    "tube_solve_fields": (_i32, [_vp]),
+    "tube_status": (_i32, [_vp, C.POINTER(TubeStats)]),
+    "tube_check": (_i32, [_vp]),
+    "tube_compact": (_i32, [_vp]),
+    "tube_set_timing": (_i32, [_vp, _i32]),
+    "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "tube_strerror": (C.c_char_p, [_i32]),
+    "tube_version": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+class SclfError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = _LIB.tube_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__("%s failed: %s (%d)" % (what, msg, code))
+
+
+def load(path=LIB_PATH):
+    """Load the in-tree library (built by ``paper_1011_6330_gb300.build``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "sclf_tube library not built (%s missing); run "
+            "`python -m paper_1011_6330_gb300.build` or __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise SclfError(rc, what)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_pd) if a is not None else None
+
+
+def default_params(**kw):
+    """tube_params_default() with keyword overrides (rho_gj_user: array)."""
+    lib = load()
+    p = TubeParams()
+    _check(lib.tube_params_default(C.byref(p)), "tube_params_default")
+    keep = None
+    for k, v in kw.items():
+        if k == "rho_gj_user":
+            keep = np.ascontiguousarray(v, dtype=np.float64)
+            p.rho_gj_user = keep.ctypes.data_as(_pd)
+        else:
+            setattr(p, k, v)
+    p._keep = keep      # keep the user profile alive with the struct
+    return p
+
+
+def derive(params):
+    lib = load()
+    d = TubeDerived()
+    _check(lib.tube_derive(C.byref(params), C.byref(d)), "tube_derive")
+    return {n: getattr(d, n) for n, _ in TubeDerived._fields_}
+
+
+def workspace_bytes(params):
+    lib = load()
+    b = C.c_int64()
+    _check(lib.tube_workspace_bytes(C.byref(params), C.byref(b)), "tube_workspace_bytes")
+    return b.value
+
+
+class Tube:
+    """One tube on the current CUDA device and stream."""
+
+    def __init__(self, params, stream=None, torch_workspace=True):
+        import torch
+        self.lib = load()
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        nbytes = workspace_bytes(params)
+        self._ws = None
+        ws_ptr = None
+        if torch_workspace:
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            ws_ptr = (base + 255) // 256 * 256
+        h = C.c_void_p()
+        _check(self.lib.tube_create(C.byref(params), ws_ptr, nbytes,
+                                    C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "tube_create")
+        self.h = h
+        d = TubeDerived()
+        _check(self.lib.tube_get_derived(self.h, C.byref(d)), "tube_get_derived")
+        self.derived = {n: getattr(d, n) for n, _ in TubeDerived._fields_}
+        self.nz = int(params.Nz)
+        self.fp64 = params.precision == SCLF_FP64
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tube_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- steps -----------------------------------------------------------
+    def step(self):
+        _check(self.lib.tube_step(self.h), "tube_step")
+
+    def run(self, n):
+        _check(self.lib.tube_run(self.h, int(n)), "tube_run")
+
+    def inject(self):
+        n = C.c_int64()
+        _check(self.lib.tube_inject(self.h, C.byref(n)), "tube_inject")
+        return n.value
+
+    def compact(self):
+        _check(self.lib.tube_compact(self.h), "tube_compact")
+
+    # -- particles -------------------------------------------------------
+    def add_particles(self, z, u):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert z.shape == u.shape
+        _check(self.lib.tube_add_particles(self.h, z.size, _dptr(z), _dptr(u)),
+               "tube_add_particles")
+
+    def read_particles(self):
+        n = C.c_int64()
+        _check(self.lib.tube_read_particles(self.h, 0, C.byref(n), None, None, None),
+               "tube_read_particles")
+        cap = n.value
+        z = np.empty(cap)
+        u = np.empty(cap)
+        ids = np.empty(cap, np.int64)
+        _check(self.lib.tube_read_particles(self.h, cap, C.byref(n), _dptr(z), _dptr(u),
+                                            ids.ctypes.data_as(_pi64)), "tube_read_particles")
+        return z[:n.value], u[:n.value], ids[:n.value]
+
+    def save_particles(self):
+        n = C.c_int64()
+        _check(self.lib.tube_save_particles(self.h, 0, C.byref(n), None, None, None),
+               "tube_save_particles")
+        dt = np.float64 if self.fp64 else np.float32
+        xi = np.empty(n.value, dt)
+        u = np.empty(n.value, dt)
+        ids = np.empty(n.value, np.int64)
+        _check(self.lib.tube_save_particles(self.h, n.value, C.byref(n), xi.ctypes.data,
+                                            u.ctypes.data, ids.ctypes.data_as(_pi64)),
+               "tube_save_particles")
+        return xi, u, ids
+
+    def load_particles(self, xi, u, ids=None):
+        dt = np.float64 if self.fp64 else np.float32
+        xi = np.ascontiguousarray(xi, dtype=dt)
+        u = np.ascontiguousarray(u, dtype=dt)
+        idp = None
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, dtype=np.int64)
+            idp = ids.ctypes.data_as(_pi64)
+        _check(self.lib.tube_load_particles(self.h, xi.size, xi.ctypes.data, u.ctypes.data, idp),
+               "tube_load_particles")
+
+    # -- fields and counters ---------------------------------------------
+    def read_fields(self, rho=True):
+        nz = self.nz
+        ez, er, b, j = np.empty(nz), np.empty(nz + 1), np.empty(nz), np.empty(nz)
+        r = np.empty(nz + 1) if rho else None
+        _check(self.lib.tube_read_fields(self.h, _dptr(ez), _dptr(er), _dptr(b), _dptr(j),
+                                         _dptr(r)), "tube_read_fields")
+        out = {"ez": ez, "er": er, "b": b, "j": j}
+        if rho:
+            out["rho"] = r
+        return out
+
+    def solve_fields(self):
+        _check(self.lib.tube_solve_fields(self.h), "tube_solve_fields")
+
+    def status(self):
+        s = TubeStats()
+        _check(self.lib.tube_status(self.h, C.byref(s)), "tube_status")
+        return {n: getattr(s, n) for n, _ in TubeStats._fields_}
+
+    def check(self):
+        return self.lib.tube_check(self.h)
+
+    def set_timing(self, enable):
+        _check(self.lib.tube_set_timing(self.h, 1 if enable else 0), "tube_set_timing")
+
+    def timing(self):
+        t = TubeTiming()
+        _check(self.lib.tube_get_timing(self.h, C.byref(t)), "tube_get_timing")
+        return {n: getattr(t, n) for n, _ in TubeTiming._fields_}
+
+
+def header_functions(path=HEADER):
+    """Names of the functions include/sclf_tube.h declares."""
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tube_[a-z_]+)\s*\(", text)))

@@ -1,0 +1,140 @@
+// Internal declarations shared by the host side and the kernels of the
+// sclf_tube library. Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sclf_tube.h"
+
+namespace sclf {
+
+// Particle tiles: a CTA of kThreads threads handles kThreads * PPT
+// consecutive slots, each thread PPT consecutive ones.
+constexpr int kThreads = 256;
+template <class Real> struct Layout;
+template <> struct Layout<float> {
+    static constexpr int kVec = 4;          // float4 loads
+    static constexpr int kPPT = 16;         // particles per thread
+    static constexpr int kTile = kThreads * kPPT;
+};
+template <> struct Layout<double> {
+    static constexpr int kVec = 2;          // double2 loads
+    static constexpr int kPPT = 8;
+    static constexpr int kTile = kThreads * kPPT;
+};
+constexpr int kMaxTile = kThreads * 16;
+
+// 2^32: quantum of the fixed-point accumulators (current fractions and the
+// base-cell weight W_0).
+constexpr double kFixedScale = 4294967296.0;
+constexpr double kFixedInv = 1.0 / 4294967296.0;
+
+// Device-resident counters of one tube. The particle kernel reads only the
+// "committed" block and writes only the "accumulated" block; the field
+// kernel's first thread folds the latter into the former once per step.
+struct DevState {
+    // committed (valid between steps)
+    long long n_slots;          // slots in use: live particles + holes
+    long long n_live;           // live particles
+    long long n_inj;            // electrons the next step injects
+    long long total_injected;   // IDs handed out
+    long long step;             // completed steps
+    long long w0;               // base-cell weight W_0 (2^-32 units)
+    long long last_injected;
+    long long last_removed;
+    double surface_field;       // E_s that produced n_inj
+    unsigned int flags;         // SCLF_FLAG_* (sticky)
+    unsigned int pad0;
+    // accumulated by the particle kernel during a step
+    unsigned long long acc_w0;
+    unsigned long long acc_removed;
+    long long inj_done;         // injections actually performed this step
+    // compaction bookkeeping
+    unsigned int ticket;        // tile ticket of the compaction kernel
+    unsigned int compact_epoch; // tags tile states of one compaction
+    unsigned long long slots_processed;  // running sum of slots pushed
+    long long pad1[3];
+};
+
+// Constants of one tube in the precision the kernels use.
+struct FieldConsts {
+    int nz;
+    double dt, cdt, fourpi_dt, s_over_dt;
+    double four_pi_s, two_pi_dz_rho0, sheet;
+};
+
+template <class Real>
+struct PushArgs {
+    DevState* st;
+    Real* xi;                  // slot positions in cell units (hole: < 0)
+    Real* u;                   // gamma beta
+    long long* ids;            // may be null
+    const Real* ez2;           // gather table, 2*(nz+1): (E_{m-1/2}, E_{m+1/2})
+    void* jacc;                // nz accumulators (long long or double)
+    long long capacity;        // slots
+    int nz;
+    Real nzf;                  // (Real)nz
+    Real dt;                   // (Real)dt
+    Real cfl;                  // (Real)(dt/dz)
+};
+
+template <class Real>
+struct FieldArgs {
+    DevState* st;
+    double* ez;                // nz cells, E_z^n -> E_z^{n+1}
+    const double* er_in;       // nz+1 nodes, E_r^n
+    double* er_out;            // nz+1 nodes, E_r^{n+1}
+    const double* b_in;        // nz cells, B^{n+1/2}
+    double* b_out;             // nz cells, B^{n+3/2}
+    void* jacc;                // nz accumulators, zeroed after use
+    double* jlast;             // nz cells, J^{n+1/2} (diagnostic copy)
+    Real* ez2;                 // gather table for the next step
+    FieldConsts c;
+};
+
+template <class Real>
+struct CompactArgs {
+    DevState* st;
+    Real* xi;
+    Real* u;
+    long long* ids;
+    unsigned long long* tile_state;  // one word per tile
+    long long capacity;
+};
+
+// Launchers (kernels.cu). All return cudaGetLastError() after the launch.
+template <class Real>
+cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid,
+                        cudaStream_t s);
+template <class Real>
+int push_grid_size(int accumulate, int device_sms);
+template <class Real>
+cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
+                         cudaStream_t s);
+template <class Real>
+cudaError_t launch_compact(const CompactArgs<Real>& a, int grid, cudaStream_t s);
+template <class Real>
+int compact_grid_size(int device_sms);
+template <class Real>
+cudaError_t launch_append(DevState* st, Real* xi, Real* u, long long* ids,
+                          long long first, long long n, bool zero_particles,
+                          cudaStream_t s);
+template <class Real>
+cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots,
+                               cudaStream_t s);
+cudaError_t launch_finish_append(DevState* st, const double* ez,
+                                 long long n_added, FieldConsts c,
+                                 cudaStream_t s);
+template <class Real>
+cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s);
+template <class Real>
+cudaError_t launch_rho(const Real* xi, long long n_slots, double* rho_acc,
+                       int nz, cudaStream_t s);
+
+// Host set-up (setup.cpp).
+int derive(const tube_params* p, tube_derived* d);
+int build_rho_gj(const tube_params* p, const tube_derived* d, double* rho);
+void solve_poisson(const double* rho, int64_t nz, double dz, double* phi);
+
+}  // namespace sclf

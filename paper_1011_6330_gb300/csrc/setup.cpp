@@ -1,0 +1,131 @@
+// Host-side set-up of a tube: unit conversion (Sec. 3), the rho_GJ profile
+// (Eq. 5, Eq. 6-7) and the empty-tube Poisson problem (Eq. 4).
+#include <cmath>
+#include <cstring>
+
+#include "sclf_internal.h"
+
+namespace sclf {
+
+namespace {
+// cgs constants (CODATA 2018).
+constexpr double kC = 2.99792458e10;          // speed of light [cm/s]
+constexpr double kE = 4.80320471e-10;         // elementary charge [esu]
+constexpr double kMe = 9.1093837015e-28;      // electron mass [g]
+constexpr double kG = 6.67430e-8;             // gravitational constant
+constexpr double kPi = 3.14159265358979323846;
+
+// rho_GJ / (Lambda0^2 / 4 pi) at dimensionless radius eta = r / R_*.
+// Flat (Eq. 5): cos i + 3/2 sqrt(eta) theta_* sin i   (cos(phi) = 1, the
+// (R_* / r)^3 factor dropped for the constant-radius tube).
+// Frame dragging (Eq. 6 with Omega -> Omega - omega on the cos i term,
+// omega / Omega = kappa / eta^3 from Eq. 7, f = H = alpha = 1).
+double bracket(int mode, double eta, const tube_params* p, const tube_derived* d) {
+    const double sin_term = 1.5 * std::sqrt(eta) * d->theta_star * std::sin(p->incl_rad);
+    if (mode == SCLF_RHO_GR)
+        return (1.0 - d->kappa / (eta * eta * eta)) * std::cos(p->incl_rad) + sin_term;
+    return std::cos(p->incl_rad) + sin_term;
+}
+}  // namespace
+
+int derive(const tube_params* p, tube_derived* d) {
+    if (!p || !d) return SCLF_EINVAL;
+    std::memset(d, 0, sizeof(*d));
+    if (!(p->Nz >= 2 && p->Nz <= (int64_t(1) << 24))) return SCLF_EINVAL;
+    if (!(p->L_over_R > 0.0) || !std::isfinite(p->L_over_R)) return SCLF_EINVAL;
+    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64) return SCLF_EINVAL;
+    if (p->accumulate != SCLF_ACC_FIXED64 && p->accumulate != SCLF_ACC_FP64) return SCLF_EINVAL;
+    if (p->rho_gj_mode < SCLF_RHO_FLAT || p->rho_gj_mode > SCLF_RHO_USER) return SCLF_EINVAL;
+    if (p->rho_gj_mode == SCLF_RHO_USER && !p->rho_gj_user) return SCLF_EINVAL;
+    if (!(p->capacity >= 0 && p->capacity <= (int64_t(1) << 31) - kMaxTile)) return SCLF_EINVAL;
+    if (p->compact_interval < 0) return SCLF_EINVAL;
+
+    if (p->rho_gj_mode == SCLF_RHO_GR && !(p->P_s > 0.0 && p->Rstar_cm > 0.0 && p->mass_g >= 0.0))
+        return SCLF_EINVAL;
+    // Sec. 3: Omega, theta_p = sqrt(Omega R_* / c), R_p = R_* theta_p,
+    // n_GJ = Omega B cos i / (2 pi c e), omega_p = sqrt(4 pi n e^2 / m).
+    if (p->P_s > 0.0 && p->Rstar_cm > 0.0) {
+        d->Omega = 2.0 * kPi / p->P_s;
+        d->theta_p = std::sqrt(d->Omega * p->Rstar_cm / kC);
+        d->R_cm = p->R_cm > 0.0 ? p->R_cm : p->Rstar_cm * d->theta_p;
+        d->n0 = d->Omega * p->B_G / (2.0 * kPi * kC * kE);
+        d->omega_p0 = std::sqrt(4.0 * kPi * d->n0 * kE * kE / kMe);
+        d->Lambda0 = d->omega_p0 * d->R_cm / kC;
+        const double rg = 2.0 * kG * p->mass_g / (kC * kC);
+        d->kappa = 0.4 * rg / p->Rstar_cm;                  // Eq. 7
+        d->theta_star = 0.67 * d->theta_p;                  // Eq. 5 text
+        d->R_over_Rstar = d->R_cm / p->Rstar_cm;
+    }
+    if (p->lambda_override > 0.0) d->Lambda0 = p->lambda_override;
+    if (p->rho_gj_mode != SCLF_RHO_USER && !(d->Lambda0 > 0.0)) return SCLF_EINVAL;
+
+    d->L = p->L_over_R;
+    d->dz = d->L / double(p->Nz);
+    if (p->dt > 0.0) {
+        d->dt = p->dt;
+    } else {
+        if (!(d->Lambda0 > 0.0)) return SCLF_EINVAL;
+        d->dt = std::fmin(0.4 * d->dz, 0.2 / d->Lambda0);
+    }
+    if (!(d->dt > 0.0 && d->dt < d->dz)) return SCLF_EINVAL;   // c dt < dz
+
+    if (p->rho_gj_mode == SCLF_RHO_USER) {
+        d->rho0 = p->rho_gj_user[0];
+    } else {
+        d->rho0 = -(d->Lambda0 * d->Lambda0 / (4.0 * kPi)) * bracket(p->rho_gj_mode, 1.0, p, d);
+    }
+    if (!std::isfinite(d->rho0)) return SCLF_EINVAL;
+    if (p->macro_charge != 0.0) {
+        d->s = p->macro_charge;
+    } else {
+        if (p->target_particles <= 0) return SCLF_EINVAL;
+        d->s = -std::fabs(d->rho0) * d->L / double(p->target_particles);
+    }
+    if (!(d->s < 0.0) || !std::isfinite(d->s)) return SCLF_EINVAL;
+    return SCLF_OK;
+}
+
+int build_rho_gj(const tube_params* p, const tube_derived* d, double* rho) {
+    const int64_t nz = p->Nz;
+    if (p->rho_gj_mode == SCLF_RHO_USER) {
+        for (int64_t j = 0; j <= nz; ++j) {
+            if (!std::isfinite(p->rho_gj_user[j])) return SCLF_EINVAL;
+            rho[j] = p->rho_gj_user[j];
+        }
+        return SCLF_OK;
+    }
+    const double scale = -(d->Lambda0 * d->Lambda0 / (4.0 * kPi));
+    for (int64_t j = 0; j <= nz; ++j) {
+        const double z = double(j) * d->dz;                 // in R
+        const double eta = 1.0 + z * d->R_over_Rstar;       // r / R_*
+        rho[j] = scale * bracket(p->rho_gj_mode, eta, p, d);
+    }
+    return SCLF_OK;
+}
+
+// Eq. 4 with an empty tube: phi'' - phi / R^2 = 4 pi rho_GJ (R = 1) on the
+// nodes, phi_0 = 0 and phi'(L) = 0 through the ghost phi_{Nz+1} = phi_{Nz-1}.
+// Tridiagonal in phi_1..phi_Nz; Thomas elimination (the matrix is strictly
+// diagonally dominant, |2 + dz^2| > 2, so no pivoting is needed).
+void solve_poisson(const double* rho, int64_t nz, double dz, double* phi) {
+    const double diag = -(2.0 + dz * dz);
+    const double rhs_scale = 4.0 * kPi * dz * dz;
+    // forward sweep; cp[i] and dp[i] for unknown i = 1..nz stored at i
+    double* cp = new double[nz + 1];
+    double* dp = new double[nz + 1];
+    for (int64_t i = 1; i <= nz; ++i) {
+        const double sub = (i == 1) ? 0.0 : (i == nz ? 2.0 : 1.0);
+        const double sup = (i == nz) ? 0.0 : 1.0;
+        const double rhs = rhs_scale * rho[i];
+        const double denom = diag - (i == 1 ? 0.0 : sub * cp[i - 1]);
+        cp[i] = sup / denom;
+        dp[i] = (rhs - (i == 1 ? 0.0 : sub * dp[i - 1])) / denom;
+    }
+    phi[0] = 0.0;
+    phi[nz] = dp[nz];
+    for (int64_t i = nz - 1; i >= 1; --i) phi[i] = dp[i] - cp[i] * phi[i + 1];
+    delete[] cp;
+    delete[] dp;
+}
+
+}  // namespace sclf

@@ -1,0 +1,756 @@
+// C ABI of the sclf_tube library (declared in include/sclf_tube.h): tube
+// creation, the step loop (direct launches or replayed CUDA graphs), device
+// memory layout, read-back, checkpointing and event timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sclf_internal.h"
+
+using namespace sclf;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Layout_ {
+    int64_t cap_pad = 0, ntiles = 0;
+    int64_t off_state = 0, off_xi = 0, off_u = 0, off_ids = 0, off_tiles = 0;
+    int64_t off_ez = 0, off_er = 0, off_b = 0, off_jacc = 0, off_jlast = 0;
+    int64_t off_ez2 = 0, off_rho = 0, total = 0;
+};
+
+Layout_ plan(const tube_params* p) {
+    Layout_ l;
+    const int64_t rs = p->precision == SCLF_FP64 ? 8 : 4;
+    const int64_t tile = p->precision == SCLF_FP64 ? Layout<double>::kTile : Layout<float>::kTile;
+    const int64_t nz = p->Nz;
+    l.cap_pad = align_up(p->capacity > 0 ? p->capacity : 1, kMaxTile);
+    l.ntiles = l.cap_pad / tile;
+    int64_t o = 0;
+    auto take = [&](int64_t bytes) { const int64_t r = o; o = align_up(o + bytes, 256); return r; };
+    l.off_state = take(sizeof(DevState));
+    l.off_xi = take(l.cap_pad * rs);
+    l.off_u = take(l.cap_pad * rs);
+    l.off_ids = p->track_ids ? take(l.cap_pad * 8) : -1;
+    l.off_tiles = take(l.ntiles * 8);
+    l.off_ez = take(nz * 8);
+    l.off_er = take(2 * (nz + 1) * 8);
+    l.off_b = take(2 * nz * 8);
+    l.off_jacc = take(nz * 8);
+    l.off_jlast = take(nz * 8);
+    l.off_ez2 = take(2 * (nz + 1) * rs);
+    l.off_rho = take((nz + 1) * 8);
+    l.total = o;
+    return l;
+}
+
+}  // namespace
+
+struct sclf_tube {
+    tube_params p{};
+    tube_derived d{};
+    Layout_ lay;
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t gstream = nullptr;     // stream used for graph capture/replay
+    bool own_gstream = false;
+    bool owns_ws = false;
+    char* ws = nullptr;
+    DevState* st = nullptr;
+    void* xi = nullptr;
+    void* u = nullptr;
+    long long* ids = nullptr;
+    unsigned long long* tiles = nullptr;
+    double* ez = nullptr;
+    double* er[2] = {nullptr, nullptr};
+    double* b[2] = {nullptr, nullptr};
+    void* jacc = nullptr;
+    double* jlast = nullptr;
+    void* ez2 = nullptr;
+    double* rho_acc = nullptr;
+    std::vector<double> rho_gj;
+    FieldConsts fc{};
+    int push_grid = 0, compact_grid = 0;
+    int64_t host_step = 0;             // steps launched (== device step count)
+    int steps_since_compact = 0;
+    int compact_every = 64;
+    // graphs
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_steps = 0;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // pool, 3 per step, 2 per compaction
+    struct Rec { int kind; int e0; };  // kind 0 step (e0, e0+1, e0+2), 1 compaction
+    std::vector<Rec> recs;
+    int ev_next = 0;
+    tube_timing acc{};
+    unsigned long long slots_base = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return SCLF_OK;
+    std::fprintf(stderr, "sclf_tube: CUDA error %s\n", cudaGetErrorString(e));
+    return SCLF_ECUDA;
+}
+#define CK(x) do { const cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
+
+template <class Real>
+PushArgs<Real> push_args(sclf_tube* t) {
+    PushArgs<Real> a;
+    a.st = t->st;
+    a.xi = static_cast<Real*>(t->xi);
+    a.u = static_cast<Real*>(t->u);
+    a.ids = t->ids;
+    a.ez2 = static_cast<const Real*>(t->ez2);
+    a.jacc = t->jacc;
+    a.capacity = t->p.capacity;
+    a.nz = static_cast<int>(t->p.Nz);
+    a.nzf = static_cast<Real>(t->p.Nz);
+    a.dt = static_cast<Real>(t->d.dt);
+    a.cfl = static_cast<Real>(t->d.dt / t->d.dz);
+    return a;
+}
+
+template <class Real>
+FieldArgs<Real> field_args(sclf_tube* t, int parity) {
+    FieldArgs<Real> a;
+    a.st = t->st;
+    a.ez = t->ez;
+    a.er_in = t->er[parity];
+    a.er_out = t->er[parity ^ 1];
+    a.b_in = t->b[parity];
+    a.b_out = t->b[parity ^ 1];
+    a.jacc = t->jacc;
+    a.jlast = t->jlast;
+    a.ez2 = static_cast<Real*>(t->ez2);
+    a.c = t->fc;
+    return a;
+}
+
+template <class Real>
+CompactArgs<Real> compact_args(sclf_tube* t) {
+    CompactArgs<Real> a;
+    a.st = t->st;
+    a.xi = static_cast<Real*>(t->xi);
+    a.u = static_cast<Real*>(t->u);
+    a.ids = t->ids;
+    a.tile_state = t->tiles;
+    a.capacity = t->p.capacity;
+    return a;
+}
+
+bool fp64(const sclf_tube* t) { return t->p.precision == SCLF_FP64; }
+
+cudaError_t enqueue_push(sclf_tube* t, cudaStream_t s) {
+    return fp64(t) ? launch_push<double>(push_args<double>(t), t->p.accumulate, t->push_grid, s)
+                   : launch_push<float>(push_args<float>(t), t->p.accumulate, t->push_grid, s);
+}
+cudaError_t enqueue_field(sclf_tube* t, int parity, cudaStream_t s) {
+    return fp64(t) ? launch_field<double>(field_args<double>(t, parity), t->p.accumulate, s)
+                   : launch_field<float>(field_args<float>(t, parity), t->p.accumulate, s);
+}
+cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&t->st->ticket, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    return fp64(t) ? launch_compact<double>(compact_args<double>(t), t->compact_grid, s)
+                   : launch_compact<float>(compact_args<float>(t), t->compact_grid, s);
+}
+
+int read_state(sclf_tube* t, DevState* h) {
+    CK(cudaMemcpyAsync(h, t->st, sizeof(DevState), cudaMemcpyDeviceToHost, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+int drain_timing(sclf_tube* t);
+
+// Reserve k consecutive events of the timing pool; returns the first index
+// or -1. Drains (synchronises) when the pool is full.
+int reserve_events(sclf_tube* t, int k) {
+    if (t->ev_next + k > static_cast<int>(t->ev.size())) {
+        if (drain_timing(t) != SCLF_OK) return -1;
+    }
+    if (t->ev_next + k > static_cast<int>(t->ev.size())) return -1;
+    const int e0 = t->ev_next;
+    t->ev_next += k;
+    return e0;
+}
+
+int one_step(sclf_tube* t) {
+    const int parity = static_cast<int>(t->host_step & 1);
+    if (t->timing) {
+        const int e0 = reserve_events(t, 3);
+        if (e0 < 0) return SCLF_ECUDA;
+        CK(cudaEventRecord(t->ev[e0], t->stream));
+        CK(enqueue_push(t, t->stream));
+        CK(cudaEventRecord(t->ev[e0 + 1], t->stream));
+        CK(enqueue_field(t, parity, t->stream));
+        CK(cudaEventRecord(t->ev[e0 + 2], t->stream));
+        t->recs.push_back({0, e0});
+    } else {
+        CK(enqueue_push(t, t->stream));
+        CK(enqueue_field(t, parity, t->stream));
+    }
+    t->host_step += 1;
+    t->steps_since_compact += 1;
+    if (t->steps_since_compact >= t->compact_every) {
+        if (t->timing) {
+            const int e0 = reserve_events(t, 2);
+            if (e0 < 0) return SCLF_ECUDA;
+            CK(cudaEventRecord(t->ev[e0], t->stream));
+            CK(enqueue_compact(t, t->stream));
+            CK(cudaEventRecord(t->ev[e0 + 1], t->stream));
+            t->recs.push_back({1, e0});
+        } else {
+            CK(enqueue_compact(t, t->stream));
+        }
+        t->steps_since_compact = 0;
+    }
+    return SCLF_OK;
+}
+
+// One captured graph = chunk_steps steps starting at even parity, then a
+// compaction (chunk_steps == compact interval, rounded up to even).
+int build_chunk(sclf_tube* t) {
+    if (t->chunk) return SCLF_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < t->chunk_steps && e == cudaSuccess; ++k) {
+        e = enqueue_push(t, t->gstream);
+        if (e == cudaSuccess) e = enqueue_field(t, k & 1, t->gstream);
+    }
+    if (e == cudaSuccess) e = enqueue_compact(t, t->gstream);
+    const cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
+    CK(e2);
+    e = cudaGraphInstantiate(&t->chunk, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return SCLF_OK;
+}
+
+int launch_chunk(sclf_tube* t) {
+    if (t->gstream != t->stream) {
+        CK(cudaEventRecord(t->fork, t->stream));
+        CK(cudaStreamWaitEvent(t->gstream, t->fork, 0));
+    }
+    CK(cudaGraphLaunch(t->chunk, t->gstream));
+    if (t->gstream != t->stream) {
+        CK(cudaEventRecord(t->join, t->gstream));
+        CK(cudaStreamWaitEvent(t->stream, t->join, 0));
+    }
+    t->host_step += t->chunk_steps;
+    t->steps_since_compact = 0;
+    return SCLF_OK;
+}
+
+int drain_timing(sclf_tube* t) {
+    CK(cudaStreamSynchronize(t->stream));
+    for (const auto& r : t->recs) {
+        float ms = 0.f;
+        if (r.kind == 0) {
+            CK(cudaEventElapsedTime(&ms, t->ev[r.e0], t->ev[r.e0 + 1]));
+            t->acc.push_ms += ms;
+            CK(cudaEventElapsedTime(&ms, t->ev[r.e0 + 1], t->ev[r.e0 + 2]));
+            t->acc.field_ms += ms;
+            t->acc.n_steps += 1;
+        } else {
+            CK(cudaEventElapsedTime(&ms, t->ev[r.e0], t->ev[r.e0 + 1]));
+            t->acc.compact_ms += ms;
+            t->acc.n_compactions += 1;
+        }
+    }
+    t->recs.clear();
+    t->ev_next = 0;
+    return SCLF_OK;
+}
+
+template <class Real>
+void to_native(const double* z, const double* u, int64_t n, double dz, std::vector<char>& xs,
+               std::vector<char>& us) {
+    xs.resize(n * sizeof(Real));
+    us.resize(n * sizeof(Real));
+    Real* x = reinterpret_cast<Real*>(xs.data());
+    Real* v = reinterpret_cast<Real*>(us.data());
+    for (int64_t i = 0; i < n; ++i) {
+        x[i] = static_cast<Real>(z[i] / dz);
+        v[i] = static_cast<Real>(u[i]);
+    }
+}
+
+// Append n raw particles (already in the tube's precision) after the slots.
+int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int64_t* id) {
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    if (h.n_slots + n > t->p.capacity) return SCLF_ECAPACITY;
+    const int64_t rs = fp64(t) ? 8 : 4;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(static_cast<char*>(t->xi) + h.n_slots * rs, xi, n * rs,
+                           cudaMemcpyHostToDevice, t->stream));
+        CK(cudaMemcpyAsync(static_cast<char*>(t->u) + h.n_slots * rs, u, n * rs,
+                           cudaMemcpyHostToDevice, t->stream));
+        if (t->ids) {
+            if (id) {
+                CK(cudaMemcpyAsync(t->ids + h.n_slots, id, n * 8, cudaMemcpyHostToDevice, t->stream));
+            } else {
+                CK(fp64(t) ? launch_append<double>(t->st, nullptr, nullptr, t->ids, h.n_slots, n, false, t->stream)
+                           : launch_append<float>(t->st, nullptr, nullptr, t->ids, h.n_slots, n, false, t->stream));
+            }
+        }
+    }
+    const int64_t slots = h.n_slots + n;
+    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), slots, t->stream)
+               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), slots, t->stream));
+    CK(launch_finish_append(t->st, t->ez, n, t->fc, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tube_params_default(tube_params* p) {
+    if (!p) return SCLF_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->B_G = 1e12;
+    p->P_s = 1.0;
+    p->Rstar_cm = 1e6;
+    p->incl_rad = 0.0;
+    p->mass_g = 1.4 * 1.98847e33;
+    p->R_cm = 0.0;
+    p->L_over_R = 8.0;
+    p->Nz = 1024;
+    p->dt = 0.0;
+    p->rho_gj_mode = SCLF_RHO_FLAT;
+    p->precision = SCLF_FP32;
+    p->macro_charge = 0.0;
+    p->target_particles = 50000;
+    p->capacity = 1 << 20;
+    p->accumulate = SCLF_ACC_FIXED64;
+    p->track_ids = 1;
+    p->compact_interval = 64;
+    p->use_graphs = 1;
+    return SCLF_OK;
+}
+
+int tube_derive(const tube_params* p, tube_derived* d) { return derive(p, d); }
+
+int tube_workspace_bytes(const tube_params* p, int64_t* bytes) {
+    if (!p || !bytes) return SCLF_EINVAL;
+    tube_derived d;
+    const int rc = derive(p, &d);
+    if (rc) return rc;
+    *bytes = plan(p).total;
+    return SCLF_OK;
+}
+
+int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, void* stream,
+                tube_t* out) {
+    if (!p || !out) return SCLF_EINVAL;
+    *out = nullptr;
+    sclf_tube* t = new (std::nothrow) sclf_tube();
+    if (!t) return SCLF_ENOMEM;
+    t->p = *p;
+    t->p.rho_gj_user = nullptr;
+    int rc = derive(p, &t->d);
+    if (rc) { delete t; return rc; }
+    t->lay = plan(p);
+    t->stream = static_cast<cudaStream_t>(stream);
+    t->compact_every = p->compact_interval > 0 ? p->compact_interval : 64;
+    t->chunk_steps = t->compact_every + (t->compact_every & 1);
+
+    auto fail = [&](int code) { tube_destroy(t); return code; };
+    if (cudaGetDevice(&t->device) != cudaSuccess) return fail(SCLF_ECUDA);
+    if (cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess)
+        return fail(SCLF_ECUDA);
+
+    if (dev_workspace) {
+        if (ws_bytes < t->lay.total || (reinterpret_cast<uintptr_t>(dev_workspace) & 255u))
+            return fail(SCLF_ENOMEM);
+        t->ws = static_cast<char*>(dev_workspace);
+    } else {
+        if (cudaMalloc(&t->ws, t->lay.total) != cudaSuccess) { t->ws = nullptr; return fail(SCLF_ENOMEM); }
+        t->owns_ws = true;
+    }
+    const Layout_& l = t->lay;
+    t->st = reinterpret_cast<DevState*>(t->ws + l.off_state);
+    t->xi = t->ws + l.off_xi;
+    t->u = t->ws + l.off_u;
+    t->ids = l.off_ids >= 0 ? reinterpret_cast<long long*>(t->ws + l.off_ids) : nullptr;
+    t->tiles = reinterpret_cast<unsigned long long*>(t->ws + l.off_tiles);
+    t->ez = reinterpret_cast<double*>(t->ws + l.off_ez);
+    t->er[0] = reinterpret_cast<double*>(t->ws + l.off_er);
+    t->er[1] = t->er[0] + (p->Nz + 1);
+    t->b[0] = reinterpret_cast<double*>(t->ws + l.off_b);
+    t->b[1] = t->b[0] + p->Nz;
+    t->jacc = t->ws + l.off_jacc;
+    t->jlast = reinterpret_cast<double*>(t->ws + l.off_jlast);
+    t->ez2 = t->ws + l.off_ez2;
+    t->rho_acc = reinterpret_cast<double*>(t->ws + l.off_rho);
+
+    // (a7) rho_GJ, Eq. 4 and the initial fields
+    const int64_t nz = p->Nz;
+    t->rho_gj.assign(nz + 1, 0.0);
+    rc = build_rho_gj(p, &t->d, t->rho_gj.data());
+    if (rc) return fail(rc);
+    std::vector<double> phi(nz + 1), ez0(nz);
+    solve_poisson(t->rho_gj.data(), nz, t->d.dz, phi.data());
+    for (int64_t j = 0; j < nz; ++j) ez0[j] = -(phi[j + 1] - phi[j]) / t->d.dz;   // E_z = -phi'
+    // E_r = phi / R with R = 1 (d/dr -> 1/R, phi = 0 on the wall)
+
+    const double dt = t->d.dt, dz = t->d.dz, s = t->d.s;
+    t->fc.nz = static_cast<int>(nz);
+    t->fc.dt = dt;
+    t->fc.cdt = dt / dz;
+    t->fc.fourpi_dt = 4.0 * kPi * dt;
+    t->fc.s_over_dt = s / dt;
+    t->fc.four_pi_s = 4.0 * kPi * s;
+    t->fc.two_pi_dz_rho0 = 2.0 * kPi * dz * t->rho_gj[0];
+    t->fc.sheet = 4.0 * kPi * std::fabs(s);
+
+    if (cudaMemsetAsync(t->ws, 0, l.total, t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
+    DevState h;
+    std::memset(&h, 0, sizeof(h));
+    h.compact_epoch = 1;
+    if (cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream) ||
+        cudaMemcpyAsync(t->ez, ez0.data(), nz * 8, cudaMemcpyHostToDevice, t->stream) ||
+        cudaMemcpyAsync(t->er[0], phi.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream))
+        return fail(SCLF_ECUDA);
+    cudaError_t e = fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), int(nz), t->stream)
+                            : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), int(nz), t->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    if (launch_finish_append(t->st, t->ez, 0, t->fc, t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
+    if (cudaStreamSynchronize(t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
+
+    t->push_grid = fp64(t) ? push_grid_size<double>(p->accumulate, t->sms)
+                           : push_grid_size<float>(p->accumulate, t->sms);
+    t->compact_grid = fp64(t) ? compact_grid_size<double>(t->sms) : compact_grid_size<float>(t->sms);
+    const int64_t tile = fp64(t) ? Layout<double>::kTile : Layout<float>::kTile;
+    const int64_t max_tiles = l.cap_pad / tile;
+    if (t->push_grid > max_tiles) t->push_grid = static_cast<int>(max_tiles);
+    if (t->compact_grid > max_tiles) t->compact_grid = static_cast<int>(max_tiles);
+
+    if (t->stream) {
+        t->gstream = t->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&t->gstream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(SCLF_ECUDA);
+        t->own_gstream = true;
+    }
+    if (cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(SCLF_ECUDA);
+    *out = t;
+    return SCLF_OK;
+}
+
+int tube_destroy(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    if (t->stream || t->gstream) cudaStreamSynchronize(t->stream);
+    if (t->chunk) cudaGraphExecDestroy(t->chunk);
+    for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
+    if (t->fork) cudaEventDestroy(t->fork);
+    if (t->join) cudaEventDestroy(t->join);
+    if (t->own_gstream && t->gstream) {
+        cudaStreamSynchronize(t->gstream);
+        cudaStreamDestroy(t->gstream);
+    }
+    if (t->owns_ws && t->ws) cudaFree(t->ws);
+    delete t;
+    return SCLF_OK;
+}
+
+int tube_get_derived(tube_t t, tube_derived* d) {
+    if (!t || !d) return SCLF_EINVAL;
+    *d = t->d;
+    return SCLF_OK;
+}
+
+int tube_inject(tube_t t, int64_t* n_injected) {
+    if (!t) return SCLF_EINVAL;
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    int64_t n = h.n_inj;
+    if (h.n_slots + n > t->p.capacity) return SCLF_ECAPACITY;
+    CK(fp64(t) ? launch_append<double>(t->st, static_cast<double*>(t->xi), static_cast<double*>(t->u), t->ids, h.n_slots, n, true, t->stream)
+               : launch_append<float>(t->st, static_cast<float*>(t->xi), static_cast<float*>(t->u), t->ids, h.n_slots, n, true, t->stream));
+    const int64_t slots = h.n_slots + n;
+    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), slots, t->stream)
+               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), slots, t->stream));
+    CK(launch_finish_append(t->st, t->ez, n, t->fc, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    if (n_injected) *n_injected = n;
+    return SCLF_OK;
+}
+
+int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
+    if (!t || n < 0 || (n > 0 && (!z || !u))) return SCLF_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(z[i] >= 0.0 && z[i] < t->d.L) || !std::isfinite(u[i])) return SCLF_EINVAL;
+    std::vector<char> xs, us;
+    if (fp64(t)) to_native<double>(z, u, n, t->d.dz, xs, us);
+    else to_native<float>(z, u, n, t->d.dz, xs, us);
+    // a position that rounds up to the top node is outside the tube
+    for (int64_t i = 0; i < n; ++i) {
+        const double x = fp64(t) ? reinterpret_cast<double*>(xs.data())[i]
+                                 : double(reinterpret_cast<float*>(xs.data())[i]);
+        if (!(x < double(t->p.Nz))) return SCLF_EINVAL;
+    }
+    return append_raw(t, n, xs.data(), us.data(), nullptr);
+}
+
+int tube_step(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    return one_step(t);
+}
+
+int tube_run(tube_t t, int64_t nsteps) {
+    if (!t || nsteps < 0) return SCLF_EINVAL;
+    while (nsteps > 0) {
+        if (t->p.use_graphs && !t->timing && (t->host_step & 1) == 0 &&
+            t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
+            int rc = build_chunk(t);
+            if (rc) return rc;
+            rc = launch_chunk(t);
+            if (rc) return rc;
+            nsteps -= t->chunk_steps;
+            continue;
+        }
+        const int rc = one_step(t);
+        if (rc) return rc;
+        nsteps -= 1;
+    }
+    return SCLF_OK;
+}
+
+int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi, double* J, double* rho) {
+    if (!t) return SCLF_EINVAL;
+    const int64_t nz = t->p.Nz;
+    const int par = static_cast<int>(t->host_step & 1);
+    CK(cudaStreamSynchronize(t->stream));
+    if (Ez) CK(cudaMemcpyAsync(Ez, t->ez, nz * 8, cudaMemcpyDeviceToHost, t->stream));
+    if (Er) CK(cudaMemcpyAsync(Er, t->er[par], (nz + 1) * 8, cudaMemcpyDeviceToHost, t->stream));
+    if (Bphi) CK(cudaMemcpyAsync(Bphi, t->b[par], nz * 8, cudaMemcpyDeviceToHost, t->stream));
+    if (J) CK(cudaMemcpyAsync(J, t->jlast, nz * 8, cudaMemcpyDeviceToHost, t->stream));
+    if (rho) {
+        DevState h;
+        int rc = read_state(t, &h);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(t->rho_acc, 0, (nz + 1) * 8, t->stream));
+        CK(fp64(t) ? launch_rho<double>(static_cast<const double*>(t->xi), h.n_slots, t->rho_acc, int(nz), t->stream)
+                   : launch_rho<float>(static_cast<const float*>(t->xi), h.n_slots, t->rho_acc, int(nz), t->stream));
+        CK(cudaMemcpyAsync(rho, t->rho_acc, (nz + 1) * 8, cudaMemcpyDeviceToHost, t->stream));
+    }
+    CK(cudaStreamSynchronize(t->stream));
+    if (rho) {
+        const double scale = t->d.s / t->d.dz;     // rho_j = s * sum(w) / dz
+        for (int64_t j = 0; j <= nz; ++j) rho[j] *= scale;
+    }
+    return SCLF_OK;
+}
+
+static int read_raw(tube_t t, int64_t cap, int64_t* n, void* xo, void* uo, int64_t* ido,
+                    bool convert) {
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    const int64_t ns = h.n_slots;
+    const int64_t rs = fp64(t) ? 8 : 4;
+    std::vector<char> xs(ns * rs), us(ns * rs);
+    std::vector<long long> is(t->ids ? ns : 0);
+    if (ns > 0) {
+        CK(cudaMemcpyAsync(xs.data(), t->xi, ns * rs, cudaMemcpyDeviceToHost, t->stream));
+        CK(cudaMemcpyAsync(us.data(), t->u, ns * rs, cudaMemcpyDeviceToHost, t->stream));
+        if (t->ids) CK(cudaMemcpyAsync(is.data(), t->ids, ns * 8, cudaMemcpyDeviceToHost, t->stream));
+        CK(cudaStreamSynchronize(t->stream));
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < ns; ++i) {
+        const double x = fp64(t) ? reinterpret_cast<double*>(xs.data())[i]
+                                 : double(reinterpret_cast<float*>(xs.data())[i]);
+        if (!(x >= 0.0)) continue;                       // hole
+        if (k < cap) {
+            const double uu = fp64(t) ? reinterpret_cast<double*>(us.data())[i]
+                                      : double(reinterpret_cast<float*>(us.data())[i]);
+            if (convert) {
+                if (xo) static_cast<double*>(xo)[k] = x * t->d.dz;
+                if (uo) static_cast<double*>(uo)[k] = uu;
+            } else {
+                if (xo) std::memcpy(static_cast<char*>(xo) + k * rs, xs.data() + i * rs, rs);
+                if (uo) std::memcpy(static_cast<char*>(uo) + k * rs, us.data() + i * rs, rs);
+            }
+            if (ido) ido[k] = t->ids ? is[i] : -1;
+        }
+        ++k;
+    }
+    if (n) *n = k;
+    return SCLF_OK;
+}
+
+int tube_read_particles(tube_t t, int64_t cap, int64_t* n, double* z, double* u, int64_t* id) {
+    if (!t || cap < 0) return SCLF_EINVAL;
+    return read_raw(t, cap, n, z, u, id, true);
+}
+
+int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u, int64_t* id) {
+    if (!t || cap < 0) return SCLF_EINVAL;
+    return read_raw(t, cap, n, xi, u, id, false);
+}
+
+int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, const int64_t* id) {
+    if (!t || n < 0 || n > t->p.capacity || (n > 0 && (!xi || !u))) return SCLF_EINVAL;
+    int64_t max_id = n - 1;
+    for (int64_t i = 0; i < n; ++i) {
+        const double x = fp64(t) ? static_cast<const double*>(xi)[i]
+                                 : double(static_cast<const float*>(xi)[i]);
+        const double v = fp64(t) ? static_cast<const double*>(u)[i]
+                                 : double(static_cast<const float*>(u)[i]);
+        if (!(x >= 0.0 && x < double(t->p.Nz)) || !std::isfinite(v)) return SCLF_EINVAL;
+        if (id && id[i] > max_id) max_id = id[i];
+    }
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    h.n_slots = 0;
+    h.n_live = 0;
+    h.total_injected = 0;
+    CK(cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream));
+    rc = append_raw(t, n, xi, u, id);
+    if (rc) return rc;
+    if (id) {   // IDs continue after the largest loaded one
+        rc = read_state(t, &h);
+        if (rc) return rc;
+        h.total_injected = max_id + 1;
+        CK(cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream));
+        CK(cudaStreamSynchronize(t->stream));
+    }
+    return SCLF_OK;
+}
+
+int tube_solve_fields(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    const int64_t nz = t->p.Nz;
+    std::vector<double> rho(nz + 1), src(nz + 1), phi(nz + 1), ez0(nz);
+    int rc = tube_read_fields(t, nullptr, nullptr, nullptr, nullptr, rho.data());
+    if (rc) return rc;
+    // phi'' - phi = 4 pi (rho_GJ - rho)
+    for (int64_t j = 0; j <= nz; ++j) src[j] = t->rho_gj[j] - rho[j];
+    solve_poisson(src.data(), nz, t->d.dz, phi.data());
+    for (int64_t j = 0; j < nz; ++j) ez0[j] = -(phi[j + 1] - phi[j]) / t->d.dz;
+    const int par = static_cast<int>(t->host_step & 1);
+    CK(cudaMemcpyAsync(t->ez, ez0.data(), nz * 8, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->er[par], phi.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemsetAsync(t->b[par], 0, nz * 8, t->stream));
+    CK(fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), int(nz), t->stream)
+               : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), int(nz), t->stream));
+    DevState h;
+    rc = read_state(t, &h);
+    if (rc) return rc;
+    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), h.n_slots, t->stream)
+               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), h.n_slots, t->stream));
+    CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+int tube_status(tube_t t, tube_stats* out) {
+    if (!t || !out) return SCLF_EINVAL;
+    DevState h;
+    const int rc = read_state(t, &h);
+    if (rc) return rc;
+    out->step = h.step;
+    out->n_particles = h.n_live;
+    out->n_slots = h.n_slots;
+    out->total_injected = h.total_injected;
+    out->last_injected = h.last_injected;
+    out->last_removed = h.last_removed;
+    out->pending_injection = h.n_inj;
+    out->surface_field = h.surface_field;
+    out->flags = h.flags;
+    out->reserved = 0;
+    return SCLF_OK;
+}
+
+int tube_check(tube_t t) {
+    tube_stats s;
+    const int rc = tube_status(t, &s);
+    if (rc) return rc;
+    if (s.flags & SCLF_FLAG_TIMEOUT) return SCLF_ETIMEOUT;
+    if (s.flags & SCLF_FLAG_NONFINITE) return SCLF_ENONFINITE;
+    if (s.flags & SCLF_FLAG_CAPACITY) return SCLF_ECAPACITY;
+    return SCLF_OK;
+}
+
+int tube_compact(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    CK(enqueue_compact(t, t->stream));
+    t->steps_since_compact = 0;
+    return SCLF_OK;
+}
+
+int tube_set_timing(tube_t t, int enable) {
+    if (!t) return SCLF_EINVAL;
+    if (enable) {
+        if (t->ev.empty()) {
+            t->ev.resize(3 * 2048 + 8, nullptr);
+            for (auto& e : t->ev)
+                if (cudaEventCreate(&e) != cudaSuccess) return SCLF_ECUDA;
+        }
+        CK(cudaStreamSynchronize(t->stream));
+        t->recs.clear();
+        t->ev_next = 0;
+        std::memset(&t->acc, 0, sizeof(t->acc));
+        DevState h;
+        const int rc = read_state(t, &h);
+        if (rc) return rc;
+        t->slots_base = h.slots_processed;
+        t->timing = true;
+    } else {
+        const int rc = drain_timing(t);
+        t->timing = false;
+        return rc;
+    }
+    return SCLF_OK;
+}
+
+int tube_get_timing(tube_t t, tube_timing* out) {
+    if (!t || !out) return SCLF_EINVAL;
+    int rc = drain_timing(t);
+    if (rc) return rc;
+    DevState h;
+    rc = read_state(t, &h);
+    if (rc) return rc;
+    *out = t->acc;
+    out->particle_slots = static_cast<int64_t>(h.slots_processed - t->slots_base);
+    return SCLF_OK;
+}
+
+const char* tube_strerror(int code) {
+    switch (code) {
+        case SCLF_OK: return "ok";
+        case SCLF_EINVAL: return "invalid argument";
+        case SCLF_ENOMEM: return "out of memory or workspace too small";
+        case SCLF_ECUDA: return "CUDA runtime error";
+        case SCLF_ECAPACITY: return "particle capacity exhausted";
+        case SCLF_ENONFINITE: return "non-finite particle state";
+        case SCLF_ETIMEOUT: return "device-side wait timed out";
+        case SCLF_ESTATE: return "invalid state for this call";
+        default: return "unknown error";
+    }
+}
+
+const char* tube_version(void) { return "sclf_tube 0.1.0 sm_103a"; }
+
+}  // extern "C"

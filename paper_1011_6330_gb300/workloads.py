@@ -1,0 +1,43 @@
+"""Named tube configurations used by the tests and the benchmark.
+
+Each returns keyword arguments for ``binding.default_params``.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import binding as B
+
+M_SUN = 1.98847e33
+
+
+def flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FP64, capacity=1 << 17):
+    """Flat-space SCLF tube: R = 1, L = 8 R, Nz = 1024, rho_GJ = -1 in code
+    units (Lambda = sqrt(4 pi)), dt = 0.4 dz, macro charge giving 5e4
+    particles for a tube full of rho_GJ."""
+    nz, L = 1024, 8.0
+    dz = L / nz
+    return dict(L_over_R=L, Nz=nz, dt=0.4 * dz, rho_gj_mode=B.SCLF_RHO_USER,
+                rho_gj_user=-np.ones(nz + 1), target_particles=50000,
+                capacity=capacity, precision=precision, accumulate=accumulate,
+                track_ids=1)
+
+
+def gr_tube(B_G=1e12, P_s=0.5, Rstar_cm=1e6, incl=0.5, Nz=65536, n_particles=10 ** 8,
+            capacity=None, precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64,
+            track_ids=0):
+    """Frame-dragging tube of a pulsar: R = R_* sqrt(R_* Omega / c), length
+    2 R_*, GR rho_GJ (Eq. 6-7) at inclination incl, dt from the default
+    rule, macro charge so that n_particles carry rho_GJ(0) over the tube."""
+    omega = 2.0 * math.pi / P_s
+    theta_p = math.sqrt(omega * Rstar_cm / 2.99792458e10)
+    L = 2.0 / theta_p                          # 2 R_* in units of R = R_* theta_p
+    if capacity is None:
+        capacity = int(n_particles * 1.02) + (1 << 20)
+    return dict(B_G=B_G, P_s=P_s, Rstar_cm=Rstar_cm, incl_rad=incl, mass_g=1.4 * M_SUN,
+                R_cm=0.0, L_over_R=L, Nz=Nz, dt=0.0, rho_gj_mode=B.SCLF_RHO_GR,
+                target_particles=n_particles, capacity=capacity, precision=precision,
+                accumulate=accumulate, track_ids=track_ids)

@@ -1,0 +1,84 @@
+"""The C ABI library on a machine without a GPU: it builds, loads, exports
+every function include/sclf_tube.h declares, and its host-only calls
+(parameter defaults, unit derivation, workspace sizing) behave."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1011_6330_gb300 import binding as B
+from paper_1011_6330_gb300 import workloads
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1011_6330_gb300 import build
+        build.build()
+    return B.load()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = B.header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B.SIGNATURES), set(names) ^ set(B.SIGNATURES)
+
+
+def test_version_and_error_strings(lib):
+    assert b"sm_103a" in lib.tube_version()
+    for code in range(0, -8, -1):
+        assert lib.tube_strerror(code)
+    assert lib.tube_strerror(-99) == b"unknown error"
+
+
+def test_defaults_are_the_standard_pulsar(lib):
+    p = B.default_params()
+    assert (p.B_G, p.P_s, p.Rstar_cm) == (1e12, 1.0, 1e6)
+    d = B.derive(p)
+    cu = orc.code_units(1e12, 1.0, 1e6, 0.0, 1.4 * orc.M_SUN)
+    # two independent restatements of the Sec. 3 / Eq. 7 formulas
+    for k in ("theta_p", "R_cm", "n0", "omega_p0", "Lambda0", "kappa", "theta_star"):
+        assert abs(d[k] / cu[k] - 1.0) < 1e-12, k
+    assert d["rho0"] == pytest.approx(-cu["Lambda0"] ** 2 / (4 * math.pi), rel=1e-13)
+    assert d["dt"] == pytest.approx(min(0.4 * d["dz"], 0.2 / d["Lambda0"]), rel=0)
+
+
+def test_gr_workload_units(lib):
+    p = B.default_params(**workloads.gr_tube())
+    d = B.derive(p)
+    cu = orc.code_units(1e12, 0.5, 1e6, 0.5, 1.4 * orc.M_SUN)
+    assert abs(d["Lambda0"] / cu["Lambda0"] - 1) < 1e-12
+    assert abs(d["L"] - 2.0 / cu["theta_p"]) < 1e-9          # 2 R_*
+    z0 = orc.rho_gj_profile(orc.RHO_GR, 0.0, cu["Lambda0"], 0.5, cu["theta_star"],
+                            cu["R_over_Rstar"], cu["kappa"])
+    assert abs(d["rho0"] / z0 - 1) < 1e-13
+    assert d["s"] == pytest.approx(-abs(z0) * d["L"] / 1e8, rel=1e-13)
+    assert 0 < d["dt"] < d["dz"]
+
+
+def test_invalid_parameters_are_rejected(lib):
+    kw = workloads.flat_sclf_small()
+    for bad in (dict(dt=kw["L_over_R"] / kw["Nz"]),       # c dt = dz
+                dict(Nz=1), dict(capacity=-1), dict(precision=7),
+                dict(accumulate=3), dict(rho_gj_mode=9), dict(L_over_R=0.0)):
+        p = B.default_params(**{**kw, **bad})
+        with pytest.raises(B.SclfError) as e:
+            B.derive(p)
+        assert e.value.code == -1
+    p = B.default_params(**{**kw, "macro_charge": 0.5})
+    with pytest.raises(B.SclfError):
+        B.derive(p)
+
+
+def test_workspace_grows_with_capacity_and_grid(lib):
+    a = B.workspace_bytes(B.default_params(**workloads.flat_sclf_small(capacity=1 << 16)))
+    b = B.workspace_bytes(B.default_params(**workloads.flat_sclf_small(capacity=1 << 18)))
+    assert b - a >= 3 * (1 << 16) * 8 * 2          # xi, u (FP64) + ids
+    g = B.workspace_bytes(B.default_params(**workloads.gr_tube()))
+    assert g >= 2 * 4 * 10 ** 8                     # FP32 xi and u of 1e8 slots
+    assert g < 2 * 4 * 10 ** 8 * 1.1 + 64 * 2 ** 20

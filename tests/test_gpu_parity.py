@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Integers (injection counts, IDs, removal counts) must match exactly.
+Floating point is compared norm-wise per field and per step,
+max|x - x_ref| / max|x_ref|: <= 1e-12 for FP64 particles, <= 1e-5 for FP32
+particles (against the oracle run in the same particle precision, so that
+the floating-point decisions -- which cell, inside or outside -- are taken
+in the same precision on both sides).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1011_6330_gb300 import binding as B
+from paper_1011_6330_gb300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {B.SCLF_FP64: 1e-12, B.SCLF_FP32: 1e-5}
+
+
+def rel(a, b):
+    den = float(np.max(np.abs(b))) if np.size(b) else 0.0
+    return float(np.max(np.abs(a - b))) / den if den > 0 else float(np.max(np.abs(a - b), initial=0.0))
+
+
+def pair(gpu_lib, kw, oprec, oacc, capacity=None):
+    t = B.Tube(B.default_params(**kw))
+    d = t.derived
+    rho = np.asarray(kw["rho_gj_user"]) if kw.get("rho_gj_mode") == B.SCLF_RHO_USER else None
+    if rho is None:
+        cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+        z = np.arange(kw["Nz"] + 1) * (kw["L_over_R"] / kw["Nz"])
+        rho = orc.rho_gj_profile(orc.RHO_GR, z, cu["Lambda0"], kw["incl_rad"],
+                                 cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+    o = orc.Tube(kw["Nz"], kw["L_over_R"], d["dt"], rho, d["s"], precision=oprec,
+                 accumulate=oacc, capacity=capacity)
+    return t, o
+
+
+def compare(t, o, tol, what=""):
+    st = t.status()
+    assert st["step"] == o.step_count
+    assert st["total_injected"] == o.total_injected, what
+    assert st["last_injected"] == o.last_injected, what
+    assert st["last_removed"] == o.last_removed, what
+    assert st["n_particles"] == o.xi.size, what
+    z, u, ids = t.read_particles()
+    assert np.array_equal(ids, o.ids), what
+    f = t.read_fields(rho=False)
+    errs = dict(ez=rel(f["ez"], o.ez), er=rel(f["er"], o.er), b=rel(f["b"], o.b),
+                j=rel(f["j"], o.j))
+    if z.size:
+        errs["z"] = float(np.max(np.abs(z - o.z()))) / o.L
+        g, go = np.sqrt(1 + u * u), o.gamma()
+        errs["gamma"] = float(np.max(np.abs(g - go) / go))
+    for k, v in errs.items():
+        assert v <= tol, (what, k, v)
+    return errs
+
+
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [B.SCLF_FP64, B.SCLF_FP32])
+def test_initial_fields_match_oracle(gpu_lib, prec):
+    kw = workloads.flat_sclf_small(precision=prec)
+    t, o = pair(gpu_lib, kw, "f64", "sum")
+    f = t.read_fields()
+    assert rel(f["ez"], o.ez) < 1e-12 and rel(f["er"], o.er) < 1e-12
+    assert np.all(f["b"] == 0) and np.all(f["rho"] == 0)
+    st = t.status()
+    n, es = orc.injection_count(o.ez[0], 0, o.s, o.dz, o.rho_gj[0])
+    assert st["pending_injection"] == n and abs(st["surface_field"] - es) < 1e-12 * abs(es)
+    t.close()
+
+
+def test_initial_fields_gr_profile_match_oracle(gpu_lib):
+    kw = workloads.gr_tube(Nz=4096, n_particles=10 ** 5, P_s=0.3)
+    t, o = pair(gpu_lib, kw, "f32", "fixed")
+    f = t.read_fields(rho=False)
+    assert rel(f["ez"], o.ez) < 1e-11 and rel(f["er"], o.er) < 1e-11
+    assert t.status()["pending_injection"] == o.injection_count()
+    t.close()
+
+
+def test_fp64_tube_matches_oracle_every_step(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FP64)
+    t, o = pair(gpu_lib, kw, "f64", "sum")
+    worst = {}
+    for n in range(200):
+        t.step()
+        o.step()
+        e = compare(t, o, TOL[B.SCLF_FP64], "step %d" % n)
+        worst = {k: max(v, worst.get(k, 0.0)) for k, v in e.items()}
+    assert o.xi.size > 3000
+    print("fp64 worst", worst)
+    t.close()
+
+
+@pytest.mark.parametrize("acc,oacc", [(B.SCLF_ACC_FIXED64, "fixed"), (B.SCLF_ACC_FP64, "sum")])
+def test_fp32_tube_matches_same_precision_oracle_every_step(gpu_lib, acc, oacc):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=acc)
+    t, o = pair(gpu_lib, kw, "f32", oacc)
+    worst = {}
+    for n in range(200):
+        t.step()
+        o.step()
+        e = compare(t, o, TOL[B.SCLF_FP32], "step %d" % n)
+        worst = {k: max(v, worst.get(k, 0.0)) for k, v in e.items()}
+    print("fp32", oacc, "worst", worst)
+    t.close()
+
+
+def test_fp32_error_against_fp64_oracle_is_stated(gpu_lib):
+    """FP32 particles against the FP64 definition: bounded, and reported."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    t, o = pair(gpu_lib, kw, "f64", "sum")
+    t.run(200)
+    o.run(200)
+    f = t.read_fields(rho=False)
+    z, u, ids = t.read_particles()
+    e_ez = rel(f["ez"], o.ez)
+    common = min(ids.size, o.ids.size)
+    print("fp32 vs fp64 oracle after 200 steps: Ez %.2e, injected %d vs %d"
+          % (e_ez, t.status()["total_injected"], o.total_injected))
+    assert e_ez < 1e-3
+    assert abs(t.status()["total_injected"] - o.total_injected) <= 0.01 * o.total_injected
+    assert common > 0
+    t.close()
+
+
+def test_ragged_tiles_compaction_schedule_and_graphs_do_not_change_results(gpu_lib):
+    """Prefilled particles spanning several tiles with a ragged tail; the same
+    run with compaction every 3 steps, every 1000 steps, and with CUDA graphs,
+    is bit-identical (fixed-point current), and matches the oracle."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    z, u = synth.random_particles(4096 * 3 + 1234, kw["L_over_R"], seed=7, u_sigma=2.0)
+    runs = []
+    for ci, graphs in ((3, 0), (1000, 0), (4, 1)):
+        t, o = pair(gpu_lib, dict(kw, compact_interval=ci, use_graphs=graphs), "f32", "fixed")
+        t.add_particles(z, u)
+        o.add_particles(z, u)
+        t.run(101)
+        o.run(101)
+        compare(t, o, TOL[B.SCLF_FP32], "compact %d graphs %d" % (ci, graphs))
+        runs.append((t.read_particles(), t.read_fields(rho=False)))
+        t.close()
+    (p0, f0) = runs[0]
+    for (p1, f1) in runs[1:]:
+        for a, b in zip(p0, p1):
+            assert np.array_equal(a, b)
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(f0[k], f1[k])
+
+
+def test_empty_tube_with_positive_rho_gj_stays_empty_and_stationary(gpu_lib):
+    nz = 257
+    kw = dict(workloads.flat_sclf_small(precision=B.SCLF_FP64), Nz=nz, dt=0.4 * 8.0 / nz,
+              rho_gj_user=np.linspace(0.5, 1.5, nz + 1), macro_charge=-1e-3)
+    t, o = pair(gpu_lib, kw, "f64", "sum")
+    f0 = t.read_fields(rho=False)
+    t.run(500)
+    o.run(500)
+    st = t.status()
+    assert st["n_particles"] == 0 and st["total_injected"] == 0
+    f = t.read_fields(rho=False)
+    assert rel(f["ez"], f0["ez"]) < 1e-12 and np.max(np.abs(f["b"])) < 1e-12 * np.max(np.abs(f0["ez"]))
+    compare(t, o, 1e-12)
+    t.close()
+
+
+def test_capacity_exhaustion_clips_injection_and_sets_the_flag(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64,
+                                   capacity=100)
+    t, o = pair(gpu_lib, kw, "f32", "fixed", capacity=100)
+    t.step()
+    o.step()
+    st = t.status()
+    assert st["total_injected"] == 100 == o.total_injected
+    assert st["flags"] & B.FLAG_CAPACITY and o.capacity_hit
+    assert t.check() == -4
+    compare(t, o, TOL[B.SCLF_FP32])
+    t.close()
+
+
+def test_particles_leave_through_both_ends(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FP64)
+    t, o = pair(gpu_lib, kw, "f64", "sum")
+    dz = kw["L_over_R"] / kw["Nz"]
+    z = np.array([0.1 * dz, 0.5, 8.0 - 0.1 * dz, 3.0])
+    u = np.array([-50.0, 0.0, 50.0, 1.0])
+    t.add_particles(z, u)
+    o.add_particles(z, u)
+    t.step()
+    o.step()
+    assert o.last_removed >= 2
+    compare(t, o, 1e-12)
+    t.close()
+
+
+def test_inject_call_save_load_and_invalid_input(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    t, o = pair(gpu_lib, kw, "f32", "fixed")
+    n = t.inject()
+    assert n == o.inject() and n > 1000
+    t.run(30)
+    xi, u, ids = t.save_particles()
+    st = t.status()
+    t.load_particles(xi, u, ids)
+    xi2, u2, ids2 = t.save_particles()
+    assert np.array_equal(xi, xi2) and np.array_equal(u, u2) and np.array_equal(ids, ids2)
+    assert t.status()["total_injected"] == int(ids.max()) + 1
+    assert t.status()["pending_injection"] == st["pending_injection"]
+    with pytest.raises(B.SclfError):
+        t.load_particles(np.array([1.0], np.float32), np.array([np.inf], np.float32))
+    with pytest.raises(B.SclfError):
+        t.add_particles([8.0], [0.0])        # z = L is outside the tube
+    t.close()
+
+
+def test_full_size_gr_step_against_oracle_on_all_particles(gpu_lib):
+    """The benchmark's tube (frame-dragging rho_GJ, 1e8 FP32 particles, Nz =
+    65536, fixed-point current) in the launch configuration the benchmark
+    times: one step from a prefilled state is checked against the oracle on
+    every particle -- each push bit for bit, the whole current grid and the
+    field update exactly, the removal and the next injection counts."""
+    kw = workloads.gr_tube()
+    t = B.Tube(B.default_params(**kw))
+    d = t.derived
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    eta = lambda zz: 1.0 + zz * cu["R_over_Rstar"]
+    gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(kw["incl_rad"])
+    z, u = synth.prefilled_beam(kw["target_particles"], d["L"], gfar, seed=0, eta_of_z=eta)
+    t.add_particles(z, u)
+    del z, u
+    t.solve_fields()
+    t.run(3)
+    f0 = t.read_fields(rho=False)
+    xi0, u0, _ = t.save_particles()
+    n_inj = t.status()["pending_injection"]
+    t.step()
+    f1 = t.read_fields(rho=False)
+    xi1, u1, _ = t.save_particles()
+    st = t.status()
+    nz = kw["Nz"]
+    assert st["last_injected"] == n_inj
+    xs_all = np.concatenate([xi0, np.zeros(n_inj, np.float32)])
+    us_all = np.concatenate([u0, np.zeros(n_inj, np.float32)])
+    del xi0, u0
+    acc = np.zeros(nz, np.int64)
+    x1o = np.empty_like(xs_all)
+    u1o = np.empty_like(us_all)
+    for s0 in range(0, xs_all.size, 10 ** 7):
+        xs, us = xs_all[s0:s0 + 10 ** 7], us_all[s0:s0 + 10 ** 7]
+        e = orc.gather(f0["ez"], xs, np.float32)
+        x1, u1c = orc.push(xs, us, e, d["dt"], d["dz"], np.float32)
+        x1o[s0:s0 + xs.size], u1o[s0:s0 + xs.size] = x1, u1c
+        acc += orc.deposit_fractions(nz, xs, x1, np.float32, "fixed")
+    alive = (x1o >= 0) & (x1o < np.float32(nz))
+    assert st["last_removed"] == x1o.size - int(np.count_nonzero(alive))
+    # every push, bit for bit, in ID order
+    assert np.array_equal(xi1, x1o[alive]) and np.array_equal(u1, u1o[alive])
+    # the whole current grid, exactly (fixed-point sums do not depend on order)
+    j = orc.current_from(acc, d["s"], d["dt"], "fixed")
+    assert np.array_equal(f1["j"], j)
+    ez, er, b = orc.field_update(f0["ez"], f0["er"], f0["b"], j, d["dt"], d["dz"])
+    assert np.array_equal(f1["ez"], ez) and np.array_equal(f1["er"], er)
+    assert np.array_equal(f1["b"], b)
+    w0 = orc.base_weight_fixed(xi1, np.float32)
+    n_next, _ = orc.injection_count(ez[0], w0, d["s"], d["dz"], d["rho0"])
+    assert st["pending_injection"] == n_next
+    assert t.check() == 0
+    t.close()
