@@ -136,7 +136,7 @@ def build_tube(B, workloads, n, acc, order, seed):
     # frame-dragging ramp for the initial momenta: gamma_far = Lambda0^2 kappa cos i
     eta_scale = d["R_over_Rstar"]
     gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
-    z, u = synth.prefilled_beam(n, d["L"], gfar, seed=seed, order=order,
+    z, u = synth.prefilled_beam(n, d["L"] - d["dz"], gfar, seed=seed, order=order,
                                 eta_of_z=lambda zz: 1.0 + zz * eta_scale)
     return t, kw, d, z, u, gfar
 
@@ -187,7 +187,7 @@ def run_reference(args):
     dt = orc.default_dt(dz, cu["Lambda0"])
     s = orc.macro_charge_for(rho[0], L, n)
     gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(0.5)
-    z, u = synth.prefilled_beam(n // stride, L, gfar, seed=0, order=args.order,
+    z, u = synth.prefilled_beam(n // stride, L - dz, gfar, seed=0, order=args.order,
                                 eta_of_z=lambda zz: 1.0 + zz * cu["R_over_Rstar"])
     o = orc.Tube(nz, L, dt, rho, s * stride, precision="f32", accumulate="fixed")
     o.add_particles(z, u)

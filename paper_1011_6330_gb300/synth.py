@@ -42,7 +42,9 @@ def gamma_ramp(z, gamma_far, scale=1.0, eta_of_z=None):
 
 def prefilled_beam(n, L, gamma_far, seed, order="descending", jitter=0.01,
                    eta_of_z=None):
-    """(z, u) of n electrons spread uniformly over the tube with
+    """(z, u) of n electrons spread uniformly over [0, L) (pass the filled
+    height, e.g. the tube length less one cell, so that no height rounds to
+    the top of the tube in float32) with
     u = sqrt(gamma^2 - 1), gamma from :func:`gamma_ramp` with a relative
     Gaussian jitter (clipped at gamma >= 1)."""
     z = stratified_heights(n, L, seed, order)
