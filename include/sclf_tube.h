@@ -241,6 +241,40 @@ int tube_set_timing(tube_t t, int enable);
 /* Accumulated timings since timing was enabled. Synchronises. */
 int tube_get_timing(tube_t t, tube_timing* out);
 
+/* ---- one pass without any device allocation --------------------------------
+ * The paper has no counterpart to this call; it is here for users of the
+ * library who cannot call cudaMalloc: an application whose own allocator has
+ * reserved the device's memory, a plug-in whose host forbids allocation once
+ * it runs, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree. It allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).
+ *
+ * One gather-push-deposit pass over n FP32 particles, the same arithmetic
+ * as a tube step without injection: cloud-in-cell gather of E_z, the Eq. 1
+ * push, the charge-conserving current summed in 2^-32 fixed point, and
+ * removal of particles leaving the tube (their xi becomes -1, u 0).
+ *   xi, u     device, n floats each, in/out: positions in cell units
+ *             (xi = z / dz; entries with xi < 0 are holes and are skipped)
+ *             and u = gamma beta
+ *   ez        device, nz doubles: E_z at the cell centres (code units)
+ *   dt, dz    step and cell size in R/c and R (0 < dt < dz); s < 0 the
+ *             macro-particle charge
+ *   j_out     device, nz doubles, out: J_{j+1/2} = (s/dt) sum of fractions
+ *   n_removed device int64 or NULL, out: particles removed by this pass
+ *   stream    cudaStream_t; the call is asynchronous on it
+ * Its scratch is one fixed file-scope device array of SCLF_STATIC_MAX_NZ
+ * cells (about 1 MB), held by every GPU that loads the library until the
+ * process exits; nz > SCLF_STATIC_MAX_NZ returns SCLF_EINVAL. The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * Every call shares the array and clears it before use, so calls that
+ * overlap on the GPU (other streams, other host threads) race with one
+ * another: serialise them. */
+#define SCLF_STATIC_MAX_NZ 65536
+int tube_push_deposit_static(float* xi, float* u, int64_t n, const double* ez,
+                             int32_t nz, double dt, double dz, double s,
+                             double* j_out, int64_t* n_removed, void* stream);
+
 /* Human-readable name of a return code (static storage). */
 const char* tube_strerror(int code);
 

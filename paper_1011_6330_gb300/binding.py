@@ -86,6 +86,8 @@ SIGNATURES = {
     "tube_compact": (_i32, [_vp]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "tube_push_deposit_static": (_i32, [_vp, _vp, _i64, _vp, C.c_int32, C.c_double,
+                                         C.c_double, C.c_double, _vp, _vp, _vp]),
     "tube_strerror": (C.c_char_p, [_i32]),
     "tube_version": (C.c_char_p, []),
 }
