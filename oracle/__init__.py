@@ -10,6 +10,6 @@ from .sclf_oracle import (  # noqa: F401
     C_LIGHT, E_CHARGE, M_ELECTRON, G_NEWTON, M_SUN, FIXED_SCALE,
     RHO_FLAT, RHO_GR, code_units, rho_gj_profile, poisson_potential, initial_fields,
     base_weight_fixed, injection_count, macro_charge_for, default_dt,
-    gather, push, fractions, accumulate, deposit_fractions, current_from,
+    gather, push, fractions, quantized_fraction, fixed_fractions, accumulate, deposit_fractions, current_from,
     field_update, rho_nodes, Tube,
 )

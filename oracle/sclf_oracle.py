@@ -60,9 +60,11 @@ Modes of :class:`Tube`:
              rounding per operation and no fused multiply-add, gathering
              from a float32 copy of E_z. All grids stay FP64.
   accumulate 'sum': the per-cell sum of current fractions in FP64, in
-             particle order; 'fixed': each fraction is rounded to a
-             multiple of 2^-32 and the sum is exact in int64, so it does
-             not depend on the order of the particles.
+             particle order; 'fixed': each F_j(xi) is rounded to a multiple
+             of 2^-32 before the difference F_j(xi') - F_j(xi) is taken, and
+             the sum is exact in int64, so it does not depend on the order
+             of the particles and a particle's moved charge telescopes
+             exactly.
   deposit    'fast': evaluates F_j only for the <= 2 cells a particle can
              touch; 'brute': evaluates it for every (particle, cell) pair.
 """
@@ -254,13 +256,28 @@ def fractions(xi0, xi1, j, rt):
             - np.minimum(np.maximum(xi0 - jj, zero), one))
 
 
+def quantized_fraction(x, j, rt):
+    """F_j(x) = clamp(x - j, 0, 1) in the particle precision, rounded
+    half-even to a multiple of 2^-32 and returned in 2^-32 units (int64)."""
+    jj = np.asarray(j).astype(rt)
+    f = np.minimum(np.maximum(x - jj, rt(0.0)), rt(1.0))
+    return np.rint(f.astype(np.float64) * FIXED_SCALE).astype(np.int64)
+
+
+def fixed_fractions(xi0, xi1, j, rt):
+    """F_j(xi1) - F_j(xi0) with each F quantised to 2^-32 first
+    (:func:`quantized_fraction`); int64 in 2^-32 units. The differences of a
+    particle's quantised F telescope, so the charge it moves is conserved
+    exactly in integers."""
+    return quantized_fraction(xi1, j, rt) - quantized_fraction(xi0, j, rt)
+
+
 def accumulate(nz, cells, frac, mode):
-    """Per-cell sum of fractions: FP64 in the given order ('sum') or exact
-    int64 multiples of 2^-32 ('fixed', each term rounded half-even)."""
+    """Per-cell sum of fractions: FP64 in the given order ('sum'), or the
+    exact int64 sum of 2^-32-unit terms ('fixed', frac already int64)."""
     if mode == "fixed":
-        q = np.rint(np.asarray(frac, np.float64) * FIXED_SCALE).astype(np.int64)
         acc = np.zeros(nz, np.int64)
-        np.add.at(acc, cells, q)
+        np.add.at(acc, cells, np.asarray(frac, np.int64))
         return acc
     acc = np.zeros(nz, np.float64)
     np.add.at(acc, cells, np.asarray(frac, np.float64))
@@ -277,10 +294,11 @@ def deposit_fractions(nz, xi0, xi1, rt, mode="sum", brute=False):
     """
     xi0 = np.asarray(xi0, rt)
     xi1 = np.asarray(xi1, rt)
+    frac_of = fixed_fractions if mode == "fixed" else fractions
     if brute:
         j = np.arange(nz, dtype=np.int64)
         cells = np.broadcast_to(j[None, :], (xi0.size, nz)).ravel()
-        fr = fractions(xi0[:, None], xi1[:, None], j[None, :], rt).ravel()
+        fr = frac_of(xi0[:, None], xi1[:, None], j[None, :], rt).ravel()
         return accumulate(nz, cells, fr, mode)
     c0 = np.floor(xi0).astype(np.int64)
     c1 = np.floor(xi1).astype(np.int64)
@@ -289,7 +307,7 @@ def deposit_fractions(nz, xi0, xi1, rt, mode="sum", brute=False):
     x0 = np.concatenate([xi0, xi0[cross]])
     x1 = np.concatenate([xi1, xi1[cross]])
     inside = (cells >= 0) & (cells < nz)
-    fr = fractions(x0[inside], x1[inside], cells[inside], rt)
+    fr = frac_of(x0[inside], x1[inside], cells[inside], rt)
     return accumulate(nz, cells[inside], fr, mode)
 
 

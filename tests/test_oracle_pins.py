@@ -378,3 +378,28 @@ def test_gr_profile_reduces_to_flat_without_frame_dragging():
     assert np.allclose(g, -(9.0 / (4 * math.pi)) * (1 - 0.1654 / eta ** 3), rtol=1e-15)
     # |rho_GJ| grows with height under frame dragging (omega falls off as eta^-3)
     assert np.all(np.diff(np.abs(g)) > 0)
+
+
+def test_fixed_point_fractions_telescope_exactly():
+    """Quantised F_j makes a particle's deposited charge telescope: over many
+    steps the sum of its current fractions on a cell equals the difference of
+    the end-point fractions, exactly in integers."""
+    rng = np.random.default_rng(2)
+    for rt in (np.float32, np.float64):
+        x = rt(5.123)
+        total = np.zeros(12, np.int64)
+        start = x
+        for _ in range(400):
+            x1 = rt(x + rt(rng.uniform(-0.3, 0.3)))
+            x1 = rt(min(max(x1, rt(0.5)), rt(10.5)))
+            j = np.arange(12)
+            total += orc.fixed_fractions(np.full(12, x, rt), np.full(12, x1, rt), j, rt)
+            x = x1
+        j = np.arange(12)
+        want = (orc.quantized_fraction(np.full(12, x, rt), j, rt)
+                - orc.quantized_fraction(np.full(12, start, rt), j, rt))
+        assert np.array_equal(total, want)
+        # and each quantised fraction is within half a quantum of the exact one
+        f = orc.quantized_fraction(np.full(12, x, rt), j, rt) / orc.FIXED_SCALE
+        exact = np.clip(np.float64(x) - j, 0, 1)
+        assert np.max(np.abs(f - exact)) <= 0.5 / orc.FIXED_SCALE + 1e-300
