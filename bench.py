@@ -348,6 +348,8 @@ def main():
                      else "push_kernel<float, fp64>",
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
+                     "compact_ms_total": tm["compact_ms"],
+                     "compaction_checks": tm["n_compactions"],
                      "bytes_per_launch": BYTES_PER_PARTICLE * slots_per_launch},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -98,7 +98,10 @@ typedef struct tube_params {
                               by removals until the next compaction)          */
     int32_t accumulate;    /* SCLF_ACC_FIXED64 or SCLF_ACC_FP64               */
     int32_t track_ids;     /* 1: keep an int64 ID per particle                */
-    int32_t compact_interval; /* steps between compactions; 0 -> 64          */
+    int32_t compact_interval; /* steps between compaction checks; 0 -> 64.
+                              A check compacts only when holes exceed 1/64
+                              of the slots or would add a quarter to the
+                              free slots                                     */
     int32_t use_graphs;    /* 1: tube_run replays captured CUDA graphs        */
 } tube_params;
 
@@ -185,8 +188,9 @@ int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u);
 /* One time step (a1..a6 of Sec. 2, Figure A). Asynchronous. */
 int tube_step(tube_t t);
 
-/* nsteps time steps; replays captured CUDA graphs when use_graphs is set
- * and timing is off. Asynchronous. */
+/* nsteps time steps; replays captured CUDA graphs of compact_interval
+ * steps when use_graphs is set (with event nodes around every kernel while
+ * timing is on). Asynchronous. */
 int tube_run(tube_t t, int64_t nsteps);
 
 /* Copy fields to host arrays (any may be NULL): Ez, Bphi, J at the Nz cell
@@ -230,12 +234,14 @@ int tube_status(tube_t t, tube_stats* out);
 /* SCLF_OK, or the error code of the most severe sticky flag. Synchronises. */
 int tube_check(tube_t t);
 
-/* Compact the particle slots now (removes holes, keeps ID order). Async. */
+/* Compact the particle slots now, whatever the number of holes (removes
+ * holes, keeps ID order). Async. */
 int tube_compact(tube_t t);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing of steps; enabling
- * clears the accumulated numbers. While enabled, tube_run launches kernels
- * directly (no graph replay). */
+ * clears the accumulated numbers. Graph replays then carry event-record
+ * nodes around each kernel; reading them back waits for the replay two
+ * chunks earlier. */
 int tube_set_timing(tube_t t, int enable);
 
 /* Accumulated timings since timing was enabled. Synchronises. */

@@ -1,0 +1,127 @@
+// Small kernels around the step: appending particles, the base-cell weight,
+// the injection count after an append, the cloud-in-cell charge density for
+// diagnostics and the initial gather table.
+#include "device_common.cuh"
+
+namespace sclf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Small kernels: append, base weight, ρ diagnostics, gather table
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void append_kernel(DevState* st, Real* xi, Real* u, long long* ids,
+                              long long first, long long n, bool zero) {
+    const long long id0 = st->total_injected;
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (zero) { xi[first + k] = Real(0); u[first + k] = Real(0); }
+        if (ids) ids[first + k] = id0 + k;
+    }
+}
+
+template <class Real>
+__global__ void base_weight_kernel(DevState* st, const Real* xi, long long n) {
+    long long w = 0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const Real x = xi[i];
+        if (x >= Real(0) && x < Real(1)) w += to_fixed(Real(1) - x);
+    }
+    w = warp_sum(w);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
+}
+
+__global__ void finish_append_kernel(DevState* st, const double* ez, long long n_added,
+                                     FieldConsts c) {
+    st->n_slots += n_added;
+    st->n_live += n_added;
+    st->total_injected += n_added;
+    st->w0 = static_cast<long long>(st->acc_w0);
+    st->acc_w0 = 0;
+    long long n;
+    double es;
+    injection_count(ez[0], st->w0, c, &n, &es);
+    st->n_inj = n;
+    st->surface_field = es;
+}
+
+template <class Real>
+__global__ void rho_kernel(const Real* xi, long long n, double* acc, int nz) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double x = double(xi[i]);
+        if (!(x >= 0.0 && x < double(nz))) continue;
+        const double jf = floor(x);
+        const int j = static_cast<int>(jf);
+        const double w = x - jf;
+        atomicAdd(acc + j, 1.0 - w);
+        atomicAdd(acc + j + 1, w);
+    }
+}
+
+template <class Real>
+__global__ void ez_table_kernel(const double* ez, Real* ez2, int nz) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > nz) return;
+    const int lo = m - 1 < 0 ? 0 : m - 1;
+    const int hi = m > nz - 1 ? nz - 1 : m;
+    ez2[2 * m] = static_cast<Real>(ez[lo]);
+    ez2[2 * m + 1] = static_cast<Real>(ez[hi]);
+}
+
+int grid_for(long long n, int block, int cap) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    return static_cast<int>(g < cap ? g : cap);
+}
+
+}  // namespace
+
+template <class Real>
+cudaError_t launch_append(DevState* st, Real* xi, Real* u, long long* ids, long long first,
+                          long long n, bool zero_particles, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (!zero_particles && !ids) return cudaSuccess;
+    append_kernel<Real><<<grid_for(n, 256, 4096), 256, 0, s>>>(st, xi, u, ids, first, n,
+                                                               zero_particles);
+    return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots, cudaStream_t s) {
+    if (n_slots <= 0) return cudaSuccess;
+    base_weight_kernel<Real><<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(st, xi, n_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_append(DevState* st, const double* ez, long long n_added,
+                                 FieldConsts c, cudaStream_t s) {
+    finish_append_kernel<<<1, 1, 0, s>>>(st, ez, n_added, c);
+    return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s) {
+    ez_table_kernel<Real><<<(nz + 1 + 255) / 256, 256, 0, s>>>(ez, ez2, nz);
+    return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_rho(const Real* xi, long long n_slots, double* rho_acc, int nz,
+                       cudaStream_t s) {
+    if (n_slots <= 0) return cudaSuccess;
+    rho_kernel<Real><<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(xi, n_slots, rho_acc, nz);
+    return cudaGetLastError();
+}
+
+#define SCLF_INSTANTIATE(R)                                                                  \
+    template cudaError_t launch_append<R>(DevState*, R*, R*, long long*, long long,          \
+                                          long long, bool, cudaStream_t);                    \
+    template cudaError_t launch_base_weight<R>(DevState*, const R*, long long, cudaStream_t); \
+    template cudaError_t launch_ez_table<R>(const double*, R*, int, cudaStream_t);           \
+    template cudaError_t launch_rho<R>(const R*, long long, double*, int, cudaStream_t);
+SCLF_INSTANTIATE(float)
+SCLF_INSTANTIATE(double)
+#undef SCLF_INSTANTIATE
+}  // namespace sclf

@@ -13,7 +13,8 @@
 //
 // The arithmetic is the same as one pass of the tube step without injection:
 // cloud-in-cell gather of E_z, the Eq. 1 push (q/m = -1, c = 1), the
-// charge-conserving current deposit summed in 2^-32 fixed point, and removal
+// charge-conserving current deposit summed in 2^-32 fixed point (each F_j
+// quantised before differencing), and removal
 // of particles that leave [0, Nz) (their slot becomes a hole, xi = -1).
 #include <mutex>
 
@@ -72,8 +73,11 @@ __global__ void static_table(StaticScratch* sc, const double* ez, int nz) {
 
 __device__ __forceinline__ float clamp01f(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
 
-__device__ __forceinline__ long long fixed_of(float x) {
-    return __float2ll_rn(x * 4294967296.0f);
+// F = clamp(v, 0, 1) in 2^-32 units, rounded half-even (as in the tube step:
+// each F is quantised before the difference F_j(x1) - F_j(x0) is taken).
+__device__ __forceinline__ long long qfrac(float v) {
+    v = clamp01f(v);
+    return v >= 1.0f ? (1LL << 32) : static_cast<long long>(__float2uint_rn(v * 4294967296.0f));
 }
 
 __global__ void static_push(StaticScratch* sc, float* xi, float* u, long long n, int nz,
@@ -101,14 +105,12 @@ __global__ void static_push(StaticScratch* sc, float* xi, float* u, long long n,
         const int c1 = static_cast<int>(floorf(x1));
         {
             const float jf = static_cast<float>(c0);
-            const float d = clamp01f(x1 - jf) - clamp01f(x - jf);
-            const long long q = fixed_of(d);
+            const long long q = qfrac(x1 - jf) - qfrac(x - jf);
             if (q) atomicAdd(&sc->acc[c0], static_cast<unsigned long long>(q));
         }
         if (c1 != c0 && c1 >= 0 && c1 < nz) {
             const float jf = static_cast<float>(c1);
-            const float d = clamp01f(x1 - jf) - clamp01f(x - jf);
-            const long long q = fixed_of(d);
+            const long long q = qfrac(x1 - jf) - qfrac(x - jf);
             if (q) atomicAdd(&sc->acc[c1], static_cast<unsigned long long>(q));
         }
         if (x1 >= 0.0f && x1 < nzf) {

@@ -15,12 +15,12 @@ constexpr int kThreads = 256;
 template <class Real> struct Layout;
 template <> struct Layout<float> {
     static constexpr int kVec = 4;          // float4 loads
-    static constexpr int kPPT = 16;         // particles per thread
+    static constexpr int kPPT = 8;          // particles per thread
     static constexpr int kTile = kThreads * kPPT;
 };
 template <> struct Layout<double> {
     static constexpr int kVec = 2;          // double2 loads
-    static constexpr int kPPT = 8;
+    static constexpr int kPPT = 4;
     static constexpr int kTile = kThreads * kPPT;
 };
 constexpr int kMaxTile = kThreads * 16;
@@ -101,6 +101,7 @@ struct CompactArgs {
     long long* ids;
     unsigned long long* tile_state;  // one word per tile
     long long capacity;
+    int force;                       // 0: only when holes or capacity call for it
 };
 
 // Launchers (kernels.cu). All return cudaGetLastError() after the launch.

@@ -83,6 +83,14 @@ struct sclf_tube {
     cudaGraphExec_t chunk = nullptr;
     int chunk_steps = 0;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // timed graphs: two copies with their own events, replayed alternately so
+    // one can be read back while the other runs
+    struct TimedChunk {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev;   // 3 per step + 2 around the compaction
+        bool pending = false;
+    } tchunk[2];
+    int tnext = 0;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;       // pool, 3 per step, 2 per compaction
@@ -136,8 +144,9 @@ FieldArgs<Real> field_args(sclf_tube* t, int parity) {
 }
 
 template <class Real>
-CompactArgs<Real> compact_args(sclf_tube* t) {
+CompactArgs<Real> compact_args(sclf_tube* t, int force) {
     CompactArgs<Real> a;
+    a.force = force;
     a.st = t->st;
     a.xi = static_cast<Real*>(t->xi);
     a.u = static_cast<Real*>(t->u);
@@ -157,11 +166,15 @@ cudaError_t enqueue_field(sclf_tube* t, int parity, cudaStream_t s) {
     return fp64(t) ? launch_field<double>(field_args<double>(t, parity), t->p.accumulate, s)
                    : launch_field<float>(field_args<float>(t, parity), t->p.accumulate, s);
 }
-cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(&t->st->ticket, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    return fp64(t) ? launch_compact<double>(compact_args<double>(t), t->compact_grid, s)
-                   : launch_compact<float>(compact_args<float>(t), t->compact_grid, s);
+// The compaction follows a field kernel, whose commit resets the tile
+// ticket; a compaction outside the step sequence resets it first.
+cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s, int force) {
+    if (force) {
+        const cudaError_t e = cudaMemsetAsync(&t->st->ticket, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+    }
+    return fp64(t) ? launch_compact<double>(compact_args<double>(t, force), t->compact_grid, s)
+                   : launch_compact<float>(compact_args<float>(t, force), t->compact_grid, s);
 }
 
 int read_state(sclf_tube* t, DevState* h) {
@@ -206,11 +219,11 @@ int one_step(sclf_tube* t) {
             const int e0 = reserve_events(t, 2);
             if (e0 < 0) return SCLF_ECUDA;
             CK(cudaEventRecord(t->ev[e0], t->stream));
-            CK(enqueue_compact(t, t->stream));
+            CK(enqueue_compact(t, t->stream, 0));
             CK(cudaEventRecord(t->ev[e0 + 1], t->stream));
             t->recs.push_back({1, e0});
         } else {
-            CK(enqueue_compact(t, t->stream));
+            CK(enqueue_compact(t, t->stream, 0));
         }
         t->steps_since_compact = 0;
     }
@@ -218,32 +231,71 @@ int one_step(sclf_tube* t) {
 }
 
 // One captured graph = chunk_steps steps starting at even parity, then a
-// compaction (chunk_steps == compact interval, rounded up to even).
-int build_chunk(sclf_tube* t) {
-    if (t->chunk) return SCLF_OK;
+// compaction check (chunk_steps == compact interval, rounded up to even).
+// With ev != nullptr, event-record nodes bracket every kernel: ev[3k],
+// ev[3k+1], ev[3k+2] around step k's particle and field kernels and the last
+// two around the compaction.
+int capture_chunk(sclf_tube* t, cudaGraphExec_t* out, const std::vector<cudaEvent_t>* ev) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < t->chunk_steps && e == cudaSuccess; ++k) {
-        e = enqueue_push(t, t->gstream);
+    auto mark = [&](int i) {
+        if (ev && e == cudaSuccess)
+            e = cudaEventRecordWithFlags((*ev)[i], t->gstream, cudaEventRecordExternal);
+    };
+    const int n = t->chunk_steps;
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        mark(3 * k);
+        if (e == cudaSuccess) e = enqueue_push(t, t->gstream);
+        mark(3 * k + 1);
         if (e == cudaSuccess) e = enqueue_field(t, k & 1, t->gstream);
+        mark(3 * k + 2);
     }
-    if (e == cudaSuccess) e = enqueue_compact(t, t->gstream);
+    mark(3 * n);
+    if (e == cudaSuccess) e = enqueue_compact(t, t->gstream, 0);
+    mark(3 * n + 1);
     const cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
     CK(e2);
-    e = cudaGraphInstantiate(&t->chunk, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     CK(e);
     return SCLF_OK;
 }
 
-int launch_chunk(sclf_tube* t) {
+int build_chunk(sclf_tube* t) {
+    if (t->chunk) return SCLF_OK;
+    return capture_chunk(t, &t->chunk, nullptr);
+}
+
+// Add a replayed timed chunk's kernel times to the totals (waits for it).
+int collect_chunk(sclf_tube* t, int which) {
+    auto& c = t->tchunk[which];
+    if (!c.pending) return SCLF_OK;
+    const int n = t->chunk_steps;
+    CK(cudaEventSynchronize(c.ev[3 * n + 1]));
+    for (int k = 0; k < n; ++k) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, c.ev[3 * k], c.ev[3 * k + 1]));
+        CK(cudaEventElapsedTime(&b, c.ev[3 * k + 1], c.ev[3 * k + 2]));
+        t->acc.push_ms += a;
+        t->acc.field_ms += b;
+    }
+    float cm = 0.f;
+    CK(cudaEventElapsedTime(&cm, c.ev[3 * n], c.ev[3 * n + 1]));
+    t->acc.compact_ms += cm;
+    t->acc.n_compactions += 1;
+    t->acc.n_steps += n;
+    c.pending = false;
+    return SCLF_OK;
+}
+
+int launch_graph(sclf_tube* t, cudaGraphExec_t exec) {
     if (t->gstream != t->stream) {
         CK(cudaEventRecord(t->fork, t->stream));
         CK(cudaStreamWaitEvent(t->gstream, t->fork, 0));
     }
-    CK(cudaGraphLaunch(t->chunk, t->gstream));
+    CK(cudaGraphLaunch(exec, t->gstream));
     if (t->gstream != t->stream) {
         CK(cudaEventRecord(t->join, t->gstream));
         CK(cudaStreamWaitEvent(t->stream, t->join, 0));
@@ -253,7 +305,31 @@ int launch_chunk(sclf_tube* t) {
     return SCLF_OK;
 }
 
+int launch_timed_chunk(sclf_tube* t) {
+    const int w = t->tnext;
+    auto& c = t->tchunk[w];
+    int rc = collect_chunk(t, w);
+    if (rc) return rc;
+    if (!c.exec) {
+        c.ev.resize(3 * t->chunk_steps + 2, nullptr);
+        for (auto& e : c.ev) CK(cudaEventCreate(&e));
+        rc = capture_chunk(t, &c.exec, &c.ev);
+        if (rc) return rc;
+    }
+    rc = launch_graph(t, c.exec);
+    if (rc) return rc;
+    c.pending = true;
+    t->tnext ^= 1;
+    return SCLF_OK;
+}
+
+int launch_chunk(sclf_tube* t) { return launch_graph(t, t->chunk); }
+
 int drain_timing(sclf_tube* t) {
+    for (int w = 0; w < 2; ++w) {
+        const int rc = collect_chunk(t, w);
+        if (rc) return rc;
+    }
     CK(cudaStreamSynchronize(t->stream));
     for (const auto& r : t->recs) {
         float ms = 0.f;
@@ -459,6 +535,10 @@ int tube_destroy(tube_t t) {
     if (!t) return SCLF_EINVAL;
     if (t->stream || t->gstream) cudaStreamSynchronize(t->stream);
     if (t->chunk) cudaGraphExecDestroy(t->chunk);
+    for (auto& c : t->tchunk) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+        for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
+    }
     for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
     if (t->fork) cudaEventDestroy(t->fork);
     if (t->join) cudaEventDestroy(t->join);
@@ -519,11 +599,15 @@ int tube_step(tube_t t) {
 int tube_run(tube_t t, int64_t nsteps) {
     if (!t || nsteps < 0) return SCLF_EINVAL;
     while (nsteps > 0) {
-        if (t->p.use_graphs && !t->timing && (t->host_step & 1) == 0 &&
+        if (t->p.use_graphs && (t->host_step & 1) == 0 &&
             t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
-            int rc = build_chunk(t);
-            if (rc) return rc;
-            rc = launch_chunk(t);
+            int rc;
+            if (t->timing) {
+                rc = launch_timed_chunk(t);
+            } else {
+                rc = build_chunk(t);
+                if (!rc) rc = launch_chunk(t);
+            }
             if (rc) return rc;
             nsteps -= t->chunk_steps;
             continue;
@@ -695,7 +779,7 @@ int tube_check(tube_t t) {
 
 int tube_compact(tube_t t) {
     if (!t) return SCLF_EINVAL;
-    CK(enqueue_compact(t, t->stream));
+    CK(enqueue_compact(t, t->stream, 1));
     t->steps_since_compact = 0;
     return SCLF_OK;
 }
@@ -711,6 +795,7 @@ int tube_set_timing(tube_t t, int enable) {
         CK(cudaStreamSynchronize(t->stream));
         t->recs.clear();
         t->ev_next = 0;
+        for (auto& c : t->tchunk) c.pending = false;   // discard an earlier session
         std::memset(&t->acc, 0, sizeof(t->acc));
         DevState h;
         const int rc = read_state(t, &h);

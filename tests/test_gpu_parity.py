@@ -137,16 +137,25 @@ def test_fp32_error_against_fp64_oracle_is_stated(gpu_lib):
 
 def test_ragged_tiles_compaction_schedule_and_graphs_do_not_change_results(gpu_lib):
     """Prefilled particles spanning several tiles with a ragged tail; the same
-    run with compaction every 3 steps, every 1000 steps, and with CUDA graphs,
-    is bit-identical (fixed-point current), and matches the oracle."""
+    run with forced compactions every 7 steps, with compaction checks every
+    1000 steps, and with CUDA graphs, is bit-identical (fixed-point current),
+    and matches the oracle."""
     kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
     z, u = synth.random_particles(4096 * 3 + 1234, kw["L_over_R"], seed=7, u_sigma=2.0)
     runs = []
-    for ci, graphs in ((3, 0), (1000, 0), (4, 1)):
+    for ci, graphs, forced in ((3, 0, True), (1000, 0, False), (4, 1, False)):
         t, o = pair(gpu_lib, dict(kw, compact_interval=ci, use_graphs=graphs), "f32", "fixed")
         t.add_particles(z, u)
         o.add_particles(z, u)
-        t.run(101)
+        if forced:                       # compact every 7 steps whatever the holes
+            for n in range(101):
+                t.step()
+                if n % 7 == 6:
+                    t.compact()
+                    st = t.status()
+                    assert st["n_slots"] == st["n_particles"]
+        else:
+            t.run(101)
         o.run(101)
         compare(t, o, TOL[B.SCLF_FP32], "compact %d graphs %d" % (ci, graphs))
         runs.append((t.read_particles(), t.read_fields(rho=False)))
