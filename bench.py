@@ -60,6 +60,26 @@ def dist_env():
     return ws, rank, local
 
 
+def combine_ranks(work, seconds, device="cpu"):
+    """Whole-job throughput of independent per-rank runs: the work of all
+    ranks over the slowest rank's time (returns work_total, seconds_max).
+    Single process: the inputs unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(work), float(seconds)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(w.item()), float(t.item())
+
+
+def rank_seed(rank, base=0):
+    """Seed of a rank's independent tube (distinct per rank)."""
+    return base + 1000003 * rank
+
+
 def kernel_sha():
     with open(KERNEL_SRC, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -233,7 +253,7 @@ def main():
     B.load()
     acc = B.SCLF_ACC_FIXED64 if args.accumulate == "fixed64" else B.SCLF_ACC_FP64
     n = int(args.particles)
-    t, kw, d, z, u, gfar = build_tube(B, workloads, n, acc, args.order, seed=rank)
+    t, kw, d, z, u, gfar = build_tube(B, workloads, n, acc, args.order, seed=rank_seed(rank))
     t.add_particles(z, u)
     t.solve_fields()
     stream = torch.cuda.current_stream()
@@ -264,12 +284,10 @@ def main():
     tm = t.timing()
     t.set_timing(False)
     st1 = t.status()
-    if ws > 1:
-        x = torch.tensor([el_ms], device="cuda")
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(x.item())
     psteps_local = 0.5 * (st0["n_particles"] + st1["n_particles"]) * args.steps
-    value = psteps_local * ws / (el_ms * 1e-3)
+    psteps, el_s = combine_ranks(psteps_local, el_ms * 1e-3, device="cuda")
+    el_ms = el_s * 1e3
+    value = psteps / el_s
 
     # roofline of the dominant kernel (the particle kernel)
     push_avg_ms = tm["push_ms"] / max(tm["n_steps"], 1)
@@ -316,12 +334,9 @@ def main():
                                      C.c_void_p(out_u.data_ptr()), None)
         torch.cuda.synchronize()
         el_e2e = time.perf_counter() - h0
-        if ws > 1:
-            x = torch.tensor([el_e2e], device="cuda")
-            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-            el_e2e = float(x.item())
+        n_all, el_e2e = combine_ranks(n_e2e, el_e2e, device="cuda")
         state_bytes = 8 * pin_x.numel()
-        e2e = {"value": n_e2e * ws / el_e2e, "unit": UNIT,
+        e2e = {"value": n_all / el_e2e, "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / ksteps,
                "d2h_bytes_per_step": (8 * min(cap, nout.value) + ksteps * 88) / ksteps,
                "path": "tube_load_particles(pinned) + K x (tube_status, tube_step) + "
