@@ -11,5 +11,6 @@ from .sclf_oracle import (  # noqa: F401
     RHO_FLAT, RHO_GR, code_units, rho_gj_profile, poisson_potential, initial_fields,
     base_weight_fixed, injection_count, macro_charge_for, default_dt,
     gather, push, fractions, quantized_fraction, fixed_fractions, accumulate, deposit_fractions, current_from,
-    field_update, rho_nodes, Tube,
+    field_update, rho_nodes, fix32_bits, gather_fix32, push_fix32, fix32_fractions,
+    deposit_fix32, base_weight_fix32, Tube,
 )

@@ -55,10 +55,14 @@ readings this oracle fixes):
     E_r at node 0 is 0 (phi = 0 on the conducting surface).
 
 Modes of :class:`Tube`:
-  precision  'f64' (default) or 'f32'. In 'f32' the particle arithmetic
-             (xi, u, weights, current fractions) is IEEE float32 with one
-             rounding per operation and no fused multiply-add, gathering
-             from a float32 copy of E_z. All grids stay FP64.
+  precision  'f64' (default), 'f32' or 'fix32'. In 'f32' the particle
+             arithmetic (xi, u, weights, current fractions) is IEEE float32
+             with one rounding per operation and no fused multiply-add,
+             gathering from a float32 copy of E_z. In 'fix32' positions are
+             integers X = xi * 2^fb (fb = 31 - ceil(log2 Nz) fractional bits,
+             uniform resolution along the tube), u and the push are float32 as
+             in 'f32', the displacement is rounded to the 2^-fb grid and the
+             current fractions are exact integers. All grids stay FP64.
   accumulate 'sum': the per-cell sum of current fractions in FP64, in
              particle order; 'fixed': each F_j(xi) is rounded to a multiple
              of 2^-32 before the difference F_j(xi') - F_j(xi) is taken, and
@@ -272,6 +276,79 @@ def fixed_fractions(xi0, xi1, j, rt):
     return quantized_fraction(xi1, j, rt) - quantized_fraction(xi0, j, rt)
 
 
+def fix32_bits(nz):
+    """Fractional bits of the 'fix32' position: the largest fb with
+    Nz * 2^fb <= 2^31 (a sign bit stays free)."""
+    return 31 - int(math.ceil(math.log2(nz)))
+
+
+def gather_fix32(ez, X, fb):
+    """(a2) on fixed-point positions X = xi 2^fb: h = X + 2^(fb-1),
+    m = h >> fb, f = float32((h mod 2^fb) 2^-fb), then as :func:`gather`."""
+    nz = ez.size
+    e = np.asarray(ez, np.float64).astype(np.float32)
+    X = np.asarray(X, np.int64)
+    h = X + (1 << (fb - 1))
+    m = h >> fb
+    f = (h & ((1 << fb) - 1)).astype(np.float32) * np.float32(2.0 ** -fb)
+    ia = np.clip(m - 1, 0, nz - 1)
+    ib = np.clip(m, 0, nz - 1)
+    return (np.float32(1.0) - f) * e[ia] + f * e[ib]
+
+
+def push_fix32(X, u, ep, dt, dz, fb):
+    """(a3) in 'fix32': the float32 push of :func:`push`, then the
+    displacement d = (u'/gamma)(dt/dz) rounded half-even to the 2^-fb grid.
+    Returns (X', u', finite) with finite = isfinite(d); X' is meaningful
+    only where finite."""
+    f32 = np.float32
+    u1 = u - ep * f32(dt)
+    gam = np.sqrt(f32(1.0) + u1 * u1)
+    d = (u1 / gam) * f32(dt / dz)
+    finite = np.isfinite(d)
+    inc = np.rint(np.where(finite, d, f32(0.0)).astype(np.float64) * 2.0 ** fb)
+    return np.asarray(X, np.int64) + inc.astype(np.int64), u1, finite
+
+
+def fix32_fractions(X0, X1, j, fb):
+    """F_j(X1) - F_j(X0) in 2^-32 units, exact: F_j(X) =
+    clamp(X - j 2^fb, 0, 2^fb) 2^(32 - fb)."""
+    one = np.int64(1) << fb
+    jj = np.asarray(j, np.int64) << fb
+    f1 = np.minimum(np.maximum(np.asarray(X1, np.int64) - jj, 0), one)
+    f0 = np.minimum(np.maximum(np.asarray(X0, np.int64) - jj, 0), one)
+    return (f1 - f0) << (32 - fb)
+
+
+def deposit_fix32(nz, X0, X1, fb, brute=False):
+    """(a4) in 'fix32' (int64 sums in 2^-32 units); cells floor(X0 / 2^fb)
+    and floor(X1 / 2^fb), or all cells with brute=True."""
+    X0 = np.asarray(X0, np.int64)
+    X1 = np.asarray(X1, np.int64)
+    if brute:
+        j = np.arange(nz, dtype=np.int64)
+        cells = np.broadcast_to(j[None, :], (X0.size, nz)).ravel()
+        fr = fix32_fractions(X0[:, None], X1[:, None], j[None, :], fb).ravel()
+        return accumulate(nz, cells, fr, "fixed")
+    c0 = X0 >> fb
+    c1 = X1 >> fb
+    cross = c1 != c0
+    cells = np.concatenate([c0, c1[cross]])
+    x0 = np.concatenate([X0, X0[cross]])
+    x1 = np.concatenate([X1, X1[cross]])
+    inside = (cells >= 0) & (cells < nz)
+    fr = fix32_fractions(x0[inside], x1[inside], cells[inside], fb)
+    return accumulate(nz, cells[inside], fr, "fixed")
+
+
+def base_weight_fix32(X, fb):
+    """W_0 in 2^-32 units for fixed-point positions: sum over the base cell
+    of (2^fb - X) 2^(32 - fb)."""
+    X = np.asarray(X, np.int64)
+    X = X[(X >= 0) & (X < (1 << fb))]
+    return int((((1 << fb) - X) << (32 - fb)).sum())
+
+
 def accumulate(nz, cells, frac, mode):
     """Per-cell sum of fractions: FP64 in the given order ('sum'), or the
     exact int64 sum of 2^-32-unit terms ('fixed', frac already int64)."""
@@ -366,8 +443,10 @@ class Tube:
 
     def __init__(self, nz, L, dt, rho_gj, s, *, capacity=None,
                  precision="f64", accumulate="sum", deposit="fast"):
-        if precision not in ("f64", "f32"):
+        if precision not in ("f64", "f32", "fix32"):
             raise ValueError(precision)
+        if precision == "fix32" and accumulate != "fixed":
+            raise ValueError("'fix32' positions deposit exact fixed-point fractions")
         if accumulate not in ("sum", "fixed"):
             raise ValueError(accumulate)
         if deposit not in ("fast", "brute"):
@@ -388,11 +467,13 @@ class Tube:
         self.precision = precision
         self.accumulate = accumulate
         self.brute = deposit == "brute"
-        self.rt = np.float32 if precision == "f32" else np.float64
+        self.rt = np.float64 if precision == "f64" else np.float32
+        self.fix = precision == "fix32"
+        self.fb = fix32_bits(self.nz) if self.fix else 0
 
         self.ez, self.er, self.b, self.phi0 = initial_fields(self.rho_gj, self.dz)
         self.j = np.zeros(self.nz)          # J^{n+1/2} of the last step
-        self.xi = np.zeros(0, self.rt)
+        self.xi = np.zeros(0, np.int64 if self.fix else self.rt)   # X in 'fix32'
         self.u = np.zeros(0, self.rt)
         self.ids = np.zeros(0, np.int64)
         self.w0 = 0                         # W_0 in 2^-32 units
@@ -409,7 +490,10 @@ class Tube:
         """Append particles at heights z (in R) with u = gamma beta;
         xi = z / dz is computed in FP64 and rounded to the precision."""
         z = np.asarray(z, np.float64)
-        xi = (z / self.dz).astype(self.rt)
+        if self.fix:
+            xi = np.rint(z / self.dz * 2.0 ** self.fb).astype(np.int64)
+        else:
+            xi = (z / self.dz).astype(self.rt)
         uu = np.asarray(u, np.float64).astype(self.rt)
         n = xi.size
         self.xi = np.concatenate([self.xi, xi])
@@ -417,7 +501,12 @@ class Tube:
         self.ids = np.concatenate(
             [self.ids, self.total_injected + np.arange(n, dtype=np.int64)])
         self.total_injected += n
-        self.w0 = base_weight_fixed(self.xi, self.rt)
+        self.w0 = self._base_weight()
+
+    def _base_weight(self):
+        if self.fix:
+            return base_weight_fix32(self.xi, self.fb)
+        return base_weight_fixed(self.xi, self.rt)
 
     def solve_fields(self):
         """Eq. 4 with the tube's current charge: phi'' - phi = -4 pi (rho - rho_GJ)
@@ -443,7 +532,7 @@ class Tube:
         if self.capacity is not None and self.xi.size + n_inj > self.capacity:
             n_inj = max(0, self.capacity - self.xi.size)
             self.capacity_hit = True
-        self.xi = np.concatenate([self.xi, np.zeros(n_inj, self.rt)])
+        self.xi = np.concatenate([self.xi, np.zeros(n_inj, self.xi.dtype)])
         self.u = np.concatenate([self.u, np.zeros(n_inj, self.rt)])
         self.ids = np.concatenate(
             [self.ids, self.total_injected + np.arange(n_inj, dtype=np.int64)])
@@ -458,18 +547,30 @@ class Tube:
         rt = self.rt
         self.inject()                                              # (a1)
         xi0, u0 = self.xi, self.u
-        ep = gather(self.ez, xi0, rt)                              # (a2)
-        xi1, u1 = push(xi0, u0, ep, self.dt, self.dz, rt)          # (a3)
-        acc = deposit_fractions(self.nz, xi0, xi1, rt,             # (a4)
-                                self.accumulate, self.brute)
-        self.j = current_from(acc, self.s, self.dt, self.accumulate)
-        finite = np.isfinite(xi1) & np.isfinite(u1)
-        if not np.all(finite):
-            self.nonfinite = True
-        alive = finite & (xi1 >= 0) & (xi1 < rt(self.nz))          # (a5)
-        self.last_removed = int(xi1.size - np.count_nonzero(alive))
+        if self.fix:
+            fb = self.fb
+            ep = gather_fix32(self.ez, xi0, fb)                    # (a2)
+            xi1, u1, finite = push_fix32(xi0, u0, ep, self.dt, self.dz, fb)   # (a3)
+            if not np.all(finite):
+                self.nonfinite = True
+            acc = deposit_fix32(self.nz, xi0[finite], xi1[finite], fb,         # (a4)
+                                self.brute)
+            self.j = current_from(acc, self.s, self.dt, "fixed")
+            alive = finite & (xi1 >= 0) & (xi1 < (self.nz << fb))  # (a5)
+            self.last_removed = int(xi1.size - np.count_nonzero(alive))
+        else:
+            ep = gather(self.ez, xi0, rt)                          # (a2)
+            xi1, u1 = push(xi0, u0, ep, self.dt, self.dz, rt)      # (a3)
+            acc = deposit_fractions(self.nz, xi0, xi1, rt,         # (a4)
+                                    self.accumulate, self.brute)
+            self.j = current_from(acc, self.s, self.dt, self.accumulate)
+            finite = np.isfinite(xi1) & np.isfinite(u1)
+            if not np.all(finite):
+                self.nonfinite = True
+            alive = finite & (xi1 >= 0) & (xi1 < rt(self.nz))      # (a5)
+            self.last_removed = int(xi1.size - np.count_nonzero(alive))
         self.xi, self.u, self.ids = xi1[alive], u1[alive], self.ids[alive]
-        self.w0 = base_weight_fixed(self.xi, rt)
+        self.w0 = self._base_weight()
         self.ez, self.er, self.b = field_update(                   # (a6)
             self.ez, self.er, self.b, self.j, self.dt, self.dz)
         self.step_count += 1
@@ -479,16 +580,22 @@ class Tube:
             self.step()
 
     # -- diagnostics -----------------------------------------------------------
+    def cells(self):
+        """Particle positions in cell units (FP64)."""
+        if self.fix:
+            return self.xi.astype(np.float64) * 2.0 ** -self.fb
+        return self.xi.astype(np.float64)
+
     def z(self):
         """Particle heights in R (FP64)."""
-        return self.xi.astype(np.float64) * self.dz
+        return self.cells() * self.dz
 
     def gamma(self):
         u = self.u.astype(np.float64)
         return np.sqrt(1.0 + u * u)
 
     def rho_nodes(self):
-        return rho_nodes(self.xi, self.s, self.dz, self.nz)
+        return rho_nodes(self.cells(), self.s, self.dz, self.nz)
 
     def gauss_residual(self):
         """G_j = (E_{j+1/2} - E_{j-1/2})/dz + E_r,j - 4 pi (rho_j - rho_GJ,j)

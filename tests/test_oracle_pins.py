@@ -403,3 +403,70 @@ def test_fixed_point_fractions_telescope_exactly():
         f = orc.quantized_fraction(np.full(12, x, rt), j, rt) / orc.FIXED_SCALE
         exact = np.clip(np.float64(x) - j, 0, 1)
         assert np.max(np.abs(f - exact)) <= 0.5 / orc.FIXED_SCALE + 1e-300
+
+
+# ---------------------------------------------------------------------------
+# 'fix32' positions (32-bit fixed point, float32 momenta)
+# ---------------------------------------------------------------------------
+
+def test_fix32_resolution_and_range():
+    assert orc.fix32_bits(1024) == 21 and orc.fix32_bits(65536) == 15
+    assert orc.fix32_bits(2 ** 20) == 11 and orc.fix32_bits(1000) == 21
+    for nz in (2, 3, 1024, 65536, 2 ** 20, 2 ** 24):
+        assert nz << orc.fix32_bits(nz) <= 2 ** 31
+
+
+def test_fix32_gather_matches_exact_positions():
+    """The integer split h = X + 2^(fb-1), m = h >> fb is floor(xi + 1/2)."""
+    nz = 40
+    fb = orc.fix32_bits(nz)
+    rng = np.random.default_rng(4)
+    X = rng.integers(0, nz << fb, 5000)
+    zc = (np.arange(nz) + 0.5)
+    ez = 3.0 - 0.25 * zc
+    ep = orc.gather_fix32(ez, X, fb)
+    xi = X * 2.0 ** -fb
+    want = np.where(xi < 0.5, ez[0], np.where(xi > nz - 0.5, ez[-1], 3.0 - 0.25 * xi))
+    assert np.max(np.abs(ep - want)) < 2e-6
+
+
+def test_fix32_continuity_is_exact_in_integers():
+    """rho^{n+1} - rho^n + dt div J = 0 exactly, in 2^-32 charge units."""
+    rng = np.random.default_rng(9)
+    nz = 30
+    fb = orc.fix32_bits(nz)
+    X0 = rng.integers(0, nz << fb, 4000)
+    X1 = X0 + rng.integers(-(1 << fb) + 1, 1 << fb, X0.size)
+    acc = orc.deposit_fix32(nz, X0, X1, fb)
+    # node charges in 2^-32 units: W_j(X) = F_{j-1}(X) - F_j(X)
+    def node_q(X):
+        j = np.arange(nz + 1)
+        keep = (X >= 0) & (X < nz << fb)
+        X = X[keep][:, None]
+        return (orc.fix32_fractions(np.zeros_like(X), X, j[None, :] - 1, fb)
+                - orc.fix32_fractions(np.zeros_like(X), X, j[None, :], fb)).sum(0)
+    q0, q1 = node_q(X0), node_q(X1)
+    div = np.zeros(nz + 1, np.int64)
+    div[1:nz] = acc[1:] - acc[:-1]
+    assert np.array_equal((q1 - q0)[1:nz] + div[1:nz], np.zeros(nz - 1, np.int64))
+
+
+def test_fix32_tube_tracks_the_fp64_definition_and_brute_force():
+    """Whole steps in 'fix32' stay within the 2^-fb position grid of the FP64
+    oracle over 200 steps, and equal the all-pairs deposit exactly."""
+    nz, L = 256, 4.0
+    dz = L / nz
+    rho = -np.ones(nz + 1)
+    s = orc.macro_charge_for(-1.0, L, 4000)
+    a = orc.Tube(nz, L, 0.4 * dz, rho, s, precision="fix32", accumulate="fixed")
+    b = orc.Tube(nz, L, 0.4 * dz, rho, s, precision="fix32", accumulate="fixed",
+                 deposit="brute")
+    c = orc.Tube(nz, L, 0.4 * dz, rho, s)
+    for _ in range(200):
+        a.step(); b.step(); c.step()
+        assert np.array_equal(a.xi, b.xi) and np.array_equal(a.ez, b.ez)
+    assert a.total_injected == c.total_injected
+    assert np.array_equal(a.ids, c.ids)
+    assert np.max(np.abs(a.cells() - c.cells())) < 1e-3
+    assert np.max(np.abs(a.ez - c.ez)) < 1e-4 * np.max(np.abs(c.ez))
+    assert np.max(np.abs(a.gauss_residual())) < 1e-9
