@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (gather+push+deposit), % HBM roofline; batched/adjoint vs plain"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 16          # FP32 xi and u, read once and written once per step
-KERNEL_SRC = os.path.join(ROOT, "paper_1011_6330_gb300", "csrc", "kernels.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_1011_6330_gb300", "csrc", f)
+              for f in ("push.cu", "device_common.cuh", "sclf_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
 
 
@@ -44,7 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--particles", type=float, default=1e8)
+    ap.add_argument("--workload", choices=["gr1e8", "large"], default="gr1e8",
+                    help="gr1e8: P = 0.5 s frame-dragging tube, Nz = 65536, FP32 particles "
+                         "(default); large: P = 0.1 s, B = 3e12 G, Nz = 2^20, 2^30 "
+                         "fixed-point particles")
+    ap.add_argument("--particles", type=float, default=None)
     ap.add_argument("--order", choices=["descending", "shuffled"], default="descending")
     ap.add_argument("--accumulate", choices=["fixed64", "fp64"], default="fixed64")
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,8 +86,12 @@ def rank_seed(rank, base=0):
 
 
 def kernel_sha():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the particle kernel's sources (ties a traffic capture to them)."""
+    h = hashlib.sha256()
+    for p in KERNEL_SRC:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -148,31 +157,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_tube(B, workloads, n, acc, order, seed):
+def build_tube(B, workloads, workload, n, acc, order, seed):
+    """Create the workload's tube and fill it with its seeded synthetic state.
+    Returns (tube, params, derived, sample_z, sample_u, stride): every
+    stride-th particle of the state, for the CPU baseline."""
     from paper_1011_6330_gb300 import synth
-    kw = workloads.gr_tube(n_particles=n, accumulate=acc)
+    if workload == "large":
+        kw = workloads.large_tube(n_particles=n)
+    else:
+        kw = workloads.gr_tube(n_particles=n, accumulate=acc)
     t = B.Tube(B.default_params(**kw))
     d = t.derived
     # frame-dragging ramp for the initial momenta: gamma_far = Lambda0^2 kappa cos i
     eta_scale = d["R_over_Rstar"]
     gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
+    eta = lambda zz: 1.0 + zz * eta_scale
+    stride = 100 if n <= 2 * 10 ** 8 else 1024
+    if order == "descending" and n > 2 * 10 ** 8:
+        zs, us = [], []
+        for z, u in synth.prefilled_beam_chunks(n, d["L"] - d["dz"], gfar, seed=seed,
+                                                chunk=1 << 26, eta_of_z=eta):
+            t.add_particles(z, u)
+            zs.append(z[::stride])
+            us.append(u[::stride])
+        return t, kw, d, np.concatenate(zs), np.concatenate(us), stride
     z, u = synth.prefilled_beam(n, d["L"] - d["dz"], gfar, seed=seed, order=order,
-                                eta_of_z=lambda zz: 1.0 + zz * eta_scale)
-    return t, kw, d, z, u, gfar
+                                eta_of_z=eta)
+    t.add_particles(z, u)
+    return t, kw, d, z[::stride], u[::stride], stride
 
 
-def cpu_baseline(z, u, kw, d, seconds, stride=100):
+def cpu_baseline(zs, us, n_total, kw, d, seconds, stride):
     """The oracle as it stands on a bounded sample: every stride-th particle
-    of the same prefilled state (macro charge times stride), FP32 particles
-    with the fixed-point current, the full Nz grid; stepped for ~seconds."""
+    of the same prefilled state (macro charge times stride), the workload's
+    particle precision with the fixed-point current, the full Nz grid;
+    stepped for ~seconds."""
     import oracle as orc
     cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
     nz = kw["Nz"]
     zn = np.arange(nz + 1) * (d["L"] / nz)
     rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
                              cu["R_over_Rstar"], cu["kappa"])
-    o = orc.Tube(nz, d["L"], d["dt"], rho, d["s"] * stride, precision="f32", accumulate="fixed")
-    o.add_particles(z[::stride], u[::stride])
+    prec = "fix32" if kw["precision"] == 2 else "f32"
+    o = orc.Tube(nz, d["L"], d["dt"], rho, d["s"] * stride, precision=prec, accumulate="fixed")
+    o.add_particles(zs, us)
     o.solve_fields()
     o.step()                                   # warm-up
     t0 = time.perf_counter()
@@ -185,8 +213,8 @@ def cpu_baseline(z, u, kw, d, seconds, stride=100):
     el = time.perf_counter() - t0
     return {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of the %d particles (every %dth, macro charge x%d), Nz=%d, "
-                      "FP32 particles + fixed-point current, %d steps in %.1f s"
-                      % (z[::stride].size, z.size, stride, stride, nz, steps, el)}
+                      "%s particles + fixed-point current, %d steps in %.1f s"
+                      % (zs.size, n_total, stride, stride, nz, prec, steps, el)}
 
 
 def run_reference(args):
@@ -195,7 +223,7 @@ def run_reference(args):
         return 0
     from paper_1011_6330_gb300 import synth
     import oracle as orc
-    n = int(args.particles)
+    n = int(args.particles or 1e8)
     stride = 100
     cu = orc.code_units(1e12, 0.5, 1e6, 0.5, 1.4 * 1.98847e33)
     L = 2.0 / cu["theta_p"]
@@ -252,9 +280,10 @@ def main():
     from paper_1011_6330_gb300 import workloads
     B.load()
     acc = B.SCLF_ACC_FIXED64 if args.accumulate == "fixed64" else B.SCLF_ACC_FP64
-    n = int(args.particles)
-    t, kw, d, z, u, gfar = build_tube(B, workloads, n, acc, args.order, seed=rank_seed(rank))
-    t.add_particles(z, u)
+    large = args.workload == "large"
+    n = int(args.particles or (2 ** 30 if large else 1e8))
+    t, kw, d, zs, us, stride = build_tube(B, workloads, args.workload, n, acc, args.order,
+                                          seed=rank_seed(rank))
     t.solve_fields()
     stream = torch.cuda.current_stream()
 
@@ -298,15 +327,16 @@ def main():
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        if tr.get("kernel_sha") == kernel_sha() and tr.get("accumulate") == args.accumulate \
-                and tr.get("order", "descending") == args.order:
-            traffic = tr["bytes_per_launch_full"]
+        ent = tr.get(args.workload, {})
+        if ent.get("kernel_sha") == kernel_sha() and ent.get("accumulate") == args.accumulate \
+                and ent.get("order", "descending") == args.order and ent.get("particles") == n:
+            traffic = ent["bytes_per_launch"]
     gpu_launches = 2 * tm["n_steps"] + tm["n_compactions"]
     check = t.check()
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not large:
         xi_h, u_h, _ = t.save_particles()
         pin_x = torch.empty(xi_h.size, dtype=torch.float32, pin_memory=True)
         pin_u = torch.empty(u_h.size, dtype=torch.float32, pin_memory=True)
@@ -344,13 +374,15 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(z, u, kw, d, args.cpu_seconds)
+        cpu = cpu_baseline(zs, us, n, kw, d, args.cpu_seconds, stride)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "gr_tube_P0.5s_B1e12G_Nz65536_%g_particles_fp32" % n,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fix32+f32" if large else "f32",
+        "data": "synthetic",
+        "config": {"workload": ("large_tube_P0.1s_B3e12G_Nz%d_%d_particles_fix32" % (kw["Nz"], n))
+                   if large else "gr_tube_P0.5s_B1e12G_Nz65536_%g_particles_fp32" % n,
                    "rho_gj": "frame-dragging (Eq. 6-7), i = 0.5 rad",
                    "particles_per_gpu": n, "Nz": kw["Nz"], "Lambda0": d["Lambda0"],
                    "dt_R_over_c": d["dt"], "order": args.order,
@@ -359,8 +391,9 @@ def main():
                    "parallelism": "independent tube per GPU" if ws > 1 else "single tube"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "push_kernel<float, fixed64>" if acc == B.SCLF_ACC_FIXED64
-                     else "push_kernel<float, fp64>",
+                     "kernel": "push_fix32_kernel" if large else
+                     ("push_kernel<float, fixed64>" if acc == B.SCLF_ACC_FIXED64
+                      else "push_kernel<float, fp64>"),
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],

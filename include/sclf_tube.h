@@ -59,6 +59,11 @@ extern "C" {
 
 #define SCLF_FP32 0          /* particle arithmetic in IEEE float32           */
 #define SCLF_FP64 1          /* particle arithmetic in IEEE float64           */
+#define SCLF_FIX32 2         /* int32 fixed-point positions X = xi 2^fb with
+                                fb = 31 - ceil(log2 Nz) (uniform resolution
+                                along the tube), float32 momenta and push, the
+                                displacement rounded half-even to 2^-fb cell;
+                                requires SCLF_ACC_FIXED64                      */
 
 #define SCLF_ACC_FIXED64 0   /* current fractions summed exactly in int64
                                 multiples of 2^-32 (order independent)        */
@@ -84,7 +89,8 @@ typedef struct tube_params {
     double dt;             /* time step in R/c; <= 0 -> min(0.4 dz, 0.2/Lambda0);
                               must satisfy 0 < dt < dz                        */
     int32_t rho_gj_mode;   /* SCLF_RHO_*                                      */
-    int32_t precision;     /* SCLF_FP32 or SCLF_FP64 (grids are always FP64)  */
+    int32_t precision;     /* SCLF_FP32, SCLF_FP64 or SCLF_FIX32 (grids are
+                              always FP64)                                   */
     const double* rho_gj_user; /* host, Nz+1 node values in code units, read
                                   by tube_create when mode is SCLF_RHO_USER   */
     double lambda_override;/* > 0: use this Lambda0 = omega_p0 R / c instead of
@@ -121,6 +127,8 @@ typedef struct tube_derived {
     double dt;             /* time step in R/c                                */
     double s;              /* macro-particle charge (< 0)                     */
     double rho0;           /* rho_GJ at node 0, code units                    */
+    double pos_unit;       /* cells per stored position unit: 2^-fb for
+                              SCLF_FIX32, 1 otherwise                        */
 } tube_derived;
 
 /* Per-tube counters, read back by tube_status (synchronises the stream). */
@@ -206,10 +214,11 @@ int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi,
 int tube_read_particles(tube_t t, int64_t cap, int64_t* n, double* z,
                         double* u, int64_t* id);
 
-/* Raw particle state in the tube's precision: xi = z / dz (cell units) and
- * u as float (SCLF_FP32) or double (SCLF_FP64), live particles only, ID
- * order. Host buffers of capacity cap; *n receives the live count.
- * Synchronises. (Checkpointing.) */
+/* Raw particle state in the tube's precision, live particles only, ID order:
+ * positions xi = z / dz as float (SCLF_FP32) or double (SCLF_FP64), or as
+ * int32 X = xi / pos_unit (SCLF_FIX32); u as float (FP32, FIX32) or double.
+ * Host buffers of capacity cap; *n receives the live count. Synchronises.
+ * (Checkpointing.) */
 int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u,
                         int64_t* id);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(PKG, "libsclf_tube.so")
 HEADER = os.path.join(ROOT, "include", "sclf_tube.h")
 
 SCLF_RHO_FLAT, SCLF_RHO_GR, SCLF_RHO_USER = 0, 1, 2
-SCLF_FP32, SCLF_FP64 = 0, 1
+SCLF_FP32, SCLF_FP64, SCLF_FIX32 = 0, 1, 2
 SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
 FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
 
@@ -41,7 +41,7 @@ class TubeParams(C.Structure):
 class TubeDerived(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "Omega", "theta_p", "R_cm", "n0", "omega_p0", "Lambda0", "kappa",
-        "theta_star", "R_over_Rstar", "L", "dz", "dt", "s", "rho0")]
+        "theta_star", "R_over_Rstar", "L", "dz", "dt", "s", "rho0", "pos_unit")]
 
 
 class TubeStats(C.Structure):
@@ -186,6 +186,7 @@ class Tube:
         self.derived = {n: getattr(d, n) for n, _ in TubeDerived._fields_}
         self.nz = int(params.Nz)
         self.fp64 = params.precision == SCLF_FP64
+        self.fix32 = params.precision == SCLF_FIX32
 
     def close(self):
         if getattr(self, "h", None):
@@ -239,7 +240,7 @@ class Tube:
         _check(self.lib.tube_save_particles(self.h, 0, C.byref(n), None, None, None),
                "tube_save_particles")
         dt = np.float64 if self.fp64 else np.float32
-        xi = np.empty(n.value, dt)
+        xi = np.empty(n.value, np.int32 if self.fix32 else dt)
         u = np.empty(n.value, dt)
         ids = np.empty(n.value, np.int64)
         _check(self.lib.tube_save_particles(self.h, n.value, C.byref(n), xi.ctypes.data,
@@ -249,7 +250,7 @@ class Tube:
 
     def load_particles(self, xi, u, ids=None):
         dt = np.float64 if self.fp64 else np.float32
-        xi = np.ascontiguousarray(xi, dtype=dt)
+        xi = np.ascontiguousarray(xi, dtype=np.int32 if self.fix32 else dt)
         u = np.ascontiguousarray(u, dtype=dt)
         idp = None
         if ids is not None:

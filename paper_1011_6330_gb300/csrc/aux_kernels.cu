@@ -9,13 +9,13 @@ namespace {
 // ---------------------------------------------------------------------------
 // Small kernels: append, base weight, ρ diagnostics, gather table
 // ---------------------------------------------------------------------------
-template <class Real>
-__global__ void append_kernel(DevState* st, Real* xi, Real* u, long long* ids,
+template <class Pos, class Mom>
+__global__ void append_kernel(DevState* st, Pos* xi, Mom* u, long long* ids,
                               long long first, long long n, bool zero) {
     const long long id0 = st->total_injected;
     for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < n;
          k += static_cast<long long>(gridDim.x) * blockDim.x) {
-        if (zero) { xi[first + k] = Real(0); u[first + k] = Real(0); }
+        if (zero) { xi[first + k] = Pos(0); u[first + k] = Mom(0); }
         if (ids) ids[first + k] = id0 + k;
     }
 }
@@ -32,12 +32,25 @@ __global__ void base_weight_kernel(DevState* st, const Real* xi, long long n) {
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
 }
 
+// W_0 of fixed-point positions: sum over the base cell of (2^fb - X) 2^(32-fb).
+__global__ void base_weight_fix32_kernel(DevState* st, const int* X, long long n, int fb) {
+    long long w = 0;
+    const int one = 1 << fb;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x = X[i];
+        if (x >= 0 && x < one) w += static_cast<long long>(one - x) << (32 - fb);
+    }
+    w = warp_sum(w);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
+}
+
 __global__ void finish_append_kernel(DevState* st, const double* ez, long long n_added,
                                      FieldConsts c) {
     st->n_slots += n_added;
     st->n_live += n_added;
     st->total_injected += n_added;
-    st->w0 = static_cast<long long>(st->acc_w0);
+    st->w0 += static_cast<long long>(st->acc_w0);
     st->acc_w0 = 0;
     long long n;
     double es;
@@ -46,11 +59,12 @@ __global__ void finish_append_kernel(DevState* st, const double* ez, long long n
     st->surface_field = es;
 }
 
-template <class Real>
-__global__ void rho_kernel(const Real* xi, long long n, double* acc, int nz) {
+template <class Pos>
+__global__ void rho_kernel(const Pos* xi, long long n, double* acc, int nz, double scale) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const double x = double(xi[i]);
+        if (!(xi[i] >= Pos(0))) continue;                      // hole
+        const double x = double(xi[i]) * scale;
         if (!(x >= 0.0 && x < double(nz))) continue;
         const double jf = floor(x);
         const int j = static_cast<int>(jf);
@@ -78,13 +92,20 @@ int grid_for(long long n, int block, int cap) {
 
 }  // namespace
 
-template <class Real>
-cudaError_t launch_append(DevState* st, Real* xi, Real* u, long long* ids, long long first,
+template <class Pos, class Mom>
+cudaError_t launch_append(DevState* st, Pos* xi, Mom* u, long long* ids, long long first,
                           long long n, bool zero_particles, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (!zero_particles && !ids) return cudaSuccess;
-    append_kernel<Real><<<grid_for(n, 256, 4096), 256, 0, s>>>(st, xi, u, ids, first, n,
-                                                               zero_particles);
+    append_kernel<Pos, Mom><<<grid_for(n, 256, 4096), 256, 0, s>>>(st, xi, u, ids, first, n,
+                                                                   zero_particles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_base_weight_fix32(DevState* st, const int* X, long long n_slots, int fb,
+                                     cudaStream_t s) {
+    if (n_slots <= 0) return cudaSuccess;
+    base_weight_fix32_kernel<<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(st, X, n_slots, fb);
     return cudaGetLastError();
 }
 
@@ -107,21 +128,25 @@ cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <class Real>
-cudaError_t launch_rho(const Real* xi, long long n_slots, double* rho_acc, int nz,
+template <class Pos>
+cudaError_t launch_rho(const Pos* xi, long long n_slots, double* rho_acc, int nz, double scale,
                        cudaStream_t s) {
     if (n_slots <= 0) return cudaSuccess;
-    rho_kernel<Real><<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(xi, n_slots, rho_acc, nz);
+    rho_kernel<Pos><<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(xi, n_slots, rho_acc, nz, scale);
     return cudaGetLastError();
 }
 
-#define SCLF_INSTANTIATE(R)                                                                  \
-    template cudaError_t launch_append<R>(DevState*, R*, R*, long long*, long long,          \
-                                          long long, bool, cudaStream_t);                    \
-    template cudaError_t launch_base_weight<R>(DevState*, const R*, long long, cudaStream_t); \
-    template cudaError_t launch_ez_table<R>(const double*, R*, int, cudaStream_t);           \
-    template cudaError_t launch_rho<R>(const R*, long long, double*, int, cudaStream_t);
-SCLF_INSTANTIATE(float)
-SCLF_INSTANTIATE(double)
-#undef SCLF_INSTANTIATE
+template cudaError_t launch_append<float, float>(DevState*, float*, float*, long long*,
+                                                long long, long long, bool, cudaStream_t);
+template cudaError_t launch_append<double, double>(DevState*, double*, double*, long long*,
+                                                  long long, long long, bool, cudaStream_t);
+template cudaError_t launch_append<int, float>(DevState*, int*, float*, long long*, long long,
+                                              long long, bool, cudaStream_t);
+template cudaError_t launch_base_weight<float>(DevState*, const float*, long long, cudaStream_t);
+template cudaError_t launch_base_weight<double>(DevState*, const double*, long long, cudaStream_t);
+template cudaError_t launch_ez_table<float>(const double*, float*, int, cudaStream_t);
+template cudaError_t launch_ez_table<double>(const double*, double*, int, cudaStream_t);
+template cudaError_t launch_rho<float>(const float*, long long, double*, int, double, cudaStream_t);
+template cudaError_t launch_rho<double>(const double*, long long, double*, int, double, cudaStream_t);
+template cudaError_t launch_rho<int>(const int*, long long, double*, int, double, cudaStream_t);
 }  // namespace sclf

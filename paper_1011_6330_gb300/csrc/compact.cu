@@ -25,9 +25,10 @@ __device__ __forceinline__ unsigned long long load_acquire(const unsigned long l
     return v;
 }
 
-template <class Real>
-__global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Real> a) {
-    using L = Layout<Real>;
+template <class Pos, class Mom>
+__global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Pos, Mom> a) {
+    using L = Layout<Pos>;
+    static_assert(Layout<Pos>::kPPT == Layout<Mom>::kPPT, "one tile shape");
     constexpr int kPPT = L::kPPT, kVec = L::kVec, kTile = L::kTile;
     __shared__ long long s_tile;
     __shared__ int s_warp[kThreads / 32];
@@ -53,7 +54,8 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Rea
         const long long tile = s_tile;
         if (tile >= ntiles) break;
         const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
-        Real xs[kPPT], us[kPPT];
+        Pos xs[kPPT];
+        Mom us[kPPT];
 #pragma unroll
         for (int v = 0; v < kPPT; v += kVec) {
             vload(a.xi + i0 + v, xs + v);
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Rea
         unsigned mask = 0;
 #pragma unroll
         for (int k = 0; k < kPPT; ++k)
-            if (i0 + k < n_slots && xs[k] >= Real(0)) mask |= 1u << k;
+            if (i0 + k < n_slots && xs[k] >= Pos(0)) mask |= 1u << k;
         const int cnt = __popc(mask);
         // block exclusive scan of cnt
         int incl = cnt;
@@ -138,22 +140,25 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Rea
 
 }  // namespace
 
-template <class Real>
+template <class Pos, class Mom>
 int compact_grid_size(int device_sms) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<Real>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<Pos, Mom>, kThreads, 0);
     if (per_sm < 1) per_sm = 1;
     return per_sm * device_sms;
 }
 
-template <class Real>
-cudaError_t launch_compact(const CompactArgs<Real>& a, int grid, cudaStream_t s) {
-    compact_kernel<Real><<<grid, kThreads, 0, s>>>(a);
+template <class Pos, class Mom>
+cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s) {
+    compact_kernel<Pos, Mom><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template int compact_grid_size<float>(int);
-template int compact_grid_size<double>(int);
-template cudaError_t launch_compact<float>(const CompactArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_compact<double>(const CompactArgs<double>&, int, cudaStream_t);
+template int compact_grid_size<float, float>(int);
+template int compact_grid_size<double, double>(int);
+template int compact_grid_size<int, float>(int);
+template cudaError_t launch_compact<float, float>(const CompactArgs<float, float>&, int, cudaStream_t);
+template cudaError_t launch_compact<double, double>(const CompactArgs<double, double>&, int, cudaStream_t);
+template cudaError_t launch_compact<int, float>(const CompactArgs<int, float>&, int, cudaStream_t);
+
 }  // namespace sclf

@@ -23,7 +23,19 @@ template <> struct Layout<double> {
     static constexpr int kPPT = 4;
     static constexpr int kTile = kThreads * kPPT;
 };
+template <> struct Layout<int> {            // fixed-point positions (int32)
+    static constexpr int kVec = 4;          // int4 loads
+    static constexpr int kPPT = 8;
+    static constexpr int kTile = kThreads * kPPT;
+};
 constexpr int kMaxTile = kThreads * 16;
+
+// Fractional bits of SCLF_FIX32 positions: the largest fb with Nz 2^fb <= 2^31.
+inline int fix32_bits(long long nz) {
+    int b = 0;
+    while ((1LL << b) < nz) ++b;        // b = ceil(log2 Nz)
+    return 31 - b;
+}
 
 // 2^32: quantum of the fixed-point accumulators (current fractions and the
 // base-cell weight W_0).
@@ -93,11 +105,29 @@ struct FieldArgs {
     FieldConsts c;
 };
 
-template <class Real>
+// Particle kernel of the SCLF_FIX32 mode: positions X = xi 2^fb (int32,
+// holes < 0), momenta float32, fixed-point current.
+struct PushFixArgs {
+    DevState* st;
+    int* X;
+    float* u;
+    long long* ids;            // may be null
+    const float* ez2;          // gather table, float32
+    long long* jacc;           // nz accumulators, 2^-32 units
+    long long capacity;
+    int nz;
+    int fb;                    // fractional bits
+    float dt;                  // (float)dt
+    float cfl;                 // (float)(dt/dz)
+    float scale;               // 2^-fb
+    float two_fb;              // 2^fb
+};
+
+template <class Pos, class Mom>
 struct CompactArgs {
     DevState* st;
-    Real* xi;
-    Real* u;
+    Pos* xi;                         // holes: xi < 0
+    Mom* u;
     long long* ids;
     unsigned long long* tile_state;  // one word per tile
     long long capacity;
@@ -113,25 +143,29 @@ int push_grid_size(int accumulate, int device_sms);
 template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
                          cudaStream_t s);
-template <class Real>
-cudaError_t launch_compact(const CompactArgs<Real>& a, int grid, cudaStream_t s);
-template <class Real>
+cudaError_t launch_push_fix32(const PushFixArgs& a, int grid, cudaStream_t s);
+int push_fix32_grid_size(int device_sms);
+template <class Pos, class Mom>
+cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s);
+template <class Pos, class Mom>
 int compact_grid_size(int device_sms);
-template <class Real>
-cudaError_t launch_append(DevState* st, Real* xi, Real* u, long long* ids,
+template <class Pos, class Mom>
+cudaError_t launch_append(DevState* st, Pos* xi, Mom* u, long long* ids,
                           long long first, long long n, bool zero_particles,
                           cudaStream_t s);
 template <class Real>
 cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots,
                                cudaStream_t s);
+cudaError_t launch_base_weight_fix32(DevState* st, const int* X, long long n_slots,
+                                     int fb, cudaStream_t s);
 cudaError_t launch_finish_append(DevState* st, const double* ez,
                                  long long n_added, FieldConsts c,
                                  cudaStream_t s);
 template <class Real>
 cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s);
-template <class Real>
-cudaError_t launch_rho(const Real* xi, long long n_slots, double* rho_acc,
-                       int nz, cudaStream_t s);
+template <class Pos>
+cudaError_t launch_rho(const Pos* xi, long long n_slots, double* rho_acc,
+                       int nz, double scale, cudaStream_t s);
 
 // Host set-up (setup.cpp).
 int derive(const tube_params* p, tube_derived* d);

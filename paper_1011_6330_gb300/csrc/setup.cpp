@@ -33,7 +33,9 @@ int derive(const tube_params* p, tube_derived* d) {
     std::memset(d, 0, sizeof(*d));
     if (!(p->Nz >= 2 && p->Nz <= (int64_t(1) << 24))) return SCLF_EINVAL;
     if (!(p->L_over_R > 0.0) || !std::isfinite(p->L_over_R)) return SCLF_EINVAL;
-    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64) return SCLF_EINVAL;
+    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64 && p->precision != SCLF_FIX32)
+        return SCLF_EINVAL;
+    if (p->precision == SCLF_FIX32 && p->accumulate != SCLF_ACC_FIXED64) return SCLF_EINVAL;
     if (p->accumulate != SCLF_ACC_FIXED64 && p->accumulate != SCLF_ACC_FP64) return SCLF_EINVAL;
     if (p->rho_gj_mode < SCLF_RHO_FLAT || p->rho_gj_mode > SCLF_RHO_USER) return SCLF_EINVAL;
     if (p->rho_gj_mode == SCLF_RHO_USER && !p->rho_gj_user) return SCLF_EINVAL;
@@ -82,6 +84,7 @@ int derive(const tube_params* p, tube_derived* d) {
         d->s = -std::fabs(d->rho0) * d->L / double(p->target_particles);
     }
     if (!(d->s < 0.0) || !std::isfinite(d->s)) return SCLF_EINVAL;
+    d->pos_unit = p->precision == SCLF_FIX32 ? std::ldexp(1.0, -fix32_bits(p->Nz)) : 1.0;
     return SCLF_OK;
 }
 

@@ -76,6 +76,7 @@ struct sclf_tube {
     std::vector<double> rho_gj;
     FieldConsts fc{};
     int push_grid = 0, compact_grid = 0;
+    int fb = 0;                        // fractional bits of SCLF_FIX32 positions
     int64_t host_step = 0;             // steps launched (== device step count)
     int steps_since_compact = 0;
     int compact_every = 64;
@@ -143,13 +144,13 @@ FieldArgs<Real> field_args(sclf_tube* t, int parity) {
     return a;
 }
 
-template <class Real>
-CompactArgs<Real> compact_args(sclf_tube* t, int force) {
-    CompactArgs<Real> a;
+template <class Pos, class Mom>
+CompactArgs<Pos, Mom> compact_args(sclf_tube* t, int force) {
+    CompactArgs<Pos, Mom> a;
     a.force = force;
     a.st = t->st;
-    a.xi = static_cast<Real*>(t->xi);
-    a.u = static_cast<Real*>(t->u);
+    a.xi = static_cast<Pos*>(t->xi);
+    a.u = static_cast<Mom*>(t->u);
     a.ids = t->ids;
     a.tile_state = t->tiles;
     a.capacity = t->p.capacity;
@@ -157,8 +158,73 @@ CompactArgs<Real> compact_args(sclf_tube* t, int force) {
 }
 
 bool fp64(const sclf_tube* t) { return t->p.precision == SCLF_FP64; }
+bool fix32(const sclf_tube* t) { return t->p.precision == SCLF_FIX32; }
+
+PushFixArgs push_fix_args(sclf_tube* t) {
+    PushFixArgs a;
+    a.st = t->st;
+    a.X = static_cast<int*>(t->xi);
+    a.u = static_cast<float*>(t->u);
+    a.ids = t->ids;
+    a.ez2 = static_cast<const float*>(t->ez2);
+    a.jacc = static_cast<long long*>(t->jacc);
+    a.capacity = t->p.capacity;
+    a.nz = static_cast<int>(t->p.Nz);
+    a.fb = t->fb;
+    a.dt = static_cast<float>(t->d.dt);
+    a.cfl = static_cast<float>(t->d.dt / t->d.dz);
+    a.scale = std::ldexp(1.0f, -t->fb);
+    a.two_fb = std::ldexp(1.0f, t->fb);
+    return a;
+}
+
+// Per-precision launches of the small kernels.
+cudaError_t do_append(sclf_tube* t, long long first, long long n, bool zero) {
+    if (fp64(t))
+        return launch_append<double, double>(t->st, static_cast<double*>(t->xi),
+                                             static_cast<double*>(t->u), t->ids, first, n, zero, t->stream);
+    if (fix32(t))
+        return launch_append<int, float>(t->st, static_cast<int*>(t->xi), static_cast<float*>(t->u),
+                                         t->ids, first, n, zero, t->stream);
+    return launch_append<float, float>(t->st, static_cast<float*>(t->xi), static_cast<float*>(t->u),
+                                       t->ids, first, n, zero, t->stream);
+}
+// Adds the base-cell weight of slots [first, first + n) to the accumulator
+// that the next finish_append folds into W_0.
+cudaError_t do_base_weight(sclf_tube* t, long long first, long long n) {
+    if (fp64(t))
+        return launch_base_weight<double>(t->st, static_cast<const double*>(t->xi) + first, n, t->stream);
+    if (fix32(t))
+        return launch_base_weight_fix32(t->st, static_cast<const int*>(t->xi) + first, n, t->fb, t->stream);
+    return launch_base_weight<float>(t->st, static_cast<const float*>(t->xi) + first, n, t->stream);
+}
+cudaError_t do_rho(sclf_tube* t, long long slots) {
+    const int nz = static_cast<int>(t->p.Nz);
+    if (fp64(t)) return launch_rho<double>(static_cast<const double*>(t->xi), slots, t->rho_acc, nz, 1.0, t->stream);
+    if (fix32(t)) return launch_rho<int>(static_cast<const int*>(t->xi), slots, t->rho_acc, nz,
+                                         std::ldexp(1.0, -t->fb), t->stream);
+    return launch_rho<float>(static_cast<const float*>(t->xi), slots, t->rho_acc, nz, 1.0, t->stream);
+}
+cudaError_t do_ez_table(sclf_tube* t) {
+    const int nz = static_cast<int>(t->p.Nz);
+    return fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), nz, t->stream)
+                   : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), nz, t->stream);
+}
+// Position of raw slot i in cell units; negative for a hole.
+double raw_cells(const sclf_tube* t, const void* raw, int64_t i) {
+    if (fp64(t)) return static_cast<const double*>(raw)[i];
+    if (fix32(t)) {
+        const int X = static_cast<const int*>(raw)[i];
+        return X < 0 ? -1.0 : std::ldexp(static_cast<double>(X), -t->fb);
+    }
+    return static_cast<const float*>(raw)[i];
+}
+double raw_mom(const sclf_tube* t, const void* raw, int64_t i) {
+    return fp64(t) ? static_cast<const double*>(raw)[i] : double(static_cast<const float*>(raw)[i]);
+}
 
 cudaError_t enqueue_push(sclf_tube* t, cudaStream_t s) {
+    if (fix32(t)) return launch_push_fix32(push_fix_args(t), t->push_grid, s);
     return fp64(t) ? launch_push<double>(push_args<double>(t), t->p.accumulate, t->push_grid, s)
                    : launch_push<float>(push_args<float>(t), t->p.accumulate, t->push_grid, s);
 }
@@ -173,8 +239,9 @@ cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s, int force) {
         const cudaError_t e = cudaMemsetAsync(&t->st->ticket, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
     }
-    return fp64(t) ? launch_compact<double>(compact_args<double>(t, force), t->compact_grid, s)
-                   : launch_compact<float>(compact_args<float>(t, force), t->compact_grid, s);
+    if (fix32(t)) return launch_compact<int, float>(compact_args<int, float>(t, force), t->compact_grid, s);
+    return fp64(t) ? launch_compact<double, double>(compact_args<double, double>(t, force), t->compact_grid, s)
+                   : launch_compact<float, float>(compact_args<float, float>(t, force), t->compact_grid, s);
 }
 
 int read_state(sclf_tube* t, DevState* h) {
@@ -379,14 +446,12 @@ int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int
             if (id) {
                 CK(cudaMemcpyAsync(t->ids + h.n_slots, id, n * 8, cudaMemcpyHostToDevice, t->stream));
             } else {
-                CK(fp64(t) ? launch_append<double>(t->st, nullptr, nullptr, t->ids, h.n_slots, n, false, t->stream)
-                           : launch_append<float>(t->st, nullptr, nullptr, t->ids, h.n_slots, n, false, t->stream));
+                CK(do_append(t, h.n_slots, n, false));
             }
         }
     }
-    const int64_t slots = h.n_slots + n;
-    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), slots, t->stream)
-               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), slots, t->stream));
+    // W_0 is a sum over particles: add the new ones' share
+    CK(do_base_weight(t, h.n_slots, n));
     CK(launch_finish_append(t->st, t->ez, n, t->fc, t->stream));
     CK(cudaStreamSynchronize(t->stream));
     return SCLF_OK;
@@ -442,6 +507,7 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     int rc = derive(p, &t->d);
     if (rc) { delete t; return rc; }
     t->lay = plan(p);
+    t->fb = p->precision == SCLF_FIX32 ? fix32_bits(p->Nz) : 0;
     t->stream = static_cast<cudaStream_t>(stream);
     t->compact_every = p->compact_interval > 0 ? p->compact_interval : 64;
     t->chunk_steps = t->compact_every + (t->compact_every & 1);
@@ -503,15 +569,17 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
         cudaMemcpyAsync(t->ez, ez0.data(), nz * 8, cudaMemcpyHostToDevice, t->stream) ||
         cudaMemcpyAsync(t->er[0], phi.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream))
         return fail(SCLF_ECUDA);
-    cudaError_t e = fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), int(nz), t->stream)
-                            : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), int(nz), t->stream);
+    cudaError_t e = do_ez_table(t);
     if (e != cudaSuccess) return fail(cuda_fail(e));
     if (launch_finish_append(t->st, t->ez, 0, t->fc, t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
     if (cudaStreamSynchronize(t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
 
-    t->push_grid = fp64(t) ? push_grid_size<double>(p->accumulate, t->sms)
+    t->push_grid = fix32(t) ? push_fix32_grid_size(t->sms)
+                 : fp64(t) ? push_grid_size<double>(p->accumulate, t->sms)
                            : push_grid_size<float>(p->accumulate, t->sms);
-    t->compact_grid = fp64(t) ? compact_grid_size<double>(t->sms) : compact_grid_size<float>(t->sms);
+    t->compact_grid = fix32(t) ? compact_grid_size<int, float>(t->sms)
+                    : fp64(t) ? compact_grid_size<double, double>(t->sms)
+                              : compact_grid_size<float, float>(t->sms);
     const int64_t tile = fp64(t) ? Layout<double>::kTile : Layout<float>::kTile;
     const int64_t max_tiles = l.cap_pad / tile;
     if (t->push_grid > max_tiles) t->push_grid = static_cast<int>(max_tiles);
@@ -564,11 +632,8 @@ int tube_inject(tube_t t, int64_t* n_injected) {
     if (rc) return rc;
     int64_t n = h.n_inj;
     if (h.n_slots + n > t->p.capacity) return SCLF_ECAPACITY;
-    CK(fp64(t) ? launch_append<double>(t->st, static_cast<double*>(t->xi), static_cast<double*>(t->u), t->ids, h.n_slots, n, true, t->stream)
-               : launch_append<float>(t->st, static_cast<float*>(t->xi), static_cast<float*>(t->u), t->ids, h.n_slots, n, true, t->stream));
-    const int64_t slots = h.n_slots + n;
-    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), slots, t->stream)
-               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), slots, t->stream));
+    CK(do_append(t, h.n_slots, n, true));
+    CK(do_base_weight(t, h.n_slots, n));
     CK(launch_finish_append(t->st, t->ez, n, t->fc, t->stream));
     CK(cudaStreamSynchronize(t->stream));
     if (n_injected) *n_injected = n;
@@ -580,14 +645,24 @@ int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
     for (int64_t i = 0; i < n; ++i)
         if (!(z[i] >= 0.0 && z[i] < t->d.L) || !std::isfinite(u[i])) return SCLF_EINVAL;
     std::vector<char> xs, us;
-    if (fp64(t)) to_native<double>(z, u, n, t->d.dz, xs, us);
-    else to_native<float>(z, u, n, t->d.dz, xs, us);
-    // a position that rounds up to the top node is outside the tube
-    for (int64_t i = 0; i < n; ++i) {
-        const double x = fp64(t) ? reinterpret_cast<double*>(xs.data())[i]
-                                 : double(reinterpret_cast<float*>(xs.data())[i]);
-        if (!(x < double(t->p.Nz))) return SCLF_EINVAL;
+    if (fp64(t)) {
+        to_native<double>(z, u, n, t->d.dz, xs, us);
+    } else if (fix32(t)) {
+        // X = round-half-even(z / dz 2^fb)
+        to_native<float>(z, u, n, t->d.dz, xs, us);
+        int* X = reinterpret_cast<int*>(xs.data());
+        const double top = std::ldexp(double(t->p.Nz), t->fb);
+        for (int64_t i = 0; i < n; ++i) {
+            const double v = std::nearbyint(std::ldexp(z[i] / t->d.dz, t->fb));
+            if (!(v < top)) return SCLF_EINVAL;
+            X[i] = static_cast<int>(v);
+        }
+    } else {
+        to_native<float>(z, u, n, t->d.dz, xs, us);
     }
+    // a position that rounds up to the top node is outside the tube
+    for (int64_t i = 0; i < n; ++i)
+        if (!(raw_cells(t, xs.data(), i) < double(t->p.Nz))) return SCLF_EINVAL;
     return append_raw(t, n, xs.data(), us.data(), nullptr);
 }
 
@@ -633,8 +708,7 @@ int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi, double* J, 
         int rc = read_state(t, &h);
         if (rc) return rc;
         CK(cudaMemsetAsync(t->rho_acc, 0, (nz + 1) * 8, t->stream));
-        CK(fp64(t) ? launch_rho<double>(static_cast<const double*>(t->xi), h.n_slots, t->rho_acc, int(nz), t->stream)
-                   : launch_rho<float>(static_cast<const float*>(t->xi), h.n_slots, t->rho_acc, int(nz), t->stream));
+        CK(do_rho(t, h.n_slots));
         CK(cudaMemcpyAsync(rho, t->rho_acc, (nz + 1) * 8, cudaMemcpyDeviceToHost, t->stream));
     }
     CK(cudaStreamSynchronize(t->stream));
@@ -662,12 +736,10 @@ static int read_raw(tube_t t, int64_t cap, int64_t* n, void* xo, void* uo, int64
     }
     int64_t k = 0;
     for (int64_t i = 0; i < ns; ++i) {
-        const double x = fp64(t) ? reinterpret_cast<double*>(xs.data())[i]
-                                 : double(reinterpret_cast<float*>(xs.data())[i]);
+        const double x = raw_cells(t, xs.data(), i);
         if (!(x >= 0.0)) continue;                       // hole
         if (k < cap) {
-            const double uu = fp64(t) ? reinterpret_cast<double*>(us.data())[i]
-                                      : double(reinterpret_cast<float*>(us.data())[i]);
+            const double uu = raw_mom(t, us.data(), i);
             if (convert) {
                 if (xo) static_cast<double*>(xo)[k] = x * t->d.dz;
                 if (uo) static_cast<double*>(uo)[k] = uu;
@@ -697,10 +769,8 @@ int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, cons
     if (!t || n < 0 || n > t->p.capacity || (n > 0 && (!xi || !u))) return SCLF_EINVAL;
     int64_t max_id = n - 1;
     for (int64_t i = 0; i < n; ++i) {
-        const double x = fp64(t) ? static_cast<const double*>(xi)[i]
-                                 : double(static_cast<const float*>(xi)[i]);
-        const double v = fp64(t) ? static_cast<const double*>(u)[i]
-                                 : double(static_cast<const float*>(u)[i]);
+        const double x = raw_cells(t, xi, i);
+        const double v = raw_mom(t, u, i);
         if (!(x >= 0.0 && x < double(t->p.Nz)) || !std::isfinite(v)) return SCLF_EINVAL;
         if (id && id[i] > max_id) max_id = id[i];
     }
@@ -710,6 +780,7 @@ int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, cons
     h.n_slots = 0;
     h.n_live = 0;
     h.total_injected = 0;
+    h.w0 = 0;
     CK(cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream));
     rc = append_raw(t, n, xi, u, id);
     if (rc) return rc;
@@ -737,13 +808,12 @@ int tube_solve_fields(tube_t t) {
     CK(cudaMemcpyAsync(t->ez, ez0.data(), nz * 8, cudaMemcpyHostToDevice, t->stream));
     CK(cudaMemcpyAsync(t->er[par], phi.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream));
     CK(cudaMemsetAsync(t->b[par], 0, nz * 8, t->stream));
-    CK(fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), int(nz), t->stream)
-               : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), int(nz), t->stream));
+    CK(do_ez_table(t));
     DevState h;
     rc = read_state(t, &h);
     if (rc) return rc;
-    CK(fp64(t) ? launch_base_weight<double>(t->st, static_cast<const double*>(t->xi), h.n_slots, t->stream)
-               : launch_base_weight<float>(t->st, static_cast<const float*>(t->xi), h.n_slots, t->stream));
+    CK(cudaMemsetAsync(&t->st->w0, 0, sizeof(long long), t->stream));
+    CK(do_base_weight(t, 0, h.n_slots));
     CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
     CK(cudaStreamSynchronize(t->stream));
     return SCLF_OK;

@@ -61,3 +61,20 @@ def random_particles(n, L, seed, u_sigma=0.5):
     z = rng.uniform(0.0, L, n)
     u = rng.normal(0.0, u_sigma, n)
     return z, u
+
+
+def prefilled_beam_chunks(n, L, gamma_far, seed, chunk=1 << 24, jitter=0.01,
+                          eta_of_z=None):
+    """The state of :func:`prefilled_beam` (descending stratified heights,
+    ramp momenta with jitter) generated in chunks of `chunk` particles so
+    that large tubes fit in host memory; chunk c draws from
+    default_rng([seed, c]). Yields (z, u) in ID order."""
+    for c, k0 in enumerate(range(0, n, chunk)):
+        m = min(chunk, n - k0)
+        rng = np.random.default_rng([seed, c])
+        k = np.arange(k0, k0 + m, dtype=np.float64)
+        z = L * (1.0 - (k + rng.random(m)) / n)
+        z = np.minimum(z, np.nextafter(L, 0.0))
+        g = gamma_ramp(z, gamma_far, eta_of_z=eta_of_z)
+        g = np.maximum(g * (1.0 + jitter * rng.standard_normal(m)), 1.0)
+        yield z, np.sqrt(g * g - 1.0)

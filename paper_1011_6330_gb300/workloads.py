@@ -41,3 +41,14 @@ def gr_tube(B_G=1e12, P_s=0.5, Rstar_cm=1e6, incl=0.5, Nz=65536, n_particles=10 
                 R_cm=0.0, L_over_R=L, Nz=Nz, dt=0.0, rho_gj_mode=B.SCLF_RHO_GR,
                 target_particles=n_particles, capacity=capacity, precision=precision,
                 accumulate=accumulate, track_ids=track_ids)
+
+
+def large_tube(n_particles=2 ** 30, Nz=2 ** 20, capacity=None, track_ids=0):
+    """Large single frame-dragging tube: B = 3e12 G, P = 0.1 s, R_* = 10 km,
+    length 2 R_*, Nz = 2^20, GR rho_GJ at i = 0.5, 2^30 particles with
+    32-bit fixed-point positions (SCLF_FIX32) and float32 momenta -- 8 bytes
+    per particle, uniform 2^-11-cell position resolution."""
+    return gr_tube(B_G=3e12, P_s=0.1, Rstar_cm=1e6, incl=0.5, Nz=Nz,
+                   n_particles=n_particles, capacity=capacity,
+                   precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64,
+                   track_ids=track_ids)

@@ -287,3 +287,96 @@ def test_full_size_gr_step_against_oracle_on_all_particles(gpu_lib):
     assert st["pending_injection"] == n_next
     assert t.check() == 0
     t.close()
+
+
+# ---------------------------------------------------------------------------
+# SCLF_FIX32: 32-bit fixed-point positions
+# ---------------------------------------------------------------------------
+
+def test_fix32_tube_matches_oracle_every_step(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64)
+    t, o = pair(gpu_lib, kw, "fix32", "fixed")
+    assert t.derived["pos_unit"] == 2.0 ** -o.fb
+    worst = {}
+    for n in range(200):
+        t.step()
+        o.step()
+        e = compare(t, o, TOL[B.SCLF_FP32], "step %d" % n)
+        worst = {k: max(v, worst.get(k, 0.0)) for k, v in e.items()}
+    X, u, ids = t.save_particles()
+    assert np.array_equal(X.astype(np.int64), o.xi) and np.array_equal(u, o.u)
+    print("fix32 worst", worst)
+    t.close()
+
+
+def test_fix32_ragged_tiles_with_forced_compaction(gpu_lib):
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64)
+    z, u = synth.random_particles(2048 * 5 + 77, kw["L_over_R"], seed=8, u_sigma=2.0)
+    t, o = pair(gpu_lib, dict(kw, compact_interval=5), "fix32", "fixed")
+    t.add_particles(z, u)
+    o.add_particles(z, u)
+    for n in range(60):
+        t.step()
+        o.step()
+        if n % 9 == 8:
+            t.compact()
+    compare(t, o, TOL[B.SCLF_FP32])
+    X, uu, ids = t.save_particles()
+    assert np.array_equal(X.astype(np.int64), o.xi) and np.array_equal(ids, o.ids)
+    t.close()
+
+
+def test_large_fix32_tube_step_against_oracle_on_all_particles(gpu_lib):
+    """The large tube's configuration (B = 3e12 G, P = 0.1 s, Nz = 2^20,
+    fixed-point positions) with 2^27 particles: one step checked against the
+    oracle on every particle -- positions and momenta bit for bit, the whole
+    current grid and the field update exactly, removals and the next
+    injection count."""
+    n = 2 ** 27
+    kw = workloads.large_tube(n_particles=n)
+    t = B.Tube(B.default_params(**kw))
+    d = t.derived
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    eta = lambda zz: 1.0 + zz * cu["R_over_Rstar"]
+    gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(kw["incl_rad"])
+    for z, u in synth.prefilled_beam_chunks(n, d["L"] - d["dz"], gfar, seed=5,
+                                            chunk=1 << 25, eta_of_z=eta):
+        t.add_particles(z, u)
+    t.solve_fields()
+    t.run(2)
+    f0 = t.read_fields(rho=False)
+    X0, u0, _ = t.save_particles()
+    n_inj = t.status()["pending_injection"]
+    t.step()
+    f1 = t.read_fields(rho=False)
+    X1, u1, _ = t.save_particles()
+    st = t.status()
+    nz, fb = kw["Nz"], orc.fix32_bits(kw["Nz"])
+    assert st["last_injected"] == n_inj
+    xs_all = np.concatenate([X0.astype(np.int64), np.zeros(n_inj, np.int64)])
+    us_all = np.concatenate([u0, np.zeros(n_inj, np.float32)])
+    del X0, u0
+    acc = np.zeros(nz, np.int64)
+    x1o = np.empty_like(xs_all)
+    u1o = np.empty_like(us_all)
+    fin = np.empty(xs_all.size, bool)
+    step = 1 << 24
+    for s0 in range(0, xs_all.size, step):
+        xs, us = xs_all[s0:s0 + step], us_all[s0:s0 + step]
+        e = orc.gather_fix32(f0["ez"], xs, fb)
+        x1, u1c, ok = orc.push_fix32(xs, us, e, d["dt"], d["dz"], fb)
+        x1o[s0:s0 + xs.size], u1o[s0:s0 + xs.size], fin[s0:s0 + xs.size] = x1, u1c, ok
+        acc += orc.deposit_fix32(nz, xs[ok], x1[ok], fb)
+    alive = fin & (x1o >= 0) & (x1o < (nz << fb))
+    assert st["last_removed"] == x1o.size - int(np.count_nonzero(alive))
+    assert np.array_equal(X1.astype(np.int64), x1o[alive]) and np.array_equal(u1, u1o[alive])
+    j = orc.current_from(acc, d["s"], d["dt"], "fixed")
+    assert np.array_equal(f1["j"], j)
+    ez, er, b = orc.field_update(f0["ez"], f0["er"], f0["b"], j, d["dt"], d["dz"])
+    assert np.array_equal(f1["ez"], ez) and np.array_equal(f1["er"], er)
+    assert np.array_equal(f1["b"], b)
+    w0 = orc.base_weight_fix32(X1.astype(np.int64), fb)
+    n_next, _ = orc.injection_count(ez[0], w0, d["s"], d["dz"], d["rho0"])
+    assert st["pending_injection"] == n_next
+    assert t.check() == 0
+    t.close()
