@@ -34,8 +34,9 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (gather+push+deposit), % HBM roofline; batched/adjoint vs plain"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 16          # FP32 xi and u, read once and written once per step
-KERNEL_SRC = [os.path.join(ROOT, "paper_1011_6330_gb300", "csrc", f)
-              for f in ("push.cu", "device_common.cuh", "sclf_internal.h")]
+CSRC = os.path.join(ROOT, "paper_1011_6330_gb300", "csrc")
+KERNEL_SRC = {"gr1e8": ["push.cu", "device_common.cuh", "sclf_internal.h"],
+              "large": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
 
 
@@ -85,11 +86,12 @@ def rank_seed(rank, base=0):
     return base + 1000003 * rank
 
 
-def kernel_sha():
-    """Hash of the particle kernel's sources (ties a traffic capture to them)."""
+def kernel_sha(workload):
+    """Hash of the workload's particle-kernel sources (ties a traffic capture
+    to them)."""
     h = hashlib.sha256()
-    for p in KERNEL_SRC:
-        with open(p, "rb") as f:
+    for p in KERNEL_SRC[workload]:
+        with open(os.path.join(CSRC, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -328,7 +330,8 @@ def main():
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         ent = tr.get(args.workload, {})
-        if ent.get("kernel_sha") == kernel_sha() and ent.get("accumulate") == args.accumulate \
+        if ent.get("kernel_sha") == kernel_sha(args.workload) \
+                and ent.get("accumulate", "fixed64") == args.accumulate \
                 and ent.get("order", "descending") == args.order and ent.get("particles") == n:
             traffic = ent["bytes_per_launch"]
     gpu_launches = 2 * tm["n_steps"] + tm["n_compactions"]

@@ -63,7 +63,7 @@ extern "C" {
                                 fb = 31 - ceil(log2 Nz) (uniform resolution
                                 along the tube), float32 momenta and push, the
                                 displacement rounded half-even to 2^-fb cell;
-                                requires SCLF_ACC_FIXED64                      */
+                                requires SCLF_ACC_FIXED64 and Nz >= 16         */
 
 #define SCLF_ACC_FIXED64 0   /* current fractions summed exactly in int64
                                 multiples of 2^-32 (order independent)        */

@@ -1,0 +1,181 @@
+// (a1)-(a5) of one PIC step (Sec. 2, Figure A of arXiv:1011.6330) for tubes
+// whose particle positions are 32-bit fixed point (SCLF_FIX32).
+#include "device_common.cuh"
+
+namespace sclf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// (a1)-(a5) with SCLF_FIX32 positions: X = xi 2^fb in int32 (holes < 0),
+// float32 momenta and push, the displacement rounded half-even to the 2^-fb
+// grid, current fractions and the base weight as exact integers (2^-32 units).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long shl_signed(long long v, int sh) {
+    return static_cast<long long>(static_cast<unsigned long long>(v) << sh);
+}
+
+__global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs a) {
+    constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
+    DevState* st = a.st;
+    const long long n_slots = st->n_slots;
+    const long long n_req = st->n_inj;
+    long long room = a.capacity - n_slots;
+    room = room > 0 ? room : 0;
+    const long long n_inj = n_req < room ? n_req : room;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->inj_done = n_inj;
+        st->slots_processed += static_cast<unsigned long long>(n_slots + n_inj);
+        if (n_inj < n_req) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+    }
+    const long long n_tot = n_slots + n_inj;
+    const long long id0 = st->total_injected;
+    const long long ntiles = (n_tot + kTile - 1) / kTile;
+
+    long long w0_acc = 0;
+    long long removed = 0;
+    bool nonfinite = false;
+
+    const int nz = a.nz, fb = a.fb, sh = 32 - a.fb;
+    const unsigned half = 1u << (fb - 1), mask = (1u << fb) - 1u;
+    const long long one = 1LL << fb;
+    const long long top = static_cast<long long>(nz) << fb;     // first position past the tube
+    const unsigned utop = static_cast<unsigned>(top);             // <= 2^31
+    const float dt = a.dt, cfl = a.cfl, scale = a.scale, two_fb = a.two_fb;
+    const float2* __restrict__ tab = reinterpret_cast<const float2*>(a.ez2);
+    long long* __restrict__ jacc = a.jacc;
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
+        int xs[kPPT];
+        float us[kPPT];
+#pragma unroll
+        for (int v = 0; v < kPPT; v += kVec) {
+            vload(a.X + i0 + v, xs + v);
+            vload(a.u + i0 + v, us + v);
+        }
+        const long long r_slots = n_slots - i0, r_tot = n_tot - i0;
+        const int k_real = r_slots <= 0 ? 0 : (r_slots >= kPPT ? kPPT : int(r_slots));
+        const int k_tot = r_tot <= 0 ? 0 : (r_tot >= kPPT ? kPPT : int(r_tot));
+        if (k_real < k_tot) {                        // (a1) new electrons at the base
+#pragma unroll
+            for (int k = 0; k < kPPT; ++k) {
+                if (k >= k_real && k < k_tot) {
+                    xs[k] = 0;
+                    us[k] = 0.0f;
+                    if (a.ids) a.ids[i0 + k] = id0 + (i0 + k - n_slots);
+                }
+            }
+        }
+        // run key: the first slot's cell (0xffffffff for a hole: no run)
+        const unsigned rkey = (k_tot > 0 && xs[0] >= 0) ? (static_cast<unsigned>(xs[0]) >> fb)
+                                                        : 0xffffffffu;
+        int ra = 0;                                   // run sum in 2^-fb units
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            const int X = xs[k];
+            const bool lv = (k < k_tot) & (X >= 0);
+            const unsigned U = lv ? static_cast<unsigned>(X) : 0u;
+            // (a2) h = X + 2^(fb-1): m = h >> fb, f = (h mod 2^fb) 2^-fb
+            const unsigned h = U + half;
+            const float f = __uint2float_rn(h & mask) * scale;
+            const float2 e = tab[h >> fb];
+            const float ep = (1.0f - f) * e.x + f * e.y;
+            // (a3) Eq. 1, then the displacement on the 2^-fb grid
+            const float u1 = us[k] - ep * dt;
+            const float g = __fsqrt_rn(1.0f + u1 * u1);
+            const float d = __fdiv_rn(u1, g) * cfl;
+            const bool fin = isfinite(d);
+            const int inc = __float2int_rn(d * two_fb);  // |inc| < 2^fb
+            // X1 = X + inc in 32-bit two's complement: with X < 2^31 and
+            // |inc| < 2^fb, 0 <= X1 < Nz 2^fb exactly when U1 < Nz 2^fb
+            const unsigned U1 = U + static_cast<unsigned>(inc);
+            const unsigned c0 = U >> fb;
+            // (a4) in-cell current fraction F_c(X1) - F_c(X) = X1 - X = inc
+            const bool common = lv & fin & (U1 < utop) & ((U1 >> fb) == c0) & (c0 != 0u) &
+                                (c0 == rkey);
+            ra += common ? inc : 0;
+            if (lv & !common) {
+                const int XX = static_cast<int>(U);
+                const long long X1 = static_cast<long long>(XX) + inc;
+                const long long c1 = X1 >> fb;
+                if (!fin) {
+                    nonfinite = true;
+                    ++removed;
+                    xs[k] = -1;
+                    us[k] = 0.0f;
+                } else {
+                    const long long b0 = static_cast<long long>(c0) << fb;
+                    const long long f0a = min(max(static_cast<long long>(XX) - b0, 0LL), one);
+                    const long long f1a = min(max(X1 - b0, 0LL), one);
+                    const long long qa = shl_signed(f1a - f0a, sh);
+                    if (qa) acc_add(jacc + c0, qa);
+                    if (c1 != static_cast<long long>(c0) && c1 >= 0 && c1 < nz) {
+                        const long long b1 = c1 << fb;
+                        const long long f0b = min(max(static_cast<long long>(XX) - b1, 0LL), one);
+                        const long long f1b = min(max(X1 - b1, 0LL), one);
+                        const long long qb = shl_signed(f1b - f0b, sh);
+                        if (qb) acc_add(jacc + static_cast<int>(c1), qb);
+                    }
+                    // (a5) removal at the ends; base-cell weight for the next injection
+                    if (X1 >= 0 && X1 < top) {
+                        xs[k] = static_cast<int>(X1);
+                        us[k] = u1;
+                        if (c1 == 0) w0_acc += shl_signed(one - X1, sh);
+                    } else {
+                        ++removed;
+                        xs[k] = -1;
+                        us[k] = 0.0f;
+                    }
+                }
+            } else {
+                xs[k] = common ? static_cast<int>(U1) : xs[k];
+                us[k] = common ? u1 : us[k];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPPT; v += kVec) {
+            if (i0 + v < n_tot) {
+                vstore(a.X + i0 + v, xs + v);
+                vstore(a.u + i0 + v, us + v);
+            }
+        }
+        warp_flush<long long>(rkey == 0xffffffffu ? -1 : static_cast<int>(rkey),
+                              shl_signed(ra, sh), jacc);
+    }
+
+    __shared__ long long s_w0[kThreads / 32], s_rm[kThreads / 32];
+    __shared__ int s_nf;
+    if (threadIdx.x == 0) s_nf = 0;
+    __syncthreads();
+    if (nonfinite) s_nf = 1;
+    w0_acc = warp_sum(w0_acc);
+    removed = warp_sum(removed);
+    if ((threadIdx.x & 31) == 0) {
+        s_w0[threadIdx.x >> 5] = w0_acc;
+        s_rm[threadIdx.x >> 5] = removed;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long w = 0, r = 0;
+        for (int i = 0; i < kThreads / 32; ++i) { w += s_w0[i]; r += s_rm[i]; }
+        if (w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
+        if (r) atomicAdd(&st->acc_removed, static_cast<unsigned long long>(r));
+        if (s_nf) atomicOr(&st->flags, SCLF_FLAG_NONFINITE);
+    }
+}
+
+}  // namespace
+
+int push_fix32_grid_size(int device_sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_fix32_kernel, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * device_sms;
+}
+
+cudaError_t launch_push_fix32(const PushFixArgs& a, int grid, cudaStream_t s) {
+    push_fix32_kernel<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sclf

@@ -36,6 +36,7 @@ int derive(const tube_params* p, tube_derived* d) {
     if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64 && p->precision != SCLF_FIX32)
         return SCLF_EINVAL;
     if (p->precision == SCLF_FIX32 && p->accumulate != SCLF_ACC_FIXED64) return SCLF_EINVAL;
+    if (p->precision == SCLF_FIX32 && p->Nz < 16) return SCLF_EINVAL;   // per-thread runs fit int32
     if (p->accumulate != SCLF_ACC_FIXED64 && p->accumulate != SCLF_ACC_FP64) return SCLF_EINVAL;
     if (p->rho_gj_mode < SCLF_RHO_FLAT || p->rho_gj_mode > SCLF_RHO_USER) return SCLF_EINVAL;
     if (p->rho_gj_mode == SCLF_RHO_USER && !p->rho_gj_user) return SCLF_EINVAL;
