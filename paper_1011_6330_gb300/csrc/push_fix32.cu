@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
         // run key: the first slot's cell (0xffffffff for a hole: no run)
         const unsigned rkey = (k_tot > 0 && xs[0] >= 0) ? (static_cast<unsigned>(xs[0]) >> fb)
                                                         : 0xffffffffu;
-        int ra = 0;                                   // run sum in 2^-fb units
+        int ra = 0, rb = 0;       // run sums on cells rkey and rkey + 1, in 2^-fb units
 #pragma unroll
         for (int k = 0; k < kPPT; ++k) {
             const int X = xs[k];
@@ -89,11 +89,16 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
             // X1 = X + inc in 32-bit two's complement: with X < 2^31 and
             // |inc| < 2^fb, 0 <= X1 < Nz 2^fb exactly when U1 < Nz 2^fb
             const unsigned U1 = U + static_cast<unsigned>(inc);
-            const unsigned c0 = U >> fb;
-            // (a4) in-cell current fraction F_c(X1) - F_c(X) = X1 - X = inc
-            const bool common = lv & fin & (U1 < utop) & ((U1 >> fb) == c0) & (c0 != 0u) &
+            const unsigned c0 = U >> fb, c1u = U1 >> fb;
+            // (a4) staying in the cell: F_c0(X1) - F_c0(X) = inc; moving up one
+            // cell: F_c0 goes to 2^fb (adds 2^fb - (X mod 2^fb)) and F_c1 from 0
+            // to X1 mod 2^fb
+            const bool stay = c1u == c0, up = c1u == c0 + 1u;
+            const bool common = lv & fin & (U1 < utop) & (stay | up) & (c1u != 0u) &
                                 (c0 == rkey);
-            ra += common ? inc : 0;
+            const int q0 = stay ? inc : static_cast<int>((1u << fb) - (U & mask));
+            ra += common ? q0 : 0;
+            rb += (common & up) ? static_cast<int>(U1 & mask) : 0;
             if (lv & !common) {
                 const int XX = static_cast<int>(U);
                 const long long X1 = static_cast<long long>(XX) + inc;
@@ -139,8 +144,9 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
                 vstore(a.u + i0 + v, us + v);
             }
         }
-        warp_flush<long long>(rkey == 0xffffffffu ? -1 : static_cast<int>(rkey),
-                              shl_signed(ra, sh), jacc);
+        const int key = rkey == 0xffffffffu ? -1 : static_cast<int>(rkey);
+        warp_flush<long long>(key, shl_signed(ra, sh), jacc);
+        warp_flush<long long>(key >= 0 && key + 1 < nz ? key + 1 : -1, shl_signed(rb, sh), jacc);
     }
 
     __shared__ long long s_w0[kThreads / 32], s_rm[kThreads / 32];
