@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["gr1e8", "large"], default="gr1e8",
+    ap.add_argument("--workload", choices=["gr1e8", "large", "batch"], default="gr1e8",
                     help="gr1e8: P = 0.5 s frame-dragging tube, Nz = 65536, FP32 particles "
                          "(default); large: P = 0.1 s, B = 3e12 G, Nz = 2^20, 2^30 "
                          "fixed-point particles")
@@ -268,10 +268,129 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The death-line batch: 256 seeded pulsar tubes (flat and frame-dragging,
+    Nz 1024..16384, 1e5..2e6 FP32 particles each) stepped by batched launches;
+    reported next to the plain form (the same tubes stepped one at a time)."""
+    import torch
+    from paper_1011_6330_gb300 import binding as B
+    from paper_1011_6330_gb300 import synth, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    kws = workloads.death_line_batch(seed=rank_seed(rank))
+    params = [B.default_params(**kw) for kw in kws]
+    batch = B.Batch(params)
+    plain = [B.Tube(p) for p in params]
+    states = []
+    for i, kw in enumerate(kws):
+        d = batch.tubes[i].derived
+        gr = kw["rho_gj_mode"] == B.SCLF_RHO_GR
+        gfar = (d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"]) if gr
+                else math.sqrt(2.0) * d["Lambda0"])
+        eta = (lambda zz, r=d["R_over_Rstar"]: 1.0 + zz * r) if gr else None
+        z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar,
+                                    seed=rank_seed(rank) + i, eta_of_z=eta)
+        for t in (batch.tubes[i], plain[i]):
+            t.add_particles(z, u)
+            t.solve_fields()
+        if i == 1:
+            states.append((z, u))
+    batch.run(args.warmup)
+    torch.cuda.synchronize()
+    n0 = sum(t.status()["n_particles"] for t in batch.tubes)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    batch.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    batch.run(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tm = batch.timing()
+    batch.set_timing(False)
+    el_s = e0.elapsed_time(e1) * 1e-3
+    n1 = sum(t.status()["n_particles"] for t in batch.tubes)
+    work, el_s = combine_ranks(0.5 * (n0 + n1) * args.steps, el_s, device="cuda")
+    push_avg_ms = tm["push_ms"] / max(tm["n_steps"], 1)
+    slots = tm["particle_slots"] / max(tm["n_steps"], 1)
+    achieved = BYTES_PER_PARTICLE * slots / (push_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    # the plain form: the same tubes, one tube at a time
+    k_plain = min(args.steps, 128)
+    for t in plain:
+        t.run(args.warmup)
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for t in plain:
+        t.run(k_plain)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - p0
+    plain_value = 0.5 * (n0 + n1) * k_plain / plain_s
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as orc
+        kw = kws[1]
+        z, u = states[0]
+        d = plain[1].derived
+        o = orc.Tube(kw["Nz"], d["L"], d["dt"], np.full(kw["Nz"] + 1, d["rho0"]), d["s"],
+                     precision="f32", accumulate="fixed")
+        o.add_particles(z, u)
+        o.solve_fields()
+        o.step()
+        t0 = time.perf_counter()
+        steps = psteps = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            psteps += o.xi.size + o.injection_count()
+            o.step()
+            steps += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "tube 1 of the batch (flat rho_GJ, Nz=%d, %d particles), %d steps in %.1f s"
+                         % (kw["Nz"], z.size, steps, el)}
+    line = {
+        "metric": METRIC, "value": work / el_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "death_line_batch_256_tubes", "tubes": len(kws),
+                   "particles_total": int(n1), "cells_total": int(sum(kw["Nz"] for kw in kws)),
+                   "l2": "inputs larger than L2 (%.0f MB of particle state)" % (8e-6 * n1),
+                   "parallelism": "independent batch per GPU" if ws > 1 else "one batch"},
+        "plain_form": {"value": plain_value, "unit": UNIT, "steps": k_plain,
+                       "how": "the same 256 tubes, each stepped alone (tube_run, graphs)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "batch_push_kernel",
+                     "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
+                     "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
+                     "compact_ms_total": tm["compact_ms"],
+                     "bytes_per_launch": BYTES_PER_PARTICLE * slots},
+        "cpu_baseline": cpu, "e2e": None,
+        "gpu_launches": int(2 * tm["n_steps"] + tm["n_compactions"] * len(kws)),
+        "clocks": clk,
+        "status": {"check": int(max(t.check() for t in batch.tubes))},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    for t in plain:
+        t.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

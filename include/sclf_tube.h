@@ -256,6 +256,45 @@ int tube_set_timing(tube_t t, int enable);
 /* Accumulated timings since timing was enabled. Synchronises. */
 int tube_get_timing(tube_t t, tube_timing* out);
 
+/* ---- batches of independent tubes -------------------------------------------
+ * Many tubes (each its own pulsar: B, P, R, Nz, rho_GJ profile, particles)
+ * advanced together: every step is one particle launch over all tubes'
+ * tiles and one field launch over all tubes' cells (plus the per-tube
+ * compaction checks), so tubes of uneven Nz and particle count share the
+ * GPU. Each tube computes exactly what it would compute alone (Sec. 2 step
+ * for every tube). Batched tubes must use SCLF_FP32 particles and
+ * SCLF_ACC_FIXED64. */
+typedef struct sclf_batch* batch_t;   /* opaque, library-owned */
+
+/* Create n tubes from params[0..n-1] (host array) on one stream; the
+ * compaction interval and graph flag of params[0] apply to the batch.
+ * Synchronises. */
+int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* out);
+
+/* Destroy the batch and its tubes. */
+int batch_destroy(batch_t b);
+
+/* Number of tubes. */
+int batch_size(batch_t b, int32_t* n);
+
+/* The i-th tube: tube_add_particles, tube_solve_fields, tube_read_*,
+ * tube_status, tube_save/load_particles, tube_inject and tube_compact work
+ * on it; tube_step and tube_run return SCLF_ESTATE (the batch steps it). */
+int batch_tube(batch_t b, int32_t i, tube_t* out);
+
+/* One step of every tube. Asynchronous. */
+int batch_step(batch_t b);
+
+/* nsteps steps of every tube (replays a captured graph when timing is off).
+ * Asynchronous. */
+int batch_run(batch_t b, int64_t nsteps);
+
+/* Per-kernel event timing of the batched launches (as tube_set_timing). */
+int batch_set_timing(batch_t b, int enable);
+
+/* Accumulated timings; particle_slots sums over all tubes. Synchronises. */
+int batch_get_timing(batch_t b, tube_timing* out);
+
 /* ---- one pass without any device allocation --------------------------------
  * The paper has no counterpart to this call; it is here for users of the
  * library who cannot call cudaMalloc: an application whose own allocator has

@@ -86,6 +86,14 @@ SIGNATURES = {
     "tube_compact": (_i32, [_vp]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "batch_create": (_i32, [C.c_int32, C.POINTER(TubeParams), _vp, C.POINTER(_vp)]),
+    "batch_destroy": (_i32, [_vp]),
+    "batch_size": (_i32, [_vp, C.POINTER(C.c_int32)]),
+    "batch_tube": (_i32, [_vp, C.c_int32, C.POINTER(_vp)]),
+    "batch_step": (_i32, [_vp]),
+    "batch_run": (_i32, [_vp, _i64]),
+    "batch_set_timing": (_i32, [_vp, _i32]),
+    "batch_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
     "tube_push_deposit_static": (_i32, [_vp, _vp, _i64, _vp, C.c_int32, C.c_double,
                                          C.c_double, C.c_double, _vp, _vp, _vp]),
     "tube_strerror": (C.c_char_p, [_i32]),
@@ -291,9 +299,80 @@ class Tube:
         return {n: getattr(t, n) for n, _ in TubeTiming._fields_}
 
 
+class _TubeView(Tube):
+    """A tube that belongs to a batch (no workspace of its own)."""
+
+    def __init__(self, lib, handle, params):
+        self.lib = lib
+        self.params = params
+        self._ws = None
+        self.h = handle
+        d = TubeDerived()
+        _check(self.lib.tube_get_derived(self.h, C.byref(d)), "tube_get_derived")
+        self.derived = {n: getattr(d, n) for n, _ in TubeDerived._fields_}
+        self.nz = int(params.Nz)
+        self.fp64 = params.precision == SCLF_FP64
+        self.fix32 = params.precision == SCLF_FIX32
+
+    def close(self):           # the batch owns it
+        self.h = None
+
+
+class Batch:
+    """Independent tubes stepped together by batched launches."""
+
+    def __init__(self, params_list, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        n = len(params_list)
+        arr = (TubeParams * n)()
+        for i, p in enumerate(params_list):
+            arr[i] = p
+        self._params = list(params_list)      # keep user profiles alive
+        h = C.c_void_p()
+        _check(self.lib.batch_create(n, arr, C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "batch_create")
+        self.h = h
+        self.tubes = []
+        for i in range(n):
+            th = C.c_void_p()
+            _check(self.lib.batch_tube(self.h, i, C.byref(th)), "batch_tube")
+            self.tubes.append(_TubeView(self.lib, th, params_list[i]))
+
+    def step(self):
+        _check(self.lib.batch_step(self.h), "batch_step")
+
+    def run(self, n):
+        _check(self.lib.batch_run(self.h, int(n)), "batch_run")
+
+    def set_timing(self, enable):
+        _check(self.lib.batch_set_timing(self.h, 1 if enable else 0), "batch_set_timing")
+
+    def timing(self):
+        t = TubeTiming()
+        _check(self.lib.batch_get_timing(self.h, C.byref(t)), "batch_get_timing")
+        return {n: getattr(t, n) for n, _ in TubeTiming._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            for t in self.tubes:
+                t.h = None
+            self.lib.batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def header_functions(path=HEADER):
     """Names of the functions include/sclf_tube.h declares."""
     import re
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tube_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:tube|batch)_[a-z_]+)\s*\(", text)))

@@ -9,12 +9,11 @@ namespace {
 // ---------------------------------------------------------------------------
 // (a6): the field kernel, one thread per cell
 // ---------------------------------------------------------------------------
+// Cell j of one tube (0 <= j < Nz); cell 0 also commits the tube's step.
 template <class Real, int kAcc>
-__global__ void __launch_bounds__(256) field_kernel(const FieldArgs<Real> a) {
+__device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
     using AccT = typename AccType<kAcc>::T;
     const int nz = a.c.nz;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nz) return;
     AccT* jacc = static_cast<AccT*>(a.jacc);
     const AccT q = jacc[j];
     jacc[j] = AccT(0);
@@ -68,6 +67,34 @@ __global__ void __launch_bounds__(256) field_kernel(const FieldArgs<Real> a) {
     }
 }
 
+template <class Real, int kAcc>
+__global__ void __launch_bounds__(256) field_kernel(const FieldArgs<Real> a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.c.nz) return;
+    field_cell<Real, kAcc>(a, j);
+}
+
+// All tubes of a batch: one thread per cell of the batch's cell space.
+__global__ void __launch_bounds__(256)
+batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ cell_tube,
+                   int n_cells, int parity) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_cells) return;
+    const BatchTube& d = tubes[cell_tube[g]];
+    FieldArgs<float> a;
+    a.st = d.st;
+    a.ez = d.ez;
+    a.er_in = d.er[parity];
+    a.er_out = d.er[parity ^ 1];
+    a.b_in = d.b[parity];
+    a.b_out = d.b[parity ^ 1];
+    a.jacc = d.jacc;
+    a.jlast = d.jlast;
+    a.ez2 = d.ez2;
+    a.c = d.fc;
+    field_cell<float, kAccFixed>(a, g - d.cell0);
+}
+
 }  // namespace
 
 template <class Real>
@@ -75,6 +102,12 @@ cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate, cudaStream_t 
     const int grid = (a.c.nz + 255) / 256;
     if (accumulate == kAccFixed) field_kernel<Real, kAccFixed><<<grid, 256, 0, s>>>(a);
     else field_kernel<Real, kAccF64><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
+                               int parity, cudaStream_t s) {
+    batch_field_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(tubes, cell_tube, n_cells, parity);
     return cudaGetLastError();
 }
 

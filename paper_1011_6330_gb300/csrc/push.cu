@@ -11,133 +11,175 @@ namespace {
 // ---------------------------------------------------------------------------
 // (a1)-(a5): the particle kernel
 // ---------------------------------------------------------------------------
+template <class Real> struct PairOf { using T = float2; };
+template <> struct PairOf<double> { using T = double2; };
+
+// What one tile of one tube needs.
+template <class Real, class AccT>
+struct TileCtx {
+    Real* xi;
+    Real* u;
+    long long* ids;
+    const typename PairOf<Real>::T* tab;
+    AccT* jacc;
+    long long n_slots, n_tot, id0;
+    Real nzf, dt, cfl;
+    int nz;
+};
+
+// One tile of kThreads * kPPT slots: thread t owns slots [i0, i0 + kPPT).
+// Adds the tile's base weight, removals and non-finite flag to the caller's
+// counters.
 template <class Real, int kAcc>
-__global__ void __launch_bounds__(kThreads)
-push_kernel(const PushArgs<Real> a) {
+__device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<kAcc>::T>& c,
+                                          long long tile, long long& w0_acc, long long& removed,
+                                          bool& nonfinite) {
     using L = Layout<Real>;
     constexpr int kPPT = L::kPPT, kVec = L::kVec, kTile = L::kTile;
     using AccT = typename AccType<kAcc>::T;
-    AccT* __restrict__ jacc = static_cast<AccT*>(a.jacc);
+    using Pair = typename PairOf<Real>::T;
+    const Real nzf = c.nzf, dt = c.dt, cfl = c.cfl;
+    const int nz = c.nz;
+    const Pair* __restrict__ tab = c.tab;
+    AccT* __restrict__ jacc = c.jacc;
 
-    DevState* st = a.st;
-    const long long n_slots = st->n_slots;
-    const long long n_req = st->n_inj;
-    long long room = a.capacity - n_slots;
-    room = room > 0 ? room : 0;
-    const long long n_inj = n_req < room ? n_req : room;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->inj_done = n_inj;
-        st->slots_processed += static_cast<unsigned long long>(n_slots + n_inj);
-        if (n_inj < n_req) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+    const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
+    Real xs[kPPT], us[kPPT];
+#pragma unroll
+    for (int v = 0; v < kPPT; v += kVec) {
+        vload(c.xi + i0 + v, xs + v);
+        vload(c.u + i0 + v, us + v);
     }
-    const long long n_tot = n_slots + n_inj;
-    const long long id0 = st->total_injected;
-    const long long ntiles = (n_tot + kTile - 1) / kTile;
+    // slots [i0, i0 + k_real) hold particles or holes, [k_real, k_tot)
+    // are this step's new electrons, the rest is padding
+    const long long r_slots = c.n_slots - i0, r_tot = c.n_tot - i0;
+    const int k_real = r_slots <= 0 ? 0 : (r_slots >= kPPT ? kPPT : int(r_slots));
+    const int k_tot = r_tot <= 0 ? 0 : (r_tot >= kPPT ? kPPT : int(r_tot));
+    if (k_real < k_tot) {                        // (a1) new electrons at the base
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            if (k >= k_real && k < k_tot) {
+                xs[k] = Real(0);
+                us[k] = Real(0);
+                if (c.ids) c.ids[i0 + k] = c.id0 + (i0 + k - c.n_slots);
+            }
+        }
+    }
+    // The common particle stays inside the cell of the thread's first
+    // particle, away from the base cell and the top: its current
+    // fraction joins a per-thread run without any branch. Everything
+    // else (crossing a node, the base cell, leaving the tube, another
+    // cell, a non-finite result) takes the rare branch.
+    const Real rkey = r_floor(xs[0]);
+    AccT ra = AccT(0);
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+        const Real x = xs[k];
+        const bool lv = (k < k_tot) & (x >= Real(0)) & (x < nzf);   // holes carry xi < 0
+        const Real xx = lv ? x : Real(0);
+        // (a2) cloud-in-cell gather from the (E_{m-1/2}, E_{m+1/2}) table;
+        // 0 <= xx < Nz keeps m in [0, Nz]
+        const Real h = xx + Real(0.5);
+        const Real mf = r_floor(h);
+        const Real f = h - mf;
+        const Pair e = tab[static_cast<int>(mf)];
+        const Real ep = (Real(1) - f) * e.x + f * e.y;
+        // (a3) Eq. 1, q/m = -1, c = 1
+        const Real u1 = us[k] - ep * dt;
+        const Real g = r_sqrt(Real(1) + u1 * u1);
+        const Real x1 = xx + r_div(u1, g) * cfl;
+        // (a4) charge-conserving deposit into cells floor(x) and floor(x1)
+        const Real x0f = r_floor(xx);
+        const Real x1f = r_floor(x1);
+        const bool common = lv & (x1f == x0f) & (x1 >= Real(1)) & (x1 < nzf) & (x0f == rkey);
+        const AccT q0 = frac_acc_in_cell<kAcc>(xx, x1, x0f);
+        ra += common ? q0 : AccT(0);
+        if (lv & !common) {
+            if (!r_finite(x1)) {                 // a non-finite u1 makes x1 non-finite
+                nonfinite = true;
+                ++removed;
+                xs[k] = Real(-1);
+                us[k] = Real(0);
+            } else {
+                const int c0 = static_cast<int>(x0f);
+                AccT qa = q0;
+                if (x1f != x0f) {
+                    qa = frac_acc<kAcc>(xx, x1, c0);
+                    const int c1 = static_cast<int>(x1f);
+                    if (c1 >= 0 && c1 < nz) {
+                        const AccT q1 = frac_acc<kAcc>(xx, x1, c1);
+                        if (q1 != AccT(0)) acc_add(jacc + c1, q1);
+                    }
+                }
+                if (qa != AccT(0)) acc_add(jacc + c0, qa);
+                // (a5) removal at the ends; base-cell weight for the next injection
+                if (x1 >= Real(0) && x1 < nzf) {
+                    xs[k] = x1;
+                    us[k] = u1;
+                    if (x1 < Real(1)) w0_acc += to_fixed(Real(1) - x1);
+                } else {
+                    ++removed;
+                    xs[k] = Real(-1);
+                    us[k] = Real(0);
+                }
+            }
+        } else {
+            xs[k] = common ? x1 : xs[k];
+            us[k] = common ? u1 : us[k];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kPPT; v += kVec) {
+        if (i0 + v < c.n_tot) {
+            vstore(c.xi + i0 + v, xs + v);
+            vstore(c.u + i0 + v, us + v);
+        }
+    }
+    warp_flush<AccT>(rkey >= Real(0) ? static_cast<int>(rkey) : -1, ra, jacc);
+}
+
+// Injection bookkeeping of a step: the pending count clipped to the free
+// slots. The caller that owns the tube's first tile records it.
+__device__ __forceinline__ long long clipped_injection(const DevState* st, long long capacity) {
+    const long long n_slots = st->n_slots, n_req = st->n_inj;
+    long long room = capacity - n_slots;
+    room = room > 0 ? room : 0;
+    return n_req < room ? n_req : room;
+}
+__device__ __forceinline__ void record_injection(DevState* st, long long n_inj) {
+    st->inj_done = n_inj;
+    st->slots_processed += static_cast<unsigned long long>(st->n_slots + n_inj);
+    if (n_inj < st->n_inj) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+}
+
+template <class Real, int kAcc>
+__global__ void __launch_bounds__(kThreads)
+push_kernel(const PushArgs<Real> a) {
+    constexpr int kTile = Layout<Real>::kTile;
+    using AccT = typename AccType<kAcc>::T;
+    DevState* st = a.st;
+    const long long n_inj = clipped_injection(st, a.capacity);
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_injection(st, n_inj);
+    TileCtx<Real, AccT> c;
+    c.xi = a.xi;
+    c.u = a.u;
+    c.ids = a.ids;
+    c.tab = reinterpret_cast<const typename PairOf<Real>::T*>(a.ez2);
+    c.jacc = static_cast<AccT*>(a.jacc);
+    c.n_slots = st->n_slots;
+    c.n_tot = c.n_slots + n_inj;
+    c.id0 = st->total_injected;
+    c.nzf = a.nzf;
+    c.dt = a.dt;
+    c.cfl = a.cfl;
+    c.nz = a.nz;
+    const long long ntiles = (c.n_tot + kTile - 1) / kTile;
 
     long long w0_acc = 0;
     long long removed = 0;
     bool nonfinite = false;
-
-    const Real nzf = a.nzf, dt = a.dt, cfl = a.cfl;
-    const int nz = a.nz;
-    using Pair = typename std::conditional<std::is_same<Real, float>::value, float2, double2>::type;
-    const Pair* __restrict__ tab = reinterpret_cast<const Pair*>(a.ez2);
-
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
-        Real xs[kPPT], us[kPPT];
-#pragma unroll
-        for (int v = 0; v < kPPT; v += kVec) {
-            vload(a.xi + i0 + v, xs + v);
-            vload(a.u + i0 + v, us + v);
-        }
-        // slots [i0, i0 + k_real) hold particles or holes, [k_real, k_tot)
-        // are this step's new electrons, the rest is padding
-        const long long r_slots = n_slots - i0, r_tot = n_tot - i0;
-        const int k_real = r_slots <= 0 ? 0 : (r_slots >= kPPT ? kPPT : int(r_slots));
-        const int k_tot = r_tot <= 0 ? 0 : (r_tot >= kPPT ? kPPT : int(r_tot));
-        if (k_real < k_tot) {                        // (a1) new electrons at the base
-#pragma unroll
-            for (int k = 0; k < kPPT; ++k) {
-                if (k >= k_real && k < k_tot) {
-                    xs[k] = Real(0);
-                    us[k] = Real(0);
-                    if (a.ids) a.ids[i0 + k] = id0 + (i0 + k - n_slots);
-                }
-            }
-        }
-        // The common particle stays inside the cell of the thread's first
-        // particle, away from the base cell and the top: its current
-        // fraction joins a per-thread run without any branch. Everything
-        // else (crossing a node, the base cell, leaving the tube, another
-        // cell, a non-finite result) takes the rare branch.
-        const Real rkey = r_floor(xs[0]);
-        AccT ra = AccT(0);
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            const Real x = xs[k];
-            const bool lv = (k < k_tot) & (x >= Real(0)) & (x < nzf);   // holes carry xi < 0
-            const Real xx = lv ? x : Real(0);
-            // (a2) cloud-in-cell gather from the (E_{m-1/2}, E_{m+1/2}) table;
-            // 0 <= xx < Nz keeps m in [0, Nz]
-            const Real h = xx + Real(0.5);
-            const Real mf = r_floor(h);
-            const Real f = h - mf;
-            const Pair e = tab[static_cast<int>(mf)];
-            const Real ep = (Real(1) - f) * e.x + f * e.y;
-            // (a3) Eq. 1, q/m = -1, c = 1
-            const Real u1 = us[k] - ep * dt;
-            const Real g = r_sqrt(Real(1) + u1 * u1);
-            const Real x1 = xx + r_div(u1, g) * cfl;
-            // (a4) charge-conserving deposit into cells floor(x) and floor(x1)
-            const Real x0f = r_floor(xx);
-            const Real x1f = r_floor(x1);
-            const bool common = lv & (x1f == x0f) & (x1 >= Real(1)) & (x1 < nzf) & (x0f == rkey);
-            const AccT q0 = frac_acc_in_cell<kAcc>(xx, x1, x0f);
-            ra += common ? q0 : AccT(0);
-            if (lv & !common) {
-                if (!r_finite(x1)) {                 // a non-finite u1 makes x1 non-finite
-                    nonfinite = true;
-                    ++removed;
-                    xs[k] = Real(-1);
-                    us[k] = Real(0);
-                } else {
-                    const int c0 = static_cast<int>(x0f);
-                    AccT qa = q0;
-                    if (x1f != x0f) {
-                        qa = frac_acc<kAcc>(xx, x1, c0);
-                        const int c1 = static_cast<int>(x1f);
-                        if (c1 >= 0 && c1 < nz) {
-                            const AccT q1 = frac_acc<kAcc>(xx, x1, c1);
-                            if (q1 != AccT(0)) acc_add(jacc + c1, q1);
-                        }
-                    }
-                    if (qa != AccT(0)) acc_add(jacc + c0, qa);
-                    // (a5) removal at the ends; base-cell weight for the next injection
-                    if (x1 >= Real(0) && x1 < nzf) {
-                        xs[k] = x1;
-                        us[k] = u1;
-                        if (x1 < Real(1)) w0_acc += to_fixed(Real(1) - x1);
-                    } else {
-                        ++removed;
-                        xs[k] = Real(-1);
-                        us[k] = Real(0);
-                    }
-                }
-            } else {
-                xs[k] = common ? x1 : xs[k];
-                us[k] = common ? u1 : us[k];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < kPPT; v += kVec) {
-            if (i0 + v < n_tot) {
-                vstore(a.xi + i0 + v, xs + v);
-                vstore(a.u + i0 + v, us + v);
-            }
-        }
-        warp_flush<AccT>(rkey >= Real(0) ? static_cast<int>(rkey) : -1, ra, jacc);
-    }
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        push_tile<Real, kAcc>(c, tile, w0_acc, removed, nonfinite);
 
     // block totals of the removal count and W_0
     __shared__ long long s_w0[kThreads / 32], s_rm[kThreads / 32];
@@ -162,6 +204,59 @@ push_kernel(const PushArgs<Real> a) {
 }
 
 
+
+// ---------------------------------------------------------------------------
+// The same step for a batch of independent tubes (FP32 particles, fixed-point
+// current) in one launch: persistent CTAs walk the batch's tile space, every
+// tile belongs to one tube and is pushed with that tube's constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void flush_tube_counters(DevState* st, long long& w0, long long& rm,
+                                                    bool& nf) {
+    const unsigned any = __ballot_sync(kFull, (w0 != 0) | (rm != 0) | nf);
+    if (any) {
+        const long long w = warp_sum(w0), r = warp_sum(rm);
+        if ((threadIdx.x & 31) == 0) {
+            if (w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
+            if (r) atomicAdd(&st->acc_removed, static_cast<unsigned long long>(r));
+        }
+        if (nf) atomicOr(&st->flags, SCLF_FLAG_NONFINITE);
+    }
+    w0 = 0;
+    rm = 0;
+    nf = false;
+}
+
+__global__ void __launch_bounds__(kThreads, 4)
+batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
+                  long long n_tiles) {
+    constexpr int kTile = Layout<float>::kTile;
+    long long w0 = 0, removed = 0;
+    bool nonfinite = false;
+    for (long long g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+        const BatchTube& d = tubes[tile_tube[g]];
+        DevState* st = d.st;
+        const long long local = g - d.tile0;
+        const long long n_inj = clipped_injection(st, d.capacity);
+        if (local == 0 && threadIdx.x == 0) record_injection(st, n_inj);
+        TileCtx<float, long long> c;
+        c.n_slots = st->n_slots;
+        c.n_tot = c.n_slots + n_inj;
+        if (local * kTile >= c.n_tot) continue;          // the same for the whole CTA
+        c.xi = d.xi;
+        c.u = d.u;
+        c.ids = d.ids;
+        c.tab = reinterpret_cast<const float2*>(d.ez2);
+        c.jacc = d.jacc;
+        c.id0 = st->total_injected;
+        c.nzf = d.nzf;
+        c.dt = d.dt;
+        c.cfl = d.cfl;
+        c.nz = d.nz;
+        push_tile<float, kAccFixed>(c, local, w0, removed, nonfinite);
+        flush_tube_counters(st, w0, removed, nonfinite);
+    }
+}
+
 }  // namespace
 
 template <class Real>
@@ -179,6 +274,19 @@ template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid, cudaStream_t s) {
     if (accumulate == kAccFixed) push_kernel<Real, kAccFixed><<<grid, kThreads, 0, s>>>(a);
     else push_kernel<Real, kAccF64><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_push_grid_size(int device_sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_push_kernel, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * device_sms;
+}
+
+cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
+                              int grid, cudaStream_t s) {
+    batch_push_kernel<<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles);
     return cudaGetLastError();
 }
 

@@ -134,7 +134,28 @@ struct CompactArgs {
     int force;                       // 0: only when holes or capacity call for it
 };
 
-// Launchers (kernels.cu). All return cudaGetLastError() after the launch.
+// One tube of a batch, as the batched kernels see it (FP32 particles,
+// fixed-point current).
+struct BatchTube {
+    DevState* st;
+    float* xi;
+    float* u;
+    long long* ids;
+    float* ez2;                // gather table (read by the particle kernel, written by the field kernel)
+    long long* jacc;
+    long long capacity;
+    long long tile0;           // first tile of this tube in the batch's tile space
+    int nz;
+    int cell0;                 // first cell of this tube in the batch's cell space
+    float nzf, dt, cfl;
+    double* ez;
+    double* er[2];
+    double* b[2];
+    double* jlast;
+    FieldConsts fc;
+};
+
+// Launchers. All return cudaGetLastError() after the launch.
 template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid,
                         cudaStream_t s);
@@ -144,6 +165,11 @@ template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
                          cudaStream_t s);
 cudaError_t launch_push_fix32(const PushFixArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
+                              int grid, cudaStream_t s);
+int batch_push_grid_size(int device_sms);
+cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
+                               int parity, cudaStream_t s);
 int push_fix32_grid_size(int device_sms);
 template <class Pos, class Mom>
 cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s);

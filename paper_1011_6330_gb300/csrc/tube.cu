@@ -100,6 +100,7 @@ struct sclf_tube {
     int ev_next = 0;
     tube_timing acc{};
     unsigned long long slots_base = 0;
+    bool in_batch = false;             // stepped by its batch, not on its own
 };
 
 namespace {
@@ -668,11 +669,13 @@ int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
 
 int tube_step(tube_t t) {
     if (!t) return SCLF_EINVAL;
+    if (t->in_batch) return SCLF_ESTATE;
     return one_step(t);
 }
 
 int tube_run(tube_t t, int64_t nsteps) {
     if (!t || nsteps < 0) return SCLF_EINVAL;
+    if (t->in_batch) return SCLF_ESTATE;
     while (nsteps > 0) {
         if (t->p.use_graphs && (t->host_step & 1) == 0 &&
             t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
@@ -907,5 +910,322 @@ const char* tube_strerror(int code) {
 }
 
 const char* tube_version(void) { return "sclf_tube 0.1.0 sm_103a"; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many independent tubes advanced by one particle launch and one
+// field launch per step.
+// ===========================================================================
+struct sclf_batch {
+    std::vector<sclf_tube*> tubes;
+    cudaStream_t stream = nullptr;
+    cudaStream_t gstream = nullptr;
+    bool own_gstream = false;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    BatchTube* d_desc = nullptr;
+    int* d_tile_tube = nullptr;
+    int* d_cell_tube = nullptr;
+    long long n_tiles = 0;
+    int n_cells = 0;
+    int push_grid = 0;
+    int64_t host_step = 0;
+    int steps_since_compact = 0;
+    int compact_every = 64;
+    int chunk_steps = 64;
+    cudaGraphExec_t chunk = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // 3 per step, 2 per compaction round
+    std::vector<std::pair<int, int>> recs;
+    int ev_next = 0;
+    tube_timing acc{};
+    std::vector<unsigned long long> slots_base;
+};
+
+namespace {
+
+int batch_enqueue_step(sclf_batch* b, cudaStream_t s, int parity) {
+    CK(launch_batch_push(b->d_desc, b->d_tile_tube, b->n_tiles, b->push_grid, s));
+    CK(launch_batch_field(b->d_desc, b->d_cell_tube, b->n_cells, parity, s));
+    return SCLF_OK;
+}
+
+int batch_enqueue_compaction(sclf_batch* b, cudaStream_t s) {
+    for (sclf_tube* t : b->tubes) CK(enqueue_compact(t, s, 0));
+    return SCLF_OK;
+}
+
+void batch_advance(sclf_batch* b, int64_t n) {
+    b->host_step += n;
+    for (sclf_tube* t : b->tubes) t->host_step += n;
+}
+
+int batch_drain(sclf_batch* b) {
+    CK(cudaStreamSynchronize(b->stream));
+    for (const auto& r : b->recs) {
+        float ms = 0.f;
+        if (r.first == 0) {
+            CK(cudaEventElapsedTime(&ms, b->ev[r.second], b->ev[r.second + 1]));
+            b->acc.push_ms += ms;
+            CK(cudaEventElapsedTime(&ms, b->ev[r.second + 1], b->ev[r.second + 2]));
+            b->acc.field_ms += ms;
+            b->acc.n_steps += 1;
+        } else {
+            CK(cudaEventElapsedTime(&ms, b->ev[r.second], b->ev[r.second + 1]));
+            b->acc.compact_ms += ms;
+            b->acc.n_compactions += 1;
+        }
+    }
+    b->recs.clear();
+    b->ev_next = 0;
+    return SCLF_OK;
+}
+
+int batch_reserve(sclf_batch* b, int k) {
+    if (b->ev_next + k > static_cast<int>(b->ev.size()))
+        if (batch_drain(b) != SCLF_OK) return -1;
+    if (b->ev_next + k > static_cast<int>(b->ev.size())) return -1;
+    const int e0 = b->ev_next;
+    b->ev_next += k;
+    return e0;
+}
+
+int batch_one_step(sclf_batch* b) {
+    const int parity = static_cast<int>(b->host_step & 1);
+    if (b->timing) {
+        const int e0 = batch_reserve(b, 3);
+        if (e0 < 0) return SCLF_ECUDA;
+        CK(cudaEventRecord(b->ev[e0], b->stream));
+        CK(launch_batch_push(b->d_desc, b->d_tile_tube, b->n_tiles, b->push_grid, b->stream));
+        CK(cudaEventRecord(b->ev[e0 + 1], b->stream));
+        CK(launch_batch_field(b->d_desc, b->d_cell_tube, b->n_cells, parity, b->stream));
+        CK(cudaEventRecord(b->ev[e0 + 2], b->stream));
+        b->recs.push_back({0, e0});
+    } else {
+        const int rc = batch_enqueue_step(b, b->stream, parity);
+        if (rc) return rc;
+    }
+    batch_advance(b, 1);
+    if (++b->steps_since_compact >= b->compact_every) {
+        int e0 = -1;
+        if (b->timing) {
+            e0 = batch_reserve(b, 2);
+            if (e0 < 0) return SCLF_ECUDA;
+            CK(cudaEventRecord(b->ev[e0], b->stream));
+        }
+        const int rc = batch_enqueue_compaction(b, b->stream);
+        if (rc) return rc;
+        if (b->timing) {
+            CK(cudaEventRecord(b->ev[e0 + 1], b->stream));
+            b->recs.push_back({1, e0});
+        }
+        b->steps_since_compact = 0;
+    }
+    return SCLF_OK;
+}
+
+int batch_build_chunk(sclf_batch* b) {
+    if (b->chunk) return SCLF_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+    int rc = SCLF_OK;
+    for (int k = 0; k < b->chunk_steps && rc == SCLF_OK; ++k) rc = batch_enqueue_step(b, b->gstream, k & 1);
+    if (rc == SCLF_OK) rc = batch_enqueue_compaction(b, b->gstream);
+    const cudaError_t e2 = cudaStreamEndCapture(b->gstream, &g);
+    if (rc != SCLF_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(e2);
+    const cudaError_t e = cudaGraphInstantiate(&b->chunk, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return SCLF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* out) {
+    if (!out || n <= 0 || !params) return SCLF_EINVAL;
+    *out = nullptr;
+    for (int32_t i = 0; i < n; ++i)
+        if (params[i].precision != SCLF_FP32 || params[i].accumulate != SCLF_ACC_FIXED64)
+            return SCLF_EINVAL;
+    sclf_batch* b = new (std::nothrow) sclf_batch();
+    if (!b) return SCLF_ENOMEM;
+    b->stream = static_cast<cudaStream_t>(stream);
+    auto fail = [&](int code) { batch_destroy(b); return code; };
+    std::vector<BatchTube> desc(n);
+    std::vector<int> tile_tube, cell_tube;
+    long long tiles = 0;
+    long long cells = 0;
+    b->compact_every = params[0].compact_interval > 0 ? params[0].compact_interval : 64;
+    b->chunk_steps = b->compact_every + (b->compact_every & 1);
+    for (int32_t i = 0; i < n; ++i) {
+        tube_t t = nullptr;
+        const int rc = tube_create(&params[i], nullptr, 0, stream, &t);
+        if (rc) return fail(rc);
+        t->in_batch = true;
+        b->tubes.push_back(t);
+        BatchTube& d = desc[i];
+        d.st = t->st;
+        d.xi = static_cast<float*>(t->xi);
+        d.u = static_cast<float*>(t->u);
+        d.ids = t->ids;
+        d.ez2 = static_cast<float*>(t->ez2);
+        d.jacc = static_cast<long long*>(t->jacc);
+        d.capacity = t->p.capacity;
+        d.tile0 = tiles;
+        d.nz = static_cast<int>(t->p.Nz);
+        d.cell0 = static_cast<int>(cells);
+        d.nzf = static_cast<float>(t->p.Nz);
+        d.dt = static_cast<float>(t->d.dt);
+        d.cfl = static_cast<float>(t->d.dt / t->d.dz);
+        d.ez = t->ez;
+        d.er[0] = t->er[0];
+        d.er[1] = t->er[1];
+        d.b[0] = t->b[0];
+        d.b[1] = t->b[1];
+        d.jlast = t->jlast;
+        d.fc = t->fc;
+        const long long nt = t->lay.cap_pad / Layout<float>::kTile;
+        tile_tube.insert(tile_tube.end(), static_cast<size_t>(nt), i);
+        cell_tube.insert(cell_tube.end(), static_cast<size_t>(t->p.Nz), i);
+        tiles += nt;
+        cells += t->p.Nz;
+        if (cells >= (1LL << 31)) return fail(SCLF_EINVAL);
+    }
+    b->n_tiles = tiles;
+    b->n_cells = static_cast<int>(cells);
+    if (cudaMalloc(&b->d_desc, sizeof(BatchTube) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_tile_tube, sizeof(int) * tiles) != cudaSuccess ||
+        cudaMalloc(&b->d_cell_tube, sizeof(int) * cells) != cudaSuccess)
+        return fail(SCLF_ENOMEM);
+    if (cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(BatchTube) * n, cudaMemcpyHostToDevice, b->stream) ||
+        cudaMemcpyAsync(b->d_tile_tube, tile_tube.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, b->stream) ||
+        cudaMemcpyAsync(b->d_cell_tube, cell_tube.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, b->stream) ||
+        cudaStreamSynchronize(b->stream))
+        return fail(SCLF_ECUDA);
+    const int sms = b->tubes[0]->sms;
+    b->push_grid = batch_push_grid_size(sms);
+    if (b->push_grid > tiles) b->push_grid = static_cast<int>(tiles);
+    if (b->stream) {
+        b->gstream = b->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(SCLF_ECUDA);
+        b->own_gstream = true;
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(SCLF_ECUDA);
+    *out = b;
+    return SCLF_OK;
+}
+
+int batch_destroy(batch_t b) {
+    if (!b) return SCLF_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    if (b->chunk) cudaGraphExecDestroy(b->chunk);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->own_gstream && b->gstream) {
+        cudaStreamSynchronize(b->gstream);
+        cudaStreamDestroy(b->gstream);
+    }
+    for (sclf_tube* t : b->tubes) tube_destroy(t);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_tile_tube) cudaFree(b->d_tile_tube);
+    if (b->d_cell_tube) cudaFree(b->d_cell_tube);
+    delete b;
+    return SCLF_OK;
+}
+
+int batch_size(batch_t b, int32_t* n) {
+    if (!b || !n) return SCLF_EINVAL;
+    *n = static_cast<int32_t>(b->tubes.size());
+    return SCLF_OK;
+}
+
+int batch_tube(batch_t b, int32_t i, tube_t* out) {
+    if (!b || !out || i < 0 || i >= static_cast<int32_t>(b->tubes.size())) return SCLF_EINVAL;
+    *out = b->tubes[i];
+    return SCLF_OK;
+}
+
+int batch_step(batch_t b) {
+    if (!b) return SCLF_EINVAL;
+    return batch_one_step(b);
+}
+
+int batch_run(batch_t b, int64_t nsteps) {
+    if (!b || nsteps < 0) return SCLF_EINVAL;
+    while (nsteps > 0) {
+        if (!b->timing && (b->host_step & 1) == 0 && b->steps_since_compact == 0 &&
+            nsteps >= b->chunk_steps && b->tubes[0]->p.use_graphs) {
+            int rc = batch_build_chunk(b);
+            if (rc) return rc;
+            if (b->gstream != b->stream) {
+                CK(cudaEventRecord(b->fork, b->stream));
+                CK(cudaStreamWaitEvent(b->gstream, b->fork, 0));
+            }
+            CK(cudaGraphLaunch(b->chunk, b->gstream));
+            if (b->gstream != b->stream) {
+                CK(cudaEventRecord(b->join, b->gstream));
+                CK(cudaStreamWaitEvent(b->stream, b->join, 0));
+            }
+            batch_advance(b, b->chunk_steps);
+            nsteps -= b->chunk_steps;
+            continue;
+        }
+        const int rc = batch_one_step(b);
+        if (rc) return rc;
+        nsteps -= 1;
+    }
+    return SCLF_OK;
+}
+
+int batch_set_timing(batch_t b, int enable) {
+    if (!b) return SCLF_EINVAL;
+    if (enable) {
+        if (b->ev.empty()) {
+            b->ev.resize(3 * 2048 + 8, nullptr);
+            for (auto& e : b->ev)
+                if (cudaEventCreate(&e) != cudaSuccess) return SCLF_ECUDA;
+        }
+        CK(cudaStreamSynchronize(b->stream));
+        b->recs.clear();
+        b->ev_next = 0;
+        std::memset(&b->acc, 0, sizeof(b->acc));
+        b->slots_base.clear();
+        for (sclf_tube* t : b->tubes) {
+            DevState h;
+            const int rc = read_state(t, &h);
+            if (rc) return rc;
+            b->slots_base.push_back(h.slots_processed);
+        }
+        b->timing = true;
+        return SCLF_OK;
+    }
+    const int rc = batch_drain(b);
+    b->timing = false;
+    return rc;
+}
+
+int batch_get_timing(batch_t b, tube_timing* out) {
+    if (!b || !out) return SCLF_EINVAL;
+    int rc = batch_drain(b);
+    if (rc) return rc;
+    *out = b->acc;
+    int64_t slots = 0;
+    for (size_t i = 0; i < b->tubes.size(); ++i) {
+        DevState h;
+        rc = read_state(b->tubes[i], &h);
+        if (rc) return rc;
+        slots += static_cast<int64_t>(h.slots_processed - (i < b->slots_base.size() ? b->slots_base[i] : 0));
+    }
+    out->particle_slots = slots;
+    return SCLF_OK;
+}
 
 }  // extern "C"

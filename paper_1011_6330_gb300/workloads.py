@@ -52,3 +52,33 @@ def large_tube(n_particles=2 ** 30, Nz=2 ** 20, capacity=None, track_ids=0):
                    n_particles=n_particles, capacity=capacity,
                    precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64,
                    track_ids=track_ids)
+
+
+def death_line_batch(n_tubes=256, seed=0, nz_min=1024, nz_max=16384, n_min=10 ** 5,
+                     n_max=2 * 10 ** 6):
+    """Batch of independent pulsar tubes for death-line / pair-front sweeps:
+    P log-uniform in [0.03, 3] s, B log-uniform in [1e11, 1e13] G (seeded),
+    frame-dragging rho_GJ (i = 0.5) for even tubes and flat (i = 0) for odd
+    ones, tube length 2 R_*; Nz grows with the tube length (in R) from
+    nz_min to nz_max (log scale, multiple of 64) and the particle count with
+    Nz from n_min to n_max. Returns a list of keyword dicts."""
+    rng = np.random.default_rng(seed)
+    P = 10.0 ** rng.uniform(math.log10(0.03), math.log10(3.0), n_tubes)
+    Bf = 10.0 ** rng.uniform(11.0, 13.0, n_tubes)
+    c = 2.99792458e10
+    L = [2.0 / math.sqrt(2.0 * math.pi / p * 1e6 / c) for p in P]
+    lmin, lmax = 2.0 / math.sqrt(2.0 * math.pi / 0.03 * 1e6 / c), 2.0 / math.sqrt(2.0 * math.pi / 3.0 * 1e6 / c)
+    out = []
+    for i in range(n_tubes):
+        frac = (math.log(L[i]) - math.log(lmin)) / (math.log(lmax) - math.log(lmin))
+        nz = int(round(nz_min * (nz_max / nz_min) ** frac / 64.0)) * 64
+        nz = min(max(nz, nz_min), nz_max)
+        npart = int(n_min * (n_max / n_min) ** ((math.log(nz) - math.log(nz_min)) /
+                                                (math.log(nz_max) - math.log(nz_min))))
+        gr = i % 2 == 0
+        kw = gr_tube(B_G=float(Bf[i]), P_s=float(P[i]), incl=0.5 if gr else 0.0, Nz=nz,
+                     n_particles=npart, capacity=int(npart * 1.05) + 8192)
+        kw["rho_gj_mode"] = B.SCLF_RHO_GR if gr else B.SCLF_RHO_FLAT
+        kw["compact_interval"] = 64
+        out.append(kw)
+    return out

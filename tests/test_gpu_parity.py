@@ -380,3 +380,87 @@ def test_large_fix32_tube_step_against_oracle_on_all_particles(gpu_lib):
     assert st["pending_injection"] == n_next
     assert t.check() == 0
     t.close()
+
+
+# ---------------------------------------------------------------------------
+# Batches of independent tubes
+# ---------------------------------------------------------------------------
+
+def _small_batch_params():
+    """Five uneven tubes: flat and frame-dragging, Nz from 64 to 4096."""
+    specs = [(1e12, 0.5, 0.5, 64, 3000), (3e11, 1.3, 0.0, 200, 9000),
+             (2e12, 0.2, 0.5, 1024, 20000), (5e12, 2.0, 0.0, 333, 1000),
+             (1e11, 0.05, 0.5, 4096, 12000)]
+    out = []
+    for i, (Bg, P, incl, nz, n) in enumerate(specs):
+        kw = workloads.gr_tube(B_G=Bg, P_s=P, incl=incl, Nz=nz, n_particles=n,
+                               capacity=n + 4096, track_ids=1)
+        kw["rho_gj_mode"] = B.SCLF_RHO_GR if incl > 0 else B.SCLF_RHO_FLAT
+        kw["compact_interval"] = 7
+        out.append(kw)
+    return out
+
+
+def _fill(t, kw, seed):
+    d = t.derived
+    gfar = 3.0 * d["Lambda0"]
+    z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar, seed=seed)
+    t.add_particles(z, u)
+    t.solve_fields()
+
+
+def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
+    kws = _small_batch_params()
+    batch = B.Batch([B.default_params(**kw) for kw in kws])
+    alone = [B.Tube(B.default_params(**kw)) for kw in kws]
+    for i, kw in enumerate(kws):
+        _fill(batch.tubes[i], kw, seed=i)
+        _fill(alone[i], kw, seed=i)
+    with pytest.raises(B.SclfError) as e:
+        batch.tubes[0].step()
+    assert e.value.code == -7                   # a batch member is stepped by its batch
+    batch.run(40)
+    batch.step()
+    batch.run(25)
+    for t in alone:
+        t.run(66)
+    for i in range(len(kws)):
+        a, b = batch.tubes[i], alone[i]
+        sa, sb = a.status(), b.status()
+        for k in ("step", "n_particles", "total_injected", "last_injected", "last_removed",
+                  "pending_injection", "flags"):
+            assert sa[k] == sb[k], (i, k)
+        pa, pb = a.read_particles(), b.read_particles()
+        for x, y in zip(pa, pb):
+            assert np.array_equal(x, y), i
+        fa, fb = a.read_fields(rho=False), b.read_fields(rho=False)
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(fa[k], fb[k]), (i, k)
+    # and two of the tubes against the oracle, step by step
+    batch2 = B.Batch([B.default_params(**kws[0]), B.default_params(**kws[3])])
+    oracles = []
+    for t, kw, seed in zip(batch2.tubes, (kws[0], kws[3]), (0, 3)):
+        cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+        zn = np.arange(kw["Nz"] + 1) * (kw["L_over_R"] / kw["Nz"])
+        mode = orc.RHO_GR if kw["rho_gj_mode"] == B.SCLF_RHO_GR else orc.RHO_FLAT
+        rho = orc.rho_gj_profile(mode, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                                 cu["R_over_Rstar"], cu["kappa"])
+        d = t.derived
+        o = orc.Tube(kw["Nz"], kw["L_over_R"], d["dt"], rho, d["s"], precision="f32",
+                     accumulate="fixed")
+        z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], 3.0 * d["Lambda0"],
+                                    seed=seed)
+        t.add_particles(z, u)
+        t.solve_fields()
+        o.add_particles(z, u)
+        o.solve_fields()
+        oracles.append(o)
+    for n in range(30):
+        batch2.step()
+        for t, o in zip(batch2.tubes, oracles):
+            o.step()
+            compare(t, o, TOL[B.SCLF_FP32], "batch step %d" % n)
+    batch.close()
+    batch2.close()
+    for t in alone:
+        t.close()
