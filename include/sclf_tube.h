@@ -295,6 +295,93 @@ int batch_set_timing(batch_t b, int enable);
 /* Accumulated timings; particle_slots sums over all tubes. Synchronises. */
 int batch_get_timing(batch_t b, tube_timing* out);
 
+/* ---- discrete adjoint of a run: gradients ------------------------------------
+ * An adjoint driver owns one tube (SCLF_FP32 or SCLF_FP64 particles,
+ * SCLF_ACC_FIXED64 current) and differentiates an N-step run of it (the
+ * Sec. 2 step of Figure A) that starts from the particles the tube holds at
+ * the first adjoint_forward, with fields solving Eq. 4 for their charge
+ * (as tube_solve_fields). The inputs it differentiates are rho_GJ at the
+ * nodes (which enters through the t = 0 fields of Eq. 4) and the
+ * macro-particle charge s (which enters the current J = (s/dt) sum F and
+ * the charge of the particles at t = 0). Held fixed: the number of
+ * electrons injected at each step (recorded by the forward pass, or given by
+ * adjoint_set_injections), the grid (L, Nz, dt in code units) and the
+ * rounding of the particle precision. The piecewise-linear gather and
+ * deposit are differentiated inside their pieces (dF_j/dx = 1 on cell j).
+ * Particles keep their slots for the whole run (no compaction).
+ *
+ * The forward pass stores the state at every checkpoint_every-th step; the
+ * backward pass recomputes each segment from its checkpoint with the
+ * recorded injections, keeping every step of that one segment, and sweeps
+ * it in reverse (transposed Eq. 3 on the grid in FP64, then per particle
+ * the adjoints of the deposit, the Eq. 1 push and the gather, in the
+ * particle precision, their grid sums in FP64). */
+typedef struct sclf_adjoint* adjoint_t;   /* opaque, library-owned */
+
+#define SCLF_OBJ_GAMMA 0   /* mean gamma = sqrt(1 + u^2) over the live particles
+                              after the last step                            */
+#define SCLF_OBJ_EZ    1   /* ||E_z||_2 = sqrt(sum_j E_z,j^2 dz) after the last
+                              step                                           */
+
+/* Create a driver for runs of nsteps steps (> 0, a multiple of
+ * checkpoint_every, which is even and > 0) of a tube with parameters p
+ * (track_ids is ignored). Device memory: about checkpoint_every +
+ * nsteps / checkpoint_every + 5 copies of the particle arrays
+ * (2 * capacity * 4 or 8 bytes each) and checkpoint_every grid copies.
+ * SCLF_EINVAL for another precision or accumulation, SCLF_ENOMEM when it
+ * does not fit. Work goes to the tube's stream (stream, or a stream of its
+ * own when NULL). Synchronises. */
+int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_every,
+                   void* stream, adjoint_t* out);
+
+/* Destroy the driver and its tube. */
+int adjoint_destroy(adjoint_t a);
+
+/* The driver's tube: fill it (tube_add_particles, tube_load_particles,
+ * tube_inject) before the first adjoint_forward; after a forward pass its
+ * particles, fields and counters are those at the end of the run (read
+ * them with tube_read_*, tube_status). tube_step and tube_run return
+ * SCLF_ESTATE on it. The driver keeps ownership. */
+int adjoint_tube(adjoint_t a, tube_t* out);
+
+/* n_inj: host, nsteps counts that the forward pass injects instead of the
+ * tube's own choice (replaying another run's events), or NULL to return
+ * to the tube's own rule. A negative count is SCLF_EINVAL. */
+int adjoint_set_injections(adjoint_t a, const int64_t* n_inj);
+
+/* Run the nsteps steps from the initial state (the tube's particles at the
+ * first call), storing checkpoints and the per-step events. values: host,
+ * 2 doubles or NULL, receives the objectives SCLF_OBJ_GAMMA and
+ * SCLF_OBJ_EZ. Synchronises. */
+int adjoint_forward(adjoint_t a, double* values);
+
+/* Per-step events of the last forward pass into host arrays of nsteps
+ * (each may be NULL): electrons injected, particles removed (left the tube
+ * or became non-finite) and slots in use before the step. SCLF_ESTATE
+ * before the first forward pass. Synchronises. */
+int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_slots);
+
+/* Gradient of one objective of the last forward pass: d_rho_gj (host,
+ * Nz+1 doubles or NULL) = d objective / d rho_GJ at the nodes (node 0 is
+ * 0: it enters only the frozen injection count), d_s (host or NULL) =
+ * d objective / d s. SCLF_ESTATE before the first forward pass.
+ * Synchronises. */
+int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s);
+
+/* Chain a gradient to the pulsar's parameters: grad (host, 4 doubles) =
+ * d objective / d(B_G, P_s, R_cm, w), where the macro charge is w s (w = 1
+ * at this point). rho_GJ is differentiated in B, P and R on the fixed grid
+ * by central differences (relative step 1e-6) of its closed form (Eq. 5, or
+ * Eq. 6-7), with R an independent coordinate taken at its derived value;
+ * a SCLF_RHO_USER profile gives 0 for B, P and R. */
+int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double* grad);
+
+/* Device time (CUDA events on the driver's stream) of the last forward and
+ * backward passes, and the particle slots one pass processes (the sum over
+ * steps of the slots in use plus the electrons injected). */
+int adjoint_timing(adjoint_t a, double* forward_ms, double* backward_ms,
+                   int64_t* particle_steps);
+
 /* ---- one pass without any device allocation --------------------------------
  * The paper has no counterpart to this call; it is here for users of the
  * library who cannot call cudaMalloc: an application whose own allocator has

@@ -22,6 +22,7 @@ SCLF_RHO_FLAT, SCLF_RHO_GR, SCLF_RHO_USER = 0, 1, 2
 SCLF_FP32, SCLF_FP64, SCLF_FIX32 = 0, 1, 2
 SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
 FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
+SCLF_OBJ_GAMMA, SCLF_OBJ_EZ = 0, 1
 
 
 class TubeParams(C.Structure):
@@ -94,6 +95,15 @@ SIGNATURES = {
     "batch_run": (_i32, [_vp, _i64]),
     "batch_set_timing": (_i32, [_vp, _i32]),
     "batch_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "adjoint_create": (_i32, [C.POINTER(TubeParams), _i64, C.c_int32, _vp, C.POINTER(_vp)]),
+    "adjoint_destroy": (_i32, [_vp]),
+    "adjoint_tube": (_i32, [_vp, C.POINTER(_vp)]),
+    "adjoint_set_injections": (_i32, [_vp, _pi64]),
+    "adjoint_forward": (_i32, [_vp, _pd]),
+    "adjoint_events": (_i32, [_vp, _pi64, _pi64, _pi64]),
+    "adjoint_backward": (_i32, [_vp, C.c_int32, _pd, _pd]),
+    "adjoint_param_gradient": (_i32, [_vp, _pd, C.c_double, _pd]),
+    "adjoint_timing": (_i32, [_vp, _pd, _pd, _pi64]),
     "tube_push_deposit_static": (_i32, [_vp, _vp, _i64, _vp, C.c_int32, C.c_double,
                                          C.c_double, C.c_double, _vp, _vp, _vp]),
     "tube_strerror": (C.c_char_p, [_i32]),
@@ -370,9 +380,162 @@ class Batch:
             pass
 
 
+class Adjoint:
+    """Discrete adjoint of an nsteps-step run of one tube, checkpointed every
+    checkpoint_every steps (adjoint_* in include/sclf_tube.h)."""
+
+    def __init__(self, params, nsteps, checkpoint_every, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.params = params
+        self.nsteps = int(nsteps)
+        h = C.c_void_p()
+        _check(self.lib.adjoint_create(C.byref(params), self.nsteps, int(checkpoint_every),
+                                       C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "adjoint_create")
+        self.h = h
+        th = C.c_void_p()
+        _check(self.lib.adjoint_tube(self.h, C.byref(th)), "adjoint_tube")
+        self.tube = _TubeView(self.lib, th, params)
+        self.nz = int(params.Nz)
+
+    def set_injections(self, n_inj=None):
+        if n_inj is None:
+            _check(self.lib.adjoint_set_injections(self.h, None), "adjoint_set_injections")
+            return
+        a = np.ascontiguousarray(n_inj, dtype=np.int64)
+        assert a.size == self.nsteps
+        _check(self.lib.adjoint_set_injections(self.h, a.ctypes.data_as(_pi64)),
+               "adjoint_set_injections")
+
+    def forward(self):
+        """(mean terminal gamma, ||E_z||_2) of the run."""
+        v = np.empty(2)
+        _check(self.lib.adjoint_forward(self.h, _dptr(v)), "adjoint_forward")
+        return float(v[0]), float(v[1])
+
+    def events(self):
+        inj, rem, slots = (np.empty(self.nsteps, np.int64) for _ in range(3))
+        _check(self.lib.adjoint_events(self.h, inj.ctypes.data_as(_pi64),
+                                       rem.ctypes.data_as(_pi64), slots.ctypes.data_as(_pi64)),
+               "adjoint_events")
+        return {"injected": inj, "removed": rem, "slots": slots}
+
+    def backward(self, objective):
+        """(d objective / d rho_GJ at the nodes, d objective / d s)."""
+        d_rho = np.empty(self.nz + 1)
+        d_s = C.c_double()
+        _check(self.lib.adjoint_backward(self.h, int(objective), _dptr(d_rho), C.byref(d_s)),
+               "adjoint_backward")
+        return d_rho, d_s.value
+
+    def param_gradient(self, d_rho, d_s):
+        """d objective / d(B_G, P_s, R_cm, w) with macro charge w s."""
+        d_rho = np.ascontiguousarray(d_rho, dtype=np.float64)
+        g = np.empty(4)
+        _check(self.lib.adjoint_param_gradient(self.h, _dptr(d_rho), float(d_s), _dptr(g)),
+               "adjoint_param_gradient")
+        return g
+
+    def timing(self):
+        f, b = C.c_double(), C.c_double()
+        n = C.c_int64()
+        _check(self.lib.adjoint_timing(self.h, C.byref(f), C.byref(b), C.byref(n)),
+               "adjoint_timing")
+        return {"forward_ms": f.value, "backward_ms": b.value, "particle_steps": n.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.tube.h = None
+            self.lib.adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adjoint_problem(params_kw, nsteps, checkpoint_every, z=None, u=None, injections=None):
+    """Fix a run for differentiation in theta = (B_G, P_s, R_cm, w): the
+    grid (L, Nz), dt and the base macro charge s_ref are taken from
+    params_kw's derived values and held, R becomes an explicit parameter.
+    Returns (spec, theta0) for :class:`TubeObjectives`."""
+    d = derive(default_params(**params_kw))
+    kw = dict(params_kw)
+    kw.update(dt=d["dt"], R_cm=d["R_cm"])
+    spec = {"params": kw, "s_ref": d["s"], "nsteps": int(nsteps),
+            "checkpoint_every": int(checkpoint_every),
+            "z": None if z is None else np.asarray(z, np.float64),
+            "u": None if u is None else np.asarray(u, np.float64),
+            "injections": injections}
+    theta0 = np.array([params_kw.get("B_G", 1e12), params_kw.get("P_s", 1.0), d["R_cm"], 1.0])
+    return spec, theta0
+
+
+def _adjoint_at(spec, theta):
+    kw = dict(spec["params"])
+    kw.update(B_G=float(theta[0]), P_s=float(theta[1]), R_cm=float(theta[2]),
+              macro_charge=float(theta[3]) * spec["s_ref"])
+    a = Adjoint(default_params(**kw), spec["nsteps"], spec["checkpoint_every"])
+    if spec["z"] is not None and spec["z"].size:
+        a.tube.add_particles(spec["z"], spec["u"])
+    if spec["injections"] is not None:
+        a.set_injections(spec["injections"])
+    return a
+
+
+def _objectives_function():
+    import torch
+
+    class TubeObjectives(torch.autograd.Function):
+        """theta = (B_G, P_s, R_cm, w) -> (mean terminal gamma, ||E_z||_2) of
+        the run that :func:`adjoint_problem` fixed, differentiated by the
+        library's discrete adjoint (float64 CPU tensors in and out)."""
+
+        @staticmethod
+        def forward(ctx, theta, spec):
+            th = theta.detach().cpu().double().numpy()
+            a = _adjoint_at(spec, th)
+            ctx.adj, ctx.spec, ctx.theta = a, spec, th
+            return torch.tensor(a.forward(), dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            a, spec = ctx.adj, ctx.spec
+            g = grad_out.detach().cpu().double().numpy()
+            grad = np.zeros(4)
+            for obj in (SCLF_OBJ_GAMMA, SCLF_OBJ_EZ):
+                if g[obj] != 0.0:
+                    d_rho, d_s = a.backward(obj)
+                    pg = a.param_gradient(d_rho, d_s)
+                    pg[3] = d_s * spec["s_ref"]          # d/dw at macro charge w s_ref
+                    grad += g[obj] * pg
+            a.close()
+            return torch.tensor(grad, dtype=torch.float64), None
+
+    return TubeObjectives
+
+
+_TUBE_OBJECTIVES = None
+
+
+def tube_objectives(theta, spec):
+    """Differentiable (mean terminal gamma, ||E_z||_2) as a function of the
+    float64 tensor theta = (B_G, P_s, R_cm, w)."""
+    global _TUBE_OBJECTIVES
+    if _TUBE_OBJECTIVES is None:
+        _TUBE_OBJECTIVES = _objectives_function()
+    return _TUBE_OBJECTIVES.apply(theta, spec)
+
+
 def header_functions(path=HEADER):
     """Names of the functions include/sclf_tube.h declares."""
     import re
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:tube|batch)_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:tube|batch|adjoint)_[a-z_]+)\s*\(", text)))

@@ -1,0 +1,513 @@
+// C ABI of the adjoint driver (declared in include/sclf_tube.h). A tube's
+// N-step run (Sec. 2, Figure A) is recorded with checkpoints every K steps
+// and then swept in reverse segment by segment: each segment is recomputed
+// from its checkpoint with its injection counts replayed, keeping every
+// step's particle arrays, gather table and current, and the reverse kernels
+// walk it back. The result is the gradient of an objective with respect to
+// rho_GJ at the nodes and to the macro charge s; through rho_GJ's closed
+// form (Eq. 5-7) it is chained to the pulsar's B, P and R.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tube_impl.h"
+
+using namespace sclf;
+
+struct sclf_adjoint {
+    sclf_tube* t = nullptr;
+    int64_t nsteps = 0;
+    int K = 0;                      // steps per segment (even)
+    int64_t nseg = 0;
+    int64_t rs = 4;                 // bytes of one particle coordinate
+    int64_t cap_pad = 0;
+    int nz = 0;
+    char* mem = nullptr;            // one device allocation for everything below
+    std::vector<char*> sx, su;      // K+1 snapshots of the slot arrays of a segment
+    char* ck_x = nullptr;           // nseg+1 checkpoints (segment starts and the end)
+    char* ck_u = nullptr;
+    double* ck_f = nullptr;         // per checkpoint: E_z (nz), E_r (nz+1), B (nz)
+    DevState* ck_st = nullptr;      // per checkpoint
+    char* tabs = nullptr;           // K+1 gather tables of a segment
+    double* jlog = nullptr;         // K currents of a segment (nz each)
+    long long* evlog = nullptr;     // kLogStride per step: the recorded events
+    long long* ulog = nullptr;      // kLogStride per step: injections set by the caller
+    long long* seglog = nullptr;    // kLogStride per step of the segment being reversed
+    char* lx = nullptr;             // adjoints of the slots
+    char* lu = nullptr;
+    double* lez = nullptr;
+    double* ler[2] = {nullptr, nullptr};
+    double* lb[2] = {nullptr, nullptr};
+    double* lsum = nullptr;         // per cell: sum over steps of lambda_J J
+    char* ls_tab = nullptr;         // per cell: (s/dt) lambda_J in the particle precision
+    double* part = nullptr;
+    double* values = nullptr;       // the two objectives of the last forward pass
+    int adj_grid = 0;
+    std::vector<double> rho_p0;     // particles' charge density at t = 0 (nodes)
+    bool started = false;           // checkpoint 0 holds the initial state
+    bool forward_done = false;
+    bool use_ulog = false;
+    int64_t current_seg = -1;       // segment whose steps the snapshots hold
+    cudaGraphExec_t g_fwd = nullptr, g_fwd_user = nullptr, g_recompute = nullptr,
+                    g_rev = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    float fwd_ms = 0.f, bwd_ms = 0.f;
+    int64_t pslots = 0;
+};
+
+namespace {
+
+int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
+
+char* tab_of(sclf_adjoint* A, int k) {
+    return A->tabs + static_cast<int64_t>(k) * align256(2 * (A->nz + 1) * A->rs);
+}
+double* ckf_of(sclf_adjoint* A, int64_t c) { return A->ck_f + c * (3 * A->nz + 1); }
+
+// K forward steps from snapshot 0: step k reads snapshot k and writes k+1.
+template <class Real>
+int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
+                    cudaGraphExec_t* out) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < A->K && e == cudaSuccess; ++k) {
+        PushArgs<Real> pa = push_args<Real>(t);
+        pa.xi = reinterpret_cast<Real*>(A->sx[k]);
+        pa.u = reinterpret_cast<Real*>(A->su[k]);
+        pa.xo = reinterpret_cast<Real*>(A->sx[k + 1]);
+        pa.uo = reinterpret_cast<Real*>(A->su[k + 1]);
+        pa.ids = nullptr;
+        pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
+        pa.evlog = evlog;
+        pa.replay = replay;
+        e = launch_push<Real>(pa, t->p.accumulate, t->push_grid, s);
+        if (e != cudaSuccess) break;
+        FieldArgs<Real> fa = field_args<Real>(t, k & 1);
+        fa.jlast = A->jlog + static_cast<int64_t>(k) * A->nz;
+        fa.ez2 = reinterpret_cast<Real*>(tab_of(A, k + 1));
+        fa.evlog = evlog;
+        e = launch_field<Real>(fa, t->p.accumulate, s);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
+    CK(e2);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return SCLF_OK;
+}
+
+// The K steps of a segment in reverse: per step the transposed field update,
+// then the particles.
+template <class Real>
+int capture_reverse(sclf_adjoint* A, cudaGraphExec_t* out) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = A->K - 1; k >= 0 && e == cudaSuccess; --k) {
+        AdjFieldArgs<Real> fa;
+        fa.lez = A->lez;
+        fa.ler_in = A->ler[(k + 1) & 1];
+        fa.ler_out = A->ler[k & 1];
+        fa.lb_in = A->lb[(k + 1) & 1];
+        fa.lb_out = A->lb[k & 1];
+        fa.jstep = A->jlog + static_cast<int64_t>(k) * A->nz;
+        fa.lsum = A->lsum;
+        fa.ls_tab = reinterpret_cast<Real*>(A->ls_tab);
+        fa.nz = A->nz;
+        fa.dt = t->fc.dt;
+        fa.cdt = t->fc.cdt;
+        fa.fourpi_dt = t->fc.fourpi_dt;
+        fa.s_over_dt = t->fc.s_over_dt;
+        e = launch_adj_field<Real>(fa, s);
+        if (e != cudaSuccess) break;
+        AdjPushArgs<Real> pa;
+        pa.xi = reinterpret_cast<const Real*>(A->sx[k]);
+        pa.u = reinterpret_cast<const Real*>(A->su[k]);
+        pa.lx = reinterpret_cast<Real*>(A->lx);
+        pa.lu = reinterpret_cast<Real*>(A->lu);
+        pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
+        pa.ls_tab = reinterpret_cast<const Real*>(A->ls_tab);
+        pa.lez = A->lez;
+        pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
+        pa.nz = A->nz;
+        pa.nzf = static_cast<Real>(A->nz);
+        pa.dt = static_cast<Real>(t->d.dt);
+        pa.cfl = static_cast<Real>(t->d.dt / t->d.dz);
+        e = launch_adj_push<Real>(pa, A->adj_grid, s);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
+    CK(e2);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return SCLF_OK;
+}
+
+// Checkpoint c <- the state at a segment start (snapshot 0, fields at even
+// parity, counters); and back.
+int save_checkpoint(sclf_adjoint* A, int64_t c, int snap) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    const int64_t bytes = A->cap_pad * A->rs;
+    const int64_t nz = A->nz;
+    double* f = ckf_of(A, c);
+    CK(cudaMemcpyAsync(A->ck_x + c * bytes, A->sx[snap], bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A->ck_u + c * bytes, A->su[snap], bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(f, t->ez, nz * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(f + nz, t->er[0], (nz + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(f + 2 * nz + 1, t->b[0], nz * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A->ck_st + c, t->st, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
+    return SCLF_OK;
+}
+
+int restore_fields(sclf_adjoint* A, int64_t c) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    const int64_t nz = A->nz;
+    const double* f = ckf_of(A, c);
+    CK(cudaMemcpyAsync(t->ez, f, nz * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->er[0], f + nz, (nz + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->b[0], f + 2 * nz + 1, nz * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->st, A->ck_st + c, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
+    return SCLF_OK;
+}
+
+int restore_checkpoint(sclf_adjoint* A, int64_t c) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    const int64_t bytes = A->cap_pad * A->rs;
+    CK(cudaMemcpyAsync(A->sx[0], A->ck_x + c * bytes, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A->su[0], A->ck_u + c * bytes, bytes, cudaMemcpyDeviceToDevice, s));
+    return restore_fields(A, c);
+}
+
+template <class Real>
+cudaError_t table0(sclf_adjoint* A) {
+    return launch_ez_table<Real>(A->t->ez, reinterpret_cast<Real*>(tab_of(A, 0)), A->nz,
+                                 A->t->gstream);
+}
+
+template <class Real>
+int run_forward(sclf_adjoint* A, double* values) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    const int64_t nz = A->nz;
+    const int64_t bytes = A->cap_pad * A->rs;
+    int rc;
+    if (!A->started) {
+        // t = 0: Eq. 4 with the charge of the particles the tube holds
+        A->rho_p0.assign(nz + 1, 0.0);
+        rc = tube_read_fields(t, nullptr, nullptr, nullptr, nullptr, A->rho_p0.data());
+        if (rc) return rc;
+        rc = tube_solve_fields(t);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(A->sx[0], t->xi, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(A->su[0], t->u, bytes, cudaMemcpyDeviceToDevice, s));
+        rc = save_checkpoint(A, 0, 0);
+        if (rc) return rc;
+        A->started = true;
+    } else {
+        rc = restore_checkpoint(A, 0);
+        if (rc) return rc;
+    }
+    CK(table0<Real>(A));
+    cudaGraphExec_t* g = A->use_ulog ? &A->g_fwd_user : &A->g_fwd;
+    if (!*g) {
+        rc = capture_forward<Real>(A, A->evlog, A->use_ulog ? A->ulog : nullptr, g);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(A->ev[0], s));
+    for (int64_t c = 0; c < A->nseg; ++c) {
+        if (c > 0) {
+            rc = save_checkpoint(A, c, 0);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(*g, s));
+        if (c + 1 < A->nseg) {
+            CK(cudaMemcpyAsync(A->sx[0], A->sx[A->K], bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(A->su[0], A->su[A->K], bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(tab_of(A, 0), tab_of(A, A->K), 2 * (nz + 1) * A->rs,
+                               cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    CK(cudaEventRecord(A->ev[1], s));
+    // the end of the run: checkpoint nseg, the objectives, the tube's own arrays
+    rc = save_checkpoint(A, A->nseg, A->K);
+    if (rc) return rc;
+    CK(launch_objectives<Real>(reinterpret_cast<const Real*>(A->sx[A->K]),
+                               reinterpret_cast<const Real*>(A->su[A->K]), t->st, t->ez,
+                               static_cast<int>(nz), t->d.dz, A->part, A->values, s));
+    CK(cudaMemcpyAsync(t->xi, A->sx[A->K], bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->u, A->su[A->K], bytes, cudaMemcpyDeviceToDevice, s));
+    double hv[2];
+    std::vector<long long> log(static_cast<size_t>(kLogStride * A->nsteps));
+    CK(cudaMemcpyAsync(hv, A->values, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(log.data(), A->evlog, log.size() * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventElapsedTime(&A->fwd_ms, A->ev[0], A->ev[1]));
+    A->pslots = 0;
+    for (int64_t n = 0; n < A->nsteps; ++n)
+        A->pslots += log[kLogStride * n + kLogSlots] + log[kLogStride * n + kLogInjected];
+    if (values) { values[0] = hv[0]; values[1] = hv[1]; }
+    A->current_seg = A->nseg - 1;
+    A->forward_done = true;
+    return SCLF_OK;
+}
+
+template <class Real>
+int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
+    sclf_tube* t = A->t;
+    cudaStream_t s = t->gstream;
+    const int64_t nz = A->nz;
+    const int64_t bytes = A->cap_pad * A->rs;
+    int rc;
+    if (!A->g_recompute) {
+        rc = capture_forward<Real>(A, nullptr, A->evlog, &A->g_recompute);
+        if (rc) return rc;
+    }
+    if (!A->g_rev) {
+        rc = capture_reverse<Real>(A, &A->g_rev);
+        if (rc) return rc;
+    }
+    // seeds at the end of the run (checkpoint nseg)
+    CK(cudaMemsetAsync(A->lez, 0, nz * 8, s));
+    CK(cudaMemsetAsync(A->ler[0], 0, (nz + 1) * 8, s));
+    CK(cudaMemsetAsync(A->lb[0], 0, nz * 8, s));
+    CK(cudaMemsetAsync(A->lsum, 0, nz * 8, s));
+    CK(cudaMemsetAsync(A->lx, 0, bytes, s));
+    CK(cudaMemsetAsync(A->lu, 0, bytes, s));
+    if (objective == SCLF_OBJ_GAMMA) {
+        CK(launch_seed_gamma<Real>(reinterpret_cast<const Real*>(A->ck_x + A->nseg * bytes),
+                                   reinterpret_cast<const Real*>(A->ck_u + A->nseg * bytes),
+                                   A->ck_st + A->nseg, reinterpret_cast<Real*>(A->lx),
+                                   reinterpret_cast<Real*>(A->lu), s));
+    } else {
+        CK(launch_seed_ez(ckf_of(A, A->nseg), static_cast<int>(nz), t->d.dz, A->values, A->lez, s));
+    }
+    CK(cudaEventRecord(A->ev[2], s));
+    for (int64_t c = A->nseg - 1; c >= 0; --c) {
+        if (c != A->current_seg) {
+            rc = restore_checkpoint(A, c);
+            if (rc) return rc;
+            CK(table0<Real>(A));
+            CK(cudaGraphLaunch(A->g_recompute, s));
+            A->current_seg = c;
+        }
+        CK(cudaMemcpyAsync(A->seglog, A->evlog + static_cast<int64_t>(kLogStride) * c * A->K,
+                           static_cast<int64_t>(kLogStride) * A->K * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaGraphLaunch(A->g_rev, s));
+    }
+    CK(cudaEventRecord(A->ev[3], s));
+    // the tube shows the end of the run again
+    rc = restore_fields(A, A->nseg);
+    if (rc) return rc;
+    std::vector<double> lez(nz), lphi(nz + 1), lsum(nz);
+    CK(cudaMemcpyAsync(lez.data(), A->lez, nz * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lphi.data(), A->ler[0], (nz + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lsum.data(), A->lsum, nz * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventElapsedTime(&A->bwd_ms, A->ev[2], A->ev[3]));
+    // t = 0: E_z = -(phi_{j+1} - phi_j)/dz, E_r = phi; phi from Eq. 4 with
+    // source rho_GJ - rho_particles(s)
+    const double dz = t->d.dz, sq = t->d.s;
+    for (int64_t j = 0; j < nz; ++j) {
+        lphi[j + 1] -= lez[j] / dz;
+        lphi[j] += lez[j] / dz;
+    }
+    std::vector<double> lrho(nz + 1);
+    solve_poisson_transpose(lphi.data(), nz, dz, lrho.data());
+    double sj = 0.0, sp = 0.0;
+    for (int64_t j = 0; j < nz; ++j) sj += lsum[j];
+    for (int64_t j = 0; j <= nz; ++j) sp += lrho[j] * A->rho_p0[j];
+    if (d_rho) std::memcpy(d_rho, lrho.data(), (nz + 1) * 8);
+    if (d_s) *d_s = sj / sq - sp / sq;
+    return SCLF_OK;
+}
+
+void free_adjoint(sclf_adjoint* A) {
+    if (!A) return;
+    if (A->t) cudaStreamSynchronize(A->t->gstream);
+    for (cudaGraphExec_t g : {A->g_fwd, A->g_fwd_user, A->g_recompute, A->g_rev})
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t e : A->ev)
+        if (e) cudaEventDestroy(e);
+    if (A->mem) cudaFree(A->mem);
+    if (A->t) tube_destroy(A->t);
+    delete A;
+}
+
+}  // namespace
+
+extern "C" {
+
+int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_every, void* stream,
+                   adjoint_t* out) {
+    if (!p || !out) return SCLF_EINVAL;
+    *out = nullptr;
+    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64) return SCLF_EINVAL;
+    if (p->accumulate != SCLF_ACC_FIXED64) return SCLF_EINVAL;
+    if (checkpoint_every <= 0 || (checkpoint_every & 1) || nsteps <= 0 ||
+        nsteps % checkpoint_every != 0)
+        return SCLF_EINVAL;
+    tube_params q = *p;
+    q.track_ids = 0;
+    sclf_adjoint* A = new (std::nothrow) sclf_adjoint();
+    if (!A) return SCLF_ENOMEM;
+    int rc = tube_create(&q, nullptr, 0, stream, &A->t);
+    if (rc) { delete A; return rc; }
+    sclf_tube* t = A->t;
+    t->owned = true;
+    A->nsteps = nsteps;
+    A->K = checkpoint_every;
+    A->nseg = nsteps / checkpoint_every;
+    A->rs = p->precision == SCLF_FP64 ? 8 : 4;
+    A->cap_pad = t->lay.cap_pad;
+    A->nz = static_cast<int>(p->Nz);
+    const int64_t nz = A->nz, K = A->K, bytes = A->cap_pad * A->rs;
+    // one allocation, every array 256-byte aligned
+    int64_t o = 0;
+    auto take = [&](int64_t b) { const int64_t r = o; o += align256(b); return r; };
+    const int64_t o_snap = take(2 * (K + 1) * bytes);
+    const int64_t o_ckx = take((A->nseg + 1) * bytes);
+    const int64_t o_cku = take((A->nseg + 1) * bytes);
+    const int64_t o_ckf = take((A->nseg + 1) * (3 * nz + 1) * 8);
+    const int64_t o_ckst = take((A->nseg + 1) * static_cast<int64_t>(sizeof(DevState)));
+    const int64_t o_tabs = take((K + 1) * align256(2 * (nz + 1) * A->rs));
+    const int64_t o_jlog = take(K * nz * 8);
+    const int64_t o_evlog = take(kLogStride * nsteps * 8);
+    const int64_t o_ulog = take(kLogStride * nsteps * 8);
+    const int64_t o_seglog = take(kLogStride * K * 8);
+    const int64_t o_lx = take(bytes);
+    const int64_t o_lu = take(bytes);
+    const int64_t o_lez = take(nz * 8);
+    const int64_t o_ler = take(2 * (nz + 1) * 8);
+    const int64_t o_lb = take(2 * nz * 8);
+    const int64_t o_lsum = take(nz * 8);
+    const int64_t o_lstab = take(nz * A->rs);
+    const int64_t o_part = take(2 * kObjBlocks * 8);
+    const int64_t o_values = take(2 * 8);
+    if (cudaMalloc(&A->mem, o) != cudaSuccess) {
+        A->mem = nullptr;
+        free_adjoint(A);
+        return SCLF_ENOMEM;
+    }
+    char* m = A->mem;
+    for (int64_t k = 0; k <= K; ++k) {
+        A->sx.push_back(m + o_snap + (2 * k) * bytes);
+        A->su.push_back(m + o_snap + (2 * k + 1) * bytes);
+    }
+    A->ck_x = m + o_ckx;
+    A->ck_u = m + o_cku;
+    A->ck_f = reinterpret_cast<double*>(m + o_ckf);
+    A->ck_st = reinterpret_cast<DevState*>(m + o_ckst);
+    A->tabs = m + o_tabs;
+    A->jlog = reinterpret_cast<double*>(m + o_jlog);
+    A->evlog = reinterpret_cast<long long*>(m + o_evlog);
+    A->ulog = reinterpret_cast<long long*>(m + o_ulog);
+    A->seglog = reinterpret_cast<long long*>(m + o_seglog);
+    A->lx = m + o_lx;
+    A->lu = m + o_lu;
+    A->lez = reinterpret_cast<double*>(m + o_lez);
+    A->ler[0] = reinterpret_cast<double*>(m + o_ler);
+    A->ler[1] = A->ler[0] + (nz + 1);
+    A->lb[0] = reinterpret_cast<double*>(m + o_lb);
+    A->lb[1] = A->lb[0] + nz;
+    A->lsum = reinterpret_cast<double*>(m + o_lsum);
+    A->ls_tab = m + o_lstab;
+    A->part = reinterpret_cast<double*>(m + o_part);
+    A->values = reinterpret_cast<double*>(m + o_values);
+    if (cudaMemsetAsync(A->mem, 0, o, t->gstream) != cudaSuccess ||
+        cudaStreamSynchronize(t->gstream) != cudaSuccess) {
+        free_adjoint(A);
+        return SCLF_ECUDA;
+    }
+    for (cudaEvent_t& e : A->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; free_adjoint(A); return SCLF_ECUDA; }
+    const int64_t tiles = A->cap_pad / (A->rs == 8 ? Layout<double>::kTile : Layout<float>::kTile);
+    A->adj_grid = A->rs == 8 ? adj_push_grid_size<double>(t->sms) : adj_push_grid_size<float>(t->sms);
+    if (A->adj_grid > tiles) A->adj_grid = static_cast<int>(tiles);
+    *out = A;
+    return SCLF_OK;
+}
+
+int adjoint_destroy(adjoint_t a) {
+    if (!a) return SCLF_EINVAL;
+    free_adjoint(a);
+    return SCLF_OK;
+}
+
+int adjoint_tube(adjoint_t a, tube_t* out) {
+    if (!a || !out) return SCLF_EINVAL;
+    *out = a->t;
+    return SCLF_OK;
+}
+
+int adjoint_set_injections(adjoint_t a, const int64_t* n_inj) {
+    if (!a) return SCLF_EINVAL;
+    if (!n_inj) {
+        a->use_ulog = false;
+        return SCLF_OK;
+    }
+    std::vector<long long> log(static_cast<size_t>(kLogStride * a->nsteps), 0);
+    for (int64_t n = 0; n < a->nsteps; ++n) {
+        if (n_inj[n] < 0) return SCLF_EINVAL;
+        log[kLogStride * n + kLogInjected] = n_inj[n];
+    }
+    CK(cudaMemcpyAsync(a->ulog, log.data(), log.size() * 8, cudaMemcpyHostToDevice, a->t->gstream));
+    CK(cudaStreamSynchronize(a->t->gstream));
+    a->use_ulog = true;
+    return SCLF_OK;
+}
+
+int adjoint_forward(adjoint_t a, double* values) {
+    if (!a) return SCLF_EINVAL;
+    CK(cudaStreamSynchronize(a->t->stream));
+    return a->rs == 8 ? run_forward<double>(a, values) : run_forward<float>(a, values);
+}
+
+int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_slots) {
+    if (!a) return SCLF_EINVAL;
+    if (!a->forward_done) return SCLF_ESTATE;
+    std::vector<long long> log(static_cast<size_t>(kLogStride * a->nsteps));
+    CK(cudaMemcpyAsync(log.data(), a->evlog, log.size() * 8, cudaMemcpyDeviceToHost, a->t->gstream));
+    CK(cudaStreamSynchronize(a->t->gstream));
+    for (int64_t n = 0; n < a->nsteps; ++n) {
+        if (n_inj) n_inj[n] = log[kLogStride * n + kLogInjected];
+        if (n_removed) n_removed[n] = log[kLogStride * n + kLogRemoved];
+        if (n_slots) n_slots[n] = log[kLogStride * n + kLogSlots];
+    }
+    return SCLF_OK;
+}
+
+int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s) {
+    if (!a || (objective != SCLF_OBJ_GAMMA && objective != SCLF_OBJ_EZ)) return SCLF_EINVAL;
+    if (!a->forward_done) return SCLF_ESTATE;
+    return a->rs == 8 ? run_backward<double>(a, objective, d_rho_gj, d_s)
+                      : run_backward<float>(a, objective, d_rho_gj, d_s);
+}
+
+int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double* grad) {
+    if (!a || !d_rho_gj || !grad) return SCLF_EINVAL;
+    const int rc = rho_gj_parameter_gradient(&a->t->p, d_rho_gj, grad);
+    if (rc) return rc;
+    grad[3] = d_s * a->t->d.s;
+    return SCLF_OK;
+}
+
+int adjoint_timing(adjoint_t a, double* forward_ms, double* backward_ms, int64_t* particle_steps) {
+    if (!a) return SCLF_EINVAL;
+    if (forward_ms) *forward_ms = a->fwd_ms;
+    if (backward_ms) *backward_ms = a->bwd_ms;
+    if (particle_steps) *particle_steps = a->pslots;
+    return SCLF_OK;
+}
+
+}  // extern "C"

@@ -53,6 +53,7 @@ __device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
         st->total_injected += inj;
         st->last_injected = inj;
         st->last_removed = rem;
+        if (a.evlog) a.evlog[kLogStride * st->step + kLogRemoved] = rem;
         st->w0 = static_cast<long long>(st->acc_w0);
         long long n;
         double es;
@@ -91,6 +92,7 @@ batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ 
     a.jacc = d.jacc;
     a.jlast = d.jlast;
     a.ez2 = d.ez2;
+    a.evlog = nullptr;
     a.c = d.fc;
     field_cell<float, kAccFixed>(a, g - d.cell0);
 }

@@ -2,7 +2,8 @@
 // particle kernel. Injection of the pending electrons as virtual slots,
 // cloud-in-cell gather of E_z, the Eq. 1 push, the charge-conserving current
 // deposit, removal at the tube ends and the base-cell weight for the next
-// injection. Persistent CTAs stream the particle slots in place.
+// injection. Persistent CTAs stream the particle slots, in place or (for a
+// recorded run) into a separate output array.
 #include "device_common.cuh"
 
 namespace sclf {
@@ -19,6 +20,8 @@ template <class Real, class AccT>
 struct TileCtx {
     Real* xi;
     Real* u;
+    Real* xo;                  // pushed slots are stored here (xi: in place)
+    Real* uo;
     long long* ids;
     const typename PairOf<Real>::T* tab;
     AccT* jacc;
@@ -131,25 +134,35 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
 #pragma unroll
     for (int v = 0; v < kPPT; v += kVec) {
         if (i0 + v < c.n_tot) {
-            vstore(c.xi + i0 + v, xs + v);
-            vstore(c.u + i0 + v, us + v);
+            vstore(c.xo + i0 + v, xs + v);
+            vstore(c.uo + i0 + v, us + v);
         }
     }
     warp_flush<AccT>(rkey >= Real(0) ? static_cast<int>(rkey) : -1, ra, jacc);
 }
 
-// Injection bookkeeping of a step: the pending count clipped to the free
-// slots. The caller that owns the tube's first tile records it.
-__device__ __forceinline__ long long clipped_injection(const DevState* st, long long capacity) {
-    const long long n_slots = st->n_slots, n_req = st->n_inj;
-    long long room = capacity - n_slots;
+// Injection bookkeeping of a step: the requested count (the tube's own, or
+// a replayed one) clipped to the free slots. The caller that owns the tube's
+// first tile records it.
+__device__ __forceinline__ long long requested_injection(const DevState* st,
+                                                         const long long* replay) {
+    return replay ? replay[kLogStride * st->step + kLogInjected] : st->n_inj;
+}
+__device__ __forceinline__ long long clipped_injection(const DevState* st, long long capacity,
+                                                       long long n_req) {
+    long long room = capacity - st->n_slots;
     room = room > 0 ? room : 0;
     return n_req < room ? n_req : room;
 }
-__device__ __forceinline__ void record_injection(DevState* st, long long n_inj) {
+__device__ __forceinline__ void record_injection(DevState* st, long long n_inj, long long n_req,
+                                                 long long* evlog) {
     st->inj_done = n_inj;
     st->slots_processed += static_cast<unsigned long long>(st->n_slots + n_inj);
-    if (n_inj < st->n_inj) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+    if (n_inj < n_req) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+    if (evlog) {
+        evlog[kLogStride * st->step + kLogSlots] = st->n_slots;
+        evlog[kLogStride * st->step + kLogInjected] = n_inj;
+    }
 }
 
 template <class Real, int kAcc>
@@ -158,11 +171,14 @@ push_kernel(const PushArgs<Real> a) {
     constexpr int kTile = Layout<Real>::kTile;
     using AccT = typename AccType<kAcc>::T;
     DevState* st = a.st;
-    const long long n_inj = clipped_injection(st, a.capacity);
-    if (blockIdx.x == 0 && threadIdx.x == 0) record_injection(st, n_inj);
+    const long long n_req = requested_injection(st, a.replay);
+    const long long n_inj = clipped_injection(st, a.capacity, n_req);
+    if (blockIdx.x == 0 && threadIdx.x == 0) record_injection(st, n_inj, n_req, a.evlog);
     TileCtx<Real, AccT> c;
     c.xi = a.xi;
     c.u = a.u;
+    c.xo = a.xo;
+    c.uo = a.uo;
     c.ids = a.ids;
     c.tab = reinterpret_cast<const typename PairOf<Real>::T*>(a.ez2);
     c.jacc = static_cast<AccT*>(a.jacc);
@@ -236,14 +252,16 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         const BatchTube& d = tubes[tile_tube[g]];
         DevState* st = d.st;
         const long long local = g - d.tile0;
-        const long long n_inj = clipped_injection(st, d.capacity);
-        if (local == 0 && threadIdx.x == 0) record_injection(st, n_inj);
+        const long long n_inj = clipped_injection(st, d.capacity, st->n_inj);
+        if (local == 0 && threadIdx.x == 0) record_injection(st, n_inj, st->n_inj, nullptr);
         TileCtx<float, long long> c;
         c.n_slots = st->n_slots;
         c.n_tot = c.n_slots + n_inj;
         if (local * kTile >= c.n_tot) continue;          // the same for the whole CTA
         c.xi = d.xi;
         c.u = d.u;
+        c.xo = d.xi;
+        c.uo = d.u;
         c.ids = d.ids;
         c.tab = reinterpret_cast<const float2*>(d.ez2);
         c.jacc = d.jacc;

@@ -69,6 +69,13 @@ struct DevState {
     long long pad1[3];
 };
 
+// Per-step event log of a recorded run: kLogStride entries per step, indexed
+// by the step counter DevState::step.
+constexpr int kLogStride = 4;
+constexpr int kLogSlots = 0;     // slots before the step's injection
+constexpr int kLogInjected = 1;  // electrons injected by the step
+constexpr int kLogRemoved = 2;   // particles that left the tube (or went non-finite)
+
 // Constants of one tube in the precision the kernels use.
 struct FieldConsts {
     int nz;
@@ -81,8 +88,13 @@ struct PushArgs {
     DevState* st;
     Real* xi;                  // slot positions in cell units (hole: < 0)
     Real* u;                   // gamma beta
+    Real* xo;                  // where the pushed slots go (xi itself: in place)
+    Real* uo;
     long long* ids;            // may be null
     const Real* ez2;           // gather table, 2*(nz+1): (E_{m-1/2}, E_{m+1/2})
+    long long* evlog;          // may be null: records slots and injections per step
+    const long long* replay;   // may be null: injection counts to use instead
+                               // of the tube's own (a log in the evlog layout)
     void* jacc;                // nz accumulators (long long or double)
     long long capacity;        // slots
     int nz;
@@ -102,6 +114,7 @@ struct FieldArgs {
     void* jacc;                // nz accumulators, zeroed after use
     double* jlast;             // nz cells, J^{n+1/2} (diagnostic copy)
     Real* ez2;                 // gather table for the next step
+    long long* evlog;          // may be null: records the step's removals
     FieldConsts c;
 };
 
@@ -155,6 +168,38 @@ struct BatchTube {
     FieldConsts fc;
 };
 
+// Reverse sweep of one step (the discrete adjoint, adjoint.cu).
+// The transposed field update of Eq. 3, one thread per cell: adjoints of
+// (E_z, E_r, B) after the step -> before it, and of the current J.
+template <class Real>
+struct AdjFieldArgs {
+    double* lez;               // nz cells, in place: after -> before the step
+    const double* ler_in;      // nz+1 nodes, after the step
+    double* ler_out;           // nz+1 nodes, before the step
+    const double* lb_in;       // nz cells, after the step
+    double* lb_out;            // nz cells, before the step
+    const double* jstep;       // nz cells, J^{n+1/2} of the step (forward)
+    double* lsum;              // nz cells: += lambda_J J (for d/ds)
+    Real* ls_tab;              // nz cells: (s/dt) lambda_J, read by the particles
+    int nz;
+    double dt, cdt, fourpi_dt, s_over_dt;
+};
+
+// Per particle: adjoints of the deposit, the Eq. 1 push and the gather.
+template <class Real>
+struct AdjPushArgs {
+    const Real* xi;            // slots before the step (holes < 0)
+    const Real* u;
+    Real* lx;                  // in: adjoint of the slots after the step;
+    Real* lu;                  // out: before it (in place)
+    const Real* ez2;           // the step's gather table
+    const Real* ls_tab;        // (s/dt) lambda_J per cell
+    double* lez;               // nz cells: the gather's share is added
+    const long long* log;      // the step's kLogStride log entries
+    int nz;
+    Real nzf, dt, cfl;
+};
+
 // Launchers. All return cudaGetLastError() after the launch.
 template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid,
@@ -193,9 +238,36 @@ template <class Pos>
 cudaError_t launch_rho(const Pos* xi, long long n_slots, double* rho_acc,
                        int nz, double scale, cudaStream_t s);
 
+template <class Real>
+cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s);
+template <class Real>
+cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s);
+template <class Real>
+int adj_push_grid_size(int device_sms);
+// Sums over the final state of a recorded run: out[0] = mean gamma of the
+// live slots, out[1] = ||E_z||_2 = sqrt(sum E_z^2 dz). part holds
+// 2 * kObjBlocks doubles.
+constexpr int kObjBlocks = 256;
+template <class Real>
+cudaError_t launch_objectives(const Real* xi, const Real* u, const DevState* st,
+                              const double* ez, int nz, double dz, double* part,
+                              double* out, cudaStream_t s);
+// Adjoint seeds: lambda_u = u / gamma / N_live (mean gamma), lambda_E =
+// E dz / ||E|| (field norm).
+template <class Real>
+cudaError_t launch_seed_gamma(const Real* xi, const Real* u, const DevState* st, Real* lx,
+                              Real* lu, cudaStream_t s);
+cudaError_t launch_seed_ez(const double* ez, int nz, double dz, const double* values,
+                           double* lez, cudaStream_t s);
+
 // Host set-up (setup.cpp).
 int derive(const tube_params* p, tube_derived* d);
 int build_rho_gj(const tube_params* p, const tube_derived* d, double* rho);
 void solve_poisson(const double* rho, int64_t nz, double dz, double* phi);
+// Transpose of solve_poisson: from the adjoint of phi (nodes 0..Nz) to that
+// of the source rho (nodes 0..Nz; node 0 gets 0).
+void solve_poisson_transpose(const double* lphi, int64_t nz, double dz, double* lrho);
+// grad[0..2] = d/d(B, P, R) of sum_j d_rho_j rho_GJ,j (grid, dt, s fixed).
+int rho_gj_parameter_gradient(const tube_params* p, const double* d_rho, double* grad);
 
 }  // namespace sclf

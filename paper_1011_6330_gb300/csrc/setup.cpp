@@ -1,7 +1,9 @@
 // Host-side set-up of a tube: unit conversion (Sec. 3), the rho_GJ profile
-// (Eq. 5, Eq. 6-7) and the empty-tube Poisson problem (Eq. 4).
+// (Eq. 5, Eq. 6-7), the empty-tube Poisson problem (Eq. 4) and, for the
+// adjoint, its transpose and the profile's derivatives in (B, P, R).
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "sclf_internal.h"
 
@@ -130,6 +132,69 @@ void solve_poisson(const double* rho, int64_t nz, double dz, double* phi) {
     for (int64_t i = nz - 1; i >= 1; --i) phi[i] = dp[i] - cp[i] * phi[i + 1];
     delete[] cp;
     delete[] dp;
+}
+
+// Transpose of solve_poisson. With phi_{1..Nz} = A^-1 (4 pi dz^2 rho_{1..Nz})
+// and phi_0 = 0, the source adjoint is lrho_{1..Nz} = 4 pi dz^2 A^-T lphi_{1..Nz},
+// lrho_0 = 0. A^T swaps A's off-diagonals: row i of A^T has 1 on the left
+// (i > 1) and, on the right, 2 in the row before the last (the ghost entry of
+// A's last row) and 1 elsewhere. A is diagonally dominant by rows, so A^T is
+// by columns and Thomas elimination without pivoting stays stable.
+void solve_poisson_transpose(const double* lphi, int64_t nz, double dz, double* lrho) {
+    const double diag = -(2.0 + dz * dz);
+    double* cp = new double[nz + 1];
+    double* dp = new double[nz + 1];
+    for (int64_t i = 1; i <= nz; ++i) {
+        const double sub = (i == 1) ? 0.0 : 1.0;
+        const double sup = (i == nz) ? 0.0 : (i + 1 == nz ? 2.0 : 1.0);
+        const double denom = diag - (i == 1 ? 0.0 : sub * cp[i - 1]);
+        cp[i] = sup / denom;
+        dp[i] = (lphi[i] - (i == 1 ? 0.0 : sub * dp[i - 1])) / denom;
+    }
+    double* y = new double[nz + 1];
+    y[nz] = dp[nz];
+    for (int64_t i = nz - 1; i >= 1; --i) y[i] = dp[i] - cp[i] * y[i + 1];
+    const double scale = 4.0 * kPi * dz * dz;
+    lrho[0] = 0.0;
+    for (int64_t i = 1; i <= nz; ++i) lrho[i] = scale * y[i];
+    delete[] cp;
+    delete[] dp;
+    delete[] y;
+}
+
+// d/d(B, P, R) of sum_j d_rho_j rho_GJ,j on a fixed grid: central
+// differences (relative step 1e-6) of the closed-form profile, with the
+// grid, dt and s held at the values of the unperturbed parameters and R an
+// independent coordinate (taken at its derived value, not R_* theta_p(P)).
+// A caller-supplied profile does not depend on them: all three are 0.
+int rho_gj_parameter_gradient(const tube_params* p, const double* d_rho, double* grad) {
+    grad[0] = grad[1] = grad[2] = 0.0;
+    if (p->rho_gj_mode == SCLF_RHO_USER) return SCLF_OK;
+    tube_derived d0;
+    int rc = derive(p, &d0);
+    if (rc) return rc;
+    tube_params q = *p;
+    q.R_cm = d0.R_cm;
+    q.dt = d0.dt;
+    q.macro_charge = d0.s;
+    const int64_t nz = p->Nz;
+    std::vector<double> rp(nz + 1), rm(nz + 1);
+    for (int k = 0; k < 3; ++k) {
+        tube_params a = q, b = q;
+        double* va = k == 0 ? &a.B_G : (k == 1 ? &a.P_s : &a.R_cm);
+        double* vb = k == 0 ? &b.B_G : (k == 1 ? &b.P_s : &b.R_cm);
+        const double h = 1e-6 * *va;
+        *va += h;
+        *vb -= h;
+        tube_derived da, db;
+        if ((rc = derive(&a, &da)) || (rc = derive(&b, &db))) return rc;
+        if ((rc = build_rho_gj(&a, &da, rp.data())) || (rc = build_rho_gj(&b, &db, rm.data())))
+            return rc;
+        double sum = 0.0;
+        for (int64_t j = 0; j <= nz; ++j) sum += d_rho[j] * (rp[j] - rm[j]);
+        grad[k] = sum / (2.0 * h);
+    }
+    return SCLF_OK;
 }
 
 }  // namespace sclf

@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "sclf_internal.h"
+#include "tube_impl.h"
 
 using namespace sclf;
 
@@ -17,15 +17,8 @@ constexpr double kPi = 3.14159265358979323846;
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-struct Layout_ {
-    int64_t cap_pad = 0, ntiles = 0;
-    int64_t off_state = 0, off_xi = 0, off_u = 0, off_ids = 0, off_tiles = 0;
-    int64_t off_ez = 0, off_er = 0, off_b = 0, off_jacc = 0, off_jlast = 0;
-    int64_t off_ez2 = 0, off_rho = 0, total = 0;
-};
-
-Layout_ plan(const tube_params* p) {
-    Layout_ l;
+TubeLayout plan(const tube_params* p) {
+    TubeLayout l;
     const int64_t rs = p->precision == SCLF_FP64 ? 8 : 4;
     const int64_t tile = p->precision == SCLF_FP64 ? Layout<double>::kTile : Layout<float>::kTile;
     const int64_t nz = p->Nz;
@@ -51,99 +44,11 @@ Layout_ plan(const tube_params* p) {
 
 }  // namespace
 
-struct sclf_tube {
-    tube_params p{};
-    tube_derived d{};
-    Layout_ lay;
-    int device = 0, sms = 0;
-    cudaStream_t stream = nullptr;      // caller's stream
-    cudaStream_t gstream = nullptr;     // stream used for graph capture/replay
-    bool own_gstream = false;
-    bool owns_ws = false;
-    char* ws = nullptr;
-    DevState* st = nullptr;
-    void* xi = nullptr;
-    void* u = nullptr;
-    long long* ids = nullptr;
-    unsigned long long* tiles = nullptr;
-    double* ez = nullptr;
-    double* er[2] = {nullptr, nullptr};
-    double* b[2] = {nullptr, nullptr};
-    void* jacc = nullptr;
-    double* jlast = nullptr;
-    void* ez2 = nullptr;
-    double* rho_acc = nullptr;
-    std::vector<double> rho_gj;
-    FieldConsts fc{};
-    int push_grid = 0, compact_grid = 0;
-    int fb = 0;                        // fractional bits of SCLF_FIX32 positions
-    int64_t host_step = 0;             // steps launched (== device step count)
-    int steps_since_compact = 0;
-    int compact_every = 64;
-    // graphs
-    cudaGraphExec_t chunk = nullptr;
-    int chunk_steps = 0;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    // timed graphs: two copies with their own events, replayed alternately so
-    // one can be read back while the other runs
-    struct TimedChunk {
-        cudaGraphExec_t exec = nullptr;
-        std::vector<cudaEvent_t> ev;   // 3 per step + 2 around the compaction
-        bool pending = false;
-    } tchunk[2];
-    int tnext = 0;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;       // pool, 3 per step, 2 per compaction
-    struct Rec { int kind; int e0; };  // kind 0 step (e0, e0+1, e0+2), 1 compaction
-    std::vector<Rec> recs;
-    int ev_next = 0;
-    tube_timing acc{};
-    unsigned long long slots_base = 0;
-    bool in_batch = false;             // stepped by its batch, not on its own
-};
 
 namespace {
 
-int cuda_fail(cudaError_t e) {
-    if (e == cudaSuccess) return SCLF_OK;
-    std::fprintf(stderr, "sclf_tube: CUDA error %s\n", cudaGetErrorString(e));
-    return SCLF_ECUDA;
-}
-#define CK(x) do { const cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
 
-template <class Real>
-PushArgs<Real> push_args(sclf_tube* t) {
-    PushArgs<Real> a;
-    a.st = t->st;
-    a.xi = static_cast<Real*>(t->xi);
-    a.u = static_cast<Real*>(t->u);
-    a.ids = t->ids;
-    a.ez2 = static_cast<const Real*>(t->ez2);
-    a.jacc = t->jacc;
-    a.capacity = t->p.capacity;
-    a.nz = static_cast<int>(t->p.Nz);
-    a.nzf = static_cast<Real>(t->p.Nz);
-    a.dt = static_cast<Real>(t->d.dt);
-    a.cfl = static_cast<Real>(t->d.dt / t->d.dz);
-    return a;
-}
 
-template <class Real>
-FieldArgs<Real> field_args(sclf_tube* t, int parity) {
-    FieldArgs<Real> a;
-    a.st = t->st;
-    a.ez = t->ez;
-    a.er_in = t->er[parity];
-    a.er_out = t->er[parity ^ 1];
-    a.b_in = t->b[parity];
-    a.b_out = t->b[parity ^ 1];
-    a.jacc = t->jacc;
-    a.jlast = t->jlast;
-    a.ez2 = static_cast<Real*>(t->ez2);
-    a.c = t->fc;
-    return a;
-}
 
 template <class Pos, class Mom>
 CompactArgs<Pos, Mom> compact_args(sclf_tube* t, int force) {
@@ -158,8 +63,6 @@ CompactArgs<Pos, Mom> compact_args(sclf_tube* t, int force) {
     return a;
 }
 
-bool fp64(const sclf_tube* t) { return t->p.precision == SCLF_FP64; }
-bool fix32(const sclf_tube* t) { return t->p.precision == SCLF_FIX32; }
 
 PushFixArgs push_fix_args(sclf_tube* t) {
     PushFixArgs a;
@@ -206,11 +109,6 @@ cudaError_t do_rho(sclf_tube* t, long long slots) {
                                          std::ldexp(1.0, -t->fb), t->stream);
     return launch_rho<float>(static_cast<const float*>(t->xi), slots, t->rho_acc, nz, 1.0, t->stream);
 }
-cudaError_t do_ez_table(sclf_tube* t) {
-    const int nz = static_cast<int>(t->p.Nz);
-    return fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), nz, t->stream)
-                   : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), nz, t->stream);
-}
 // Position of raw slot i in cell units; negative for a hole.
 double raw_cells(const sclf_tube* t, const void* raw, int64_t i) {
     if (fp64(t)) return static_cast<const double*>(raw)[i];
@@ -245,11 +143,6 @@ cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s, int force) {
                    : launch_compact<float, float>(compact_args<float, float>(t, force), t->compact_grid, s);
 }
 
-int read_state(sclf_tube* t, DevState* h) {
-    CK(cudaMemcpyAsync(h, t->st, sizeof(DevState), cudaMemcpyDeviceToHost, t->stream));
-    CK(cudaStreamSynchronize(t->stream));
-    return SCLF_OK;
-}
 
 int drain_timing(sclf_tube* t);
 
@@ -526,7 +419,7 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
         if (cudaMalloc(&t->ws, t->lay.total) != cudaSuccess) { t->ws = nullptr; return fail(SCLF_ENOMEM); }
         t->owns_ws = true;
     }
-    const Layout_& l = t->lay;
+    const TubeLayout& l = t->lay;
     t->st = reinterpret_cast<DevState*>(t->ws + l.off_state);
     t->xi = t->ws + l.off_xi;
     t->u = t->ws + l.off_u;
@@ -669,13 +562,13 @@ int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
 
 int tube_step(tube_t t) {
     if (!t) return SCLF_EINVAL;
-    if (t->in_batch) return SCLF_ESTATE;
+    if (t->owned) return SCLF_ESTATE;
     return one_step(t);
 }
 
 int tube_run(tube_t t, int64_t nsteps) {
     if (!t || nsteps < 0) return SCLF_EINVAL;
-    if (t->in_batch) return SCLF_ESTATE;
+    if (t->owned) return SCLF_ESTATE;
     while (nsteps > 0) {
         if (t->p.use_graphs && (t->host_step & 1) == 0 &&
             t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
@@ -1064,7 +957,7 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         tube_t t = nullptr;
         const int rc = tube_create(&params[i], nullptr, 0, stream, &t);
         if (rc) return fail(rc);
-        t->in_batch = true;
+        t->owned = true;
         b->tubes.push_back(t);
         BatchTube& d = desc[i];
         d.st = t->st;

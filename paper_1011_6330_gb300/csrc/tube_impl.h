@@ -1,0 +1,138 @@
+// Internal definition of a tube (struct sclf_tube) and the helpers that the
+// translation units driving tubes (the tube and batch ABI, the adjoint
+// driver) share. Not part of the C ABI.
+#pragma once
+
+#include <cstdio>
+#include <vector>
+
+#include "sclf_internal.h"
+
+namespace sclf {
+
+// Byte offsets of the arrays in a tube's device workspace.
+struct TubeLayout {
+    int64_t cap_pad = 0, ntiles = 0;
+    int64_t off_state = 0, off_xi = 0, off_u = 0, off_ids = 0, off_tiles = 0;
+    int64_t off_ez = 0, off_er = 0, off_b = 0, off_jacc = 0, off_jlast = 0;
+    int64_t off_ez2 = 0, off_rho = 0, total = 0;
+};
+
+}  // namespace sclf
+
+struct sclf_tube {
+    tube_params p{};
+    tube_derived d{};
+    sclf::TubeLayout lay;
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t gstream = nullptr;     // stream used for graph capture/replay
+    bool own_gstream = false;
+    bool owns_ws = false;
+    char* ws = nullptr;
+    sclf::DevState* st = nullptr;
+    void* xi = nullptr;
+    void* u = nullptr;
+    long long* ids = nullptr;
+    unsigned long long* tiles = nullptr;
+    double* ez = nullptr;
+    double* er[2] = {nullptr, nullptr};
+    double* b[2] = {nullptr, nullptr};
+    void* jacc = nullptr;
+    double* jlast = nullptr;
+    void* ez2 = nullptr;
+    double* rho_acc = nullptr;
+    std::vector<double> rho_gj;
+    sclf::FieldConsts fc{};
+    int push_grid = 0, compact_grid = 0;
+    int fb = 0;                        // fractional bits of SCLF_FIX32 positions
+    int64_t host_step = 0;             // steps launched (== device step count)
+    int steps_since_compact = 0;
+    int compact_every = 64;
+    // graphs
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_steps = 0;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    // timed graphs: two copies with their own events, replayed alternately so
+    // one can be read back while the other runs
+    struct TimedChunk {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev;   // 3 per step + 2 around the compaction
+        bool pending = false;
+    } tchunk[2];
+    int tnext = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // pool, 3 per step, 2 per compaction
+    struct Rec { int kind; int e0; };  // kind 0 step (e0, e0+1, e0+2), 1 compaction
+    std::vector<Rec> recs;
+    int ev_next = 0;
+    tube_timing acc{};
+    unsigned long long slots_base = 0;
+    bool owned = false;                // stepped by a batch or an adjoint driver,
+                                       // not by tube_step / tube_run
+};
+
+namespace sclf {
+
+inline int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return SCLF_OK;
+    std::fprintf(stderr, "sclf_tube: CUDA error %s\n", cudaGetErrorString(e));
+    return SCLF_ECUDA;
+}
+#define CK(x) do { const cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
+
+inline bool fp64(const sclf_tube* t) { return t->p.precision == SCLF_FP64; }
+inline bool fix32(const sclf_tube* t) { return t->p.precision == SCLF_FIX32; }
+
+template <class Real>
+inline PushArgs<Real> push_args(sclf_tube* t) {
+    PushArgs<Real> a;
+    a.st = t->st;
+    a.xi = static_cast<Real*>(t->xi);
+    a.u = static_cast<Real*>(t->u);
+    a.xo = a.xi;
+    a.uo = a.u;
+    a.ids = t->ids;
+    a.ez2 = static_cast<const Real*>(t->ez2);
+    a.evlog = nullptr;
+    a.replay = nullptr;
+    a.jacc = t->jacc;
+    a.capacity = t->p.capacity;
+    a.nz = static_cast<int>(t->p.Nz);
+    a.nzf = static_cast<Real>(t->p.Nz);
+    a.dt = static_cast<Real>(t->d.dt);
+    a.cfl = static_cast<Real>(t->d.dt / t->d.dz);
+    return a;
+}
+
+template <class Real>
+inline FieldArgs<Real> field_args(sclf_tube* t, int parity) {
+    FieldArgs<Real> a;
+    a.st = t->st;
+    a.ez = t->ez;
+    a.er_in = t->er[parity];
+    a.er_out = t->er[parity ^ 1];
+    a.b_in = t->b[parity];
+    a.b_out = t->b[parity ^ 1];
+    a.jacc = t->jacc;
+    a.jlast = t->jlast;
+    a.ez2 = static_cast<Real*>(t->ez2);
+    a.evlog = nullptr;
+    a.c = t->fc;
+    return a;
+}
+
+inline cudaError_t do_ez_table(sclf_tube* t) {
+    const int nz = static_cast<int>(t->p.Nz);
+    return fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), nz, t->stream)
+                   : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), nz, t->stream);
+}
+
+inline int read_state(sclf_tube* t, DevState* h) {
+    CK(cudaMemcpyAsync(h, t->st, sizeof(DevState), cudaMemcpyDeviceToHost, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+}  // namespace sclf

@@ -82,3 +82,18 @@ def test_workspace_grows_with_capacity_and_grid(lib):
     g = B.workspace_bytes(B.default_params(**workloads.gr_tube()))
     assert g >= 2 * 4 * 10 ** 8                     # FP32 xi and u of 1e8 slots
     assert g < 2 * 4 * 10 ** 8 * 1.1 + 64 * 2 ** 20
+
+
+def test_adjoint_create_validates_before_touching_the_device():
+    """adjoint_create rejects FIX32 particles, FP64 atomics and bad
+    checkpoint intervals with SCLF_EINVAL before any CUDA call."""
+    import ctypes as C
+    lib = B.load()
+    h = C.c_void_p()
+    for kw, n, k in ((dict(precision=B.SCLF_FIX32, Nz=1024), 100, 10),
+                     (dict(accumulate=B.SCLF_ACC_FP64), 100, 10),
+                     (dict(), 100, 7), (dict(), 100, 0), (dict(), 105, 10), (dict(), 0, 10)):
+        p = B.default_params(**kw)
+        assert lib.adjoint_create(C.byref(p), n, k, None, C.byref(h)) == -1
+    assert lib.adjoint_backward(None, 0, None, None) == -1
+    assert lib.adjoint_forward(None, None) == -1
