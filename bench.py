@@ -46,10 +46,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["gr1e8", "large", "batch"], default="gr1e8",
+    ap.add_argument("--workload", choices=["gr1e8", "large", "batch", "adjoint"], default="gr1e8",
                     help="gr1e8: P = 0.5 s frame-dragging tube, Nz = 65536, FP32 particles "
                          "(default); large: P = 0.1 s, B = 3e12 G, Nz = 2^20, 2^30 "
-                         "fixed-point particles")
+                         "fixed-point particles; batch: 256 pulsar tubes; adjoint: "
+                         "gradients of a 2000-step run of a P = 0.3 s tube, Nz = 16384, "
+                         "1e6 FP32 particles")
     ap.add_argument("--particles", type=float, default=None)
     ap.add_argument("--order", choices=["descending", "shuffled"], default="descending")
     ap.add_argument("--accumulate", choices=["fixed64", "fp64"], default="fixed64")
@@ -385,12 +387,230 @@ def run_batch(args):
     return 0
 
 
+ADJ_STEPS, ADJ_EVERY, ADJ_TIME_EVERY = 2000, 100, 5
+
+
+def adjoint_state(B, kw, seed):
+    """Seeded prefilled beam of the adjoint workload (as for gr1e8)."""
+    from paper_1011_6330_gb300 import synth
+    d = B.derive(B.default_params(**kw))
+    gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
+    return synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar, seed=seed,
+                                eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
+
+
+def adjoint_cpu_baseline(kw, d, z, u, seconds, stride=100):
+    """The oracle's FP64 adjoint as it stands (float32 forward, reverse in
+    FP64) on every stride-th particle of the same state (macro charge times
+    stride), the full Nz = 16384 grid, as many steps as fit in ~seconds."""
+    import oracle as orc
+    from oracle import adjoint as oadj
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"],
+                        kw["R_cm"])
+    nz = kw["Nz"]
+    zn = np.arange(nz + 1) * (d["L"] / nz)
+    rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"])
+    run = oadj.AdjointRun(nz, d["L"], d["dt"], rho, d["s"] * stride, z[::stride], u[::stride],
+                          precision="f32", accumulate="fixed")
+    t0 = time.perf_counter()
+    run.gradient("gamma", 4)
+    per_step = (time.perf_counter() - t0) / 4
+    n = min(ADJ_STEPS, max(4, int(seconds / per_step)))
+    t0 = time.perf_counter()
+    _, _, _, inj, _ = run.gradient("gamma", n)
+    el = time.perf_counter() - t0
+    ps = n * z[::stride].size + sum((n - k) * c for k, c in enumerate(inj))
+    return {"value": ps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle adjoint (forward + reverse) of %d steps on %d of the %d particles "
+                      "(every %dth, macro charge x%d), Nz=%d, in %.1f s"
+                      % (n, z[::stride].size, z.size, stride, stride, nz, el)}
+
+
+def run_adjoint(args):
+    """Gradients of the mean terminal gamma with respect to (B, P, R, w) for a
+    2000-step run of the B = 1e12 G, P = 0.3 s frame-dragging tube (Nz =
+    16384, 1e6 FP32 electrons), checkpointed every 100 steps: one timed
+    evaluation is the forward run plus the backward sweep. Reported next to
+    the plain forward run of the same tube."""
+    import torch
+    from paper_1011_6330_gb300 import binding as B
+    from paper_1011_6330_gb300 import workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    kw = workloads.adjoint_tube()
+    d = B.derive(B.default_params(**kw))
+    z, u = adjoint_state(B, kw, rank_seed(rank))
+    a = B.Adjoint(B.default_params(**kw), ADJ_STEPS, ADJ_EVERY)
+    a.tube.add_particles(z, u)
+    n_eval = max(3, args.steps // ADJ_STEPS)
+    for _ in range(max(1, args.warmup // 4)):
+        a.forward()
+        a.backward(B.SCLF_OBJ_GAMMA)
+    a.set_timing(1)                          # builds both timed instances of each graph
+    a.forward()
+    a.backward(B.SCLF_OBJ_GAMMA)
+    # timed region: every TIME_EVERY-th segment replays a graph with event
+    # nodes around each kernel (they cost 2-3 us each against ~10 us kernels)
+    a.set_timing(ADJ_TIME_EVERY)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    tf = tb = 0.0
+    for _ in range(n_eval):
+        vals = a.forward()
+        tf += a.timing()["forward_ms"]
+        g_rho, g_s = a.backward(B.SCLF_OBJ_GAMMA)
+        tb += a.timing()["backward_ms"]
+    clk = clocks.stop()
+    kt = a.kernel_times()
+    a.set_timing(0)
+    psteps = a.timing()["particle_steps"]
+    a.forward()                              # the same pass without any event node
+    untimed_f = a.timing()["forward_ms"]
+    a.backward(B.SCLF_OBJ_GAMMA)
+    untimed_b = a.timing()["backward_ms"]
+    grad_gamma = a.param_gradient(g_rho, g_s)
+    g_rho_e, g_s_e = a.backward(B.SCLF_OBJ_EZ)
+    bwd_ez_ms = a.timing()["backward_ms"]
+    grad_ez = a.param_gradient(g_rho_e, g_s_e)
+    el_s = 1e-3 * (tf + tb)
+    work, el_s = combine_ranks(psteps * n_eval, el_s, device="cuda")
+    # the plain form: the same tube and particles stepped by tube_run (graphs,
+    # no event nodes), timed by events around the whole run
+    t = B.Tube(B.default_params(**dict(kw, track_ids=0)))
+    t.add_particles(z, u)
+    t.solve_fields()
+    t.run(2 * ADJ_EVERY)
+    stream = torch.cuda.current_stream()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0 = t.status()["n_particles"]
+    p0.record(stream)
+    t.run(ADJ_STEPS)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    s1 = t.status()["n_particles"]
+    plain_value = 0.5 * (s0 + s1) * ADJ_STEPS / (1e-3 * p0.elapsed_time(p1))
+    t.close()
+    # FP32 against FP64: the same run with FP64 particles
+    a64 = B.Adjoint(B.default_params(**dict(kw, precision=B.SCLF_FP64)), ADJ_STEPS, ADJ_EVERY)
+    a64.tube.add_particles(z, u)
+    v64 = a64.forward()
+    g64 = [a64.param_gradient(*a64.backward(i)) for i in (B.SCLF_OBJ_GAMMA, B.SCLF_OBJ_EZ)]
+    a64.close()
+    err32 = {name: [float(abs(x - y) / abs(y)) for x, y in zip(g32, gg)]
+             for name, g32, gg in (("gamma", grad_gamma, g64[0]), ("ez", grad_ez, g64[1]))}
+    val_err32 = [float(abs(x - y) / abs(y)) for x, y in zip(vals, v64)]
+    # per kernel: the forward and recompute passes launch the same two kernels
+    # algorithmic bytes per launch: particles 16 B (x, u in and out) forward,
+    # 24 B (x, u in; lambda_x, lambda_u in and out) in reverse; grid kernels
+    # 80 B per cell forward (J accumulator read and cleared, E_z, E_r, B in
+    # and out, J and the float gather table out) and 76 B per cell in reverse
+    slots = psteps / ADJ_STEPS
+    nzc = kw["Nz"]
+    kernels = {
+        "push_kernel": (kt["forward_push"][0] + kt["recompute_push"][0],
+                        kt["forward_push"][1] + kt["recompute_push"][1], 16 * slots),
+        "field_kernel": (kt["forward_field"][0] + kt["recompute_field"][0],
+                         kt["forward_field"][1] + kt["recompute_field"][1], 80 * nzc),
+        "adj_push_kernel": (kt["reverse_push"][0], kt["reverse_push"][1], 24 * slots),
+        "adj_field_kernel": (kt["reverse_field"][0], kt["reverse_field"][1], 76 * nzc),
+    }
+    nseg = ADJ_STEPS // ADJ_EVERY
+    per_eval = {"push_kernel": 2 * ADJ_STEPS - ADJ_EVERY, "field_kernel": 2 * ADJ_STEPS - ADJ_EVERY,
+                "adj_push_kernel": ADJ_STEPS, "adj_field_kernel": ADJ_STEPS}
+    per_launch = {k: (ms / n if n else 0.0) for k, (ms, n, _) in kernels.items()}
+    share = {k: per_launch[k] * per_eval[k] for k in kernels}
+    dom = max(share, key=share.get)
+    peak, peak_kind = measured_peaks()
+    bpl = kernels[dom][2]
+    achieved = bpl / (per_launch[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": peak_kind,
+            "bytes_per_launch": bpl, "timed_launches": kernels[dom][1],
+            "note": "1e6 particles (8 MB per slot array) per launch: launch- and "
+                    "latency-bound; event brackets add ~3 us to each timed launch"}
+    # end to end through the public API: theta -> objectives, .backward()
+    e2e = None
+    if not args.no_e2e:
+        spec, theta0 = B.adjoint_problem({k: v for k, v in kw.items() if k not in ("dt", "R_cm")},
+                                         ADJ_STEPS, ADJ_EVERY, z, u)
+        spec["params"].update(dt=kw["dt"], R_cm=kw["R_cm"])
+        reps = []
+        for i in range(3):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            th = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+            out = B.tube_objectives(th, spec)
+            out[0].backward()
+            g = th.grad.numpy().copy()
+            torch.cuda.synchronize()
+            if i > 0:
+                reps.append(time.perf_counter() - w0)
+        e2e = {"value": psteps / statistics.median(reps), "unit": UNIT,
+               "h2d_bytes_per_step": int(z.nbytes + u.nbytes),
+               "d2h_bytes_per_step": int(8 * (kw["Nz"] + 1) + 8 + 16 + 32),
+               "how": "tube_objectives(theta).backward(): driver creation, host particles in, "
+                      "forward, backward, gradient out; median of 2 after 1 warm-up",
+               "grad_matches": bool(np.allclose(g, grad_gamma, rtol=1e-9, atol=0))}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = adjoint_cpu_baseline(kw, d, z, u, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": work / el_s, "unit": UNIT, "n_gpus": ws,
+        "steps": n_eval * ADJ_STEPS, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el_s / (n_eval * ADJ_STEPS), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint_gr_tube_P0.3s_B1e12G_Nz16384_1e6_particles_fp32",
+                   "run_steps": ADJ_STEPS, "checkpoint_every": ADJ_EVERY,
+                   "gradient_evaluations": n_eval,
+                   "objective": "mean terminal gamma; d/d(B, P, R, w)",
+                   "l2": "each pass writes 16 MB per step of snapshots (1.6 GB per segment), "
+                         "larger than L2",
+                   "parallelism": "independent tube per GPU" if ws > 1 else "one tube"},
+        "adjoint": {"forward_ms": tf / n_eval, "backward_ms": tb / n_eval,
+                    "timed_segments": "every %dth" % ADJ_TIME_EVERY,
+                    "untimed_forward_ms": untimed_f, "untimed_backward_ms": untimed_b,
+                    "backward_ez_ms": bwd_ez_ms, "values": list(vals),
+                    "grad_gamma_BPRw": [float(x) for x in grad_gamma],
+                    "grad_ez_BPRw": [float(x) for x in grad_ez],
+                    "fp64_values": list(v64), "fp32_vs_fp64_values_rel_err": val_err32,
+                    "fp32_vs_fp64_grad_rel_err": err32,
+                    "kernels_ms_per_launch": per_launch,
+                    "kernels_share_per_evaluation": {k: v / sum(share.values())
+                                                     for k, v in share.items()}},
+        "plain_form": {"value": plain_value, "unit": UNIT, "steps": ADJ_STEPS,
+                       "how": "the same tube and particles stepped by tube_run (graphs), "
+                              "CUDA events around the run",
+                       "adjoint_over_plain": (work / el_s) / plain_value},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        # per evaluation: the graph kernels (forward, recompute without the
+        # last segment, reverse), the gather table, objectives (2) and seed
+        # launches and one gather table per recomputed segment
+        "gpu_launches": int(n_eval * (sum(per_eval.values()) + 4 + nseg - 1)),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    a.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

@@ -382,6 +382,19 @@ int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, doub
 int adjoint_timing(adjoint_t a, double* forward_ms, double* backward_ms,
                    int64_t* particle_steps);
 
+/* Per-kernel CUDA-event timing of the passes that follow: every > 0 times
+ * every every-th segment of each kind (recorded forward, recompute,
+ * reverse) with a graph that carries event-record nodes around each
+ * kernel (about 2-3 us each on this GPU, hence the sampling); 0 turns it
+ * off. Clears the totals. SCLF_EINVAL for every < 0. Synchronises. */
+int adjoint_set_timing(adjoint_t a, int every);
+
+/* Per-kernel totals of the timed segments since timing was enabled, 6
+ * entries each (host, may be NULL): forward particle, forward field,
+ * recompute particle, recompute field, reverse field, reverse particle
+ * kernels; ms = summed device time, launches = number of timed launches. */
+int adjoint_kernel_times(adjoint_t a, double* ms, int64_t* launches);
+
 /* ---- one pass without any device allocation --------------------------------
  * The paper has no counterpart to this call; it is here for users of the
  * library who cannot call cudaMalloc: an application whose own allocator has

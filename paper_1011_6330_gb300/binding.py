@@ -104,6 +104,8 @@ SIGNATURES = {
     "adjoint_backward": (_i32, [_vp, C.c_int32, _pd, _pd]),
     "adjoint_param_gradient": (_i32, [_vp, _pd, C.c_double, _pd]),
     "adjoint_timing": (_i32, [_vp, _pd, _pd, _pi64]),
+    "adjoint_set_timing": (_i32, [_vp, _i32]),
+    "adjoint_kernel_times": (_i32, [_vp, _pd, _pi64]),
     "tube_push_deposit_static": (_i32, [_vp, _vp, _i64, _vp, C.c_int32, C.c_double,
                                          C.c_double, C.c_double, _vp, _vp, _vp]),
     "tube_strerror": (C.c_char_p, [_i32]),
@@ -446,6 +448,20 @@ class Adjoint:
         _check(self.lib.adjoint_timing(self.h, C.byref(f), C.byref(b), C.byref(n)),
                "adjoint_timing")
         return {"forward_ms": f.value, "backward_ms": b.value, "particle_steps": n.value}
+
+    KERNELS = ("forward_push", "forward_field", "recompute_push", "recompute_field",
+               "reverse_field", "reverse_push")
+
+    def set_timing(self, every):
+        """Time every every-th segment of each kind (0 or False: off)."""
+        _check(self.lib.adjoint_set_timing(self.h, int(every)), "adjoint_set_timing")
+
+    def kernel_times(self):
+        ms = np.empty(6)
+        n = np.empty(6, np.int64)
+        _check(self.lib.adjoint_kernel_times(self.h, _dptr(ms), n.ctypes.data_as(_pi64)),
+               "adjoint_kernel_times")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
     def close(self):
         if getattr(self, "h", None):

@@ -49,8 +49,24 @@ struct sclf_adjoint {
     bool forward_done = false;
     bool use_ulog = false;
     int64_t current_seg = -1;       // segment whose steps the snapshots hold
-    cudaGraphExec_t g_fwd = nullptr, g_fwd_user = nullptr, g_recompute = nullptr,
-                    g_rev = nullptr;
+    // Segment graphs of the four kinds (recorded forward, forward with the
+    // caller's injections, recompute, reverse): one plain instance each and,
+    // in timing mode, two instances with event-record nodes around every
+    // kernel, replayed alternately so that one is read back while the other
+    // runs.
+    struct TimedGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev;   // 2K+1
+        bool pending = false;
+        int ka = 0, kb = 0;            // kernel kinds of its even and odd kernels
+    };
+    cudaGraphExec_t plain[4] = {nullptr, nullptr, nullptr, nullptr};
+    TimedGraph timed[4][2];
+    int tnext[4] = {0, 0, 0, 0};
+    int timing = 0;                 // 0: off; n > 0: every n-th segment of a kind is timed
+    int64_t seg_count[4] = {0, 0, 0, 0};
+    double kms[6] = {0, 0, 0, 0, 0, 0};        // per kernel kind since timing was enabled
+    int64_t klaunch[6] = {0, 0, 0, 0, 0, 0};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     float fwd_ms = 0.f, bwd_ms = 0.f;
     int64_t pslots = 0;
@@ -65,15 +81,23 @@ char* tab_of(sclf_adjoint* A, int k) {
 }
 double* ckf_of(sclf_adjoint* A, int64_t c) { return A->ck_f + c * (3 * A->nz + 1); }
 
+// An event-record node of a timed segment graph (ev non-null): event 0 goes
+// before the first kernel and events 2k+1, 2k+2 after the two kernels of
+// the graph's k-th step.
+cudaError_t mark(sclf_adjoint* A, const std::vector<cudaEvent_t>* ev, int i) {
+    if (!ev) return cudaSuccess;
+    return cudaEventRecordWithFlags((*ev)[i], A->t->gstream, cudaEventRecordExternal);
+}
+
 // K forward steps from snapshot 0: step k reads snapshot k and writes k+1.
 template <class Real>
 int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
-                    cudaGraphExec_t* out) {
+                    const std::vector<cudaEvent_t>* timed, cudaGraphExec_t* out) {
     sclf_tube* t = A->t;
     cudaStream_t s = t->gstream;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = mark(A, timed, 0);
     for (int k = 0; k < A->K && e == cudaSuccess; ++k) {
         PushArgs<Real> pa = push_args<Real>(t);
         pa.xi = reinterpret_cast<Real*>(A->sx[k]);
@@ -85,12 +109,14 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
         pa.evlog = evlog;
         pa.replay = replay;
         e = launch_push<Real>(pa, t->p.accumulate, t->push_grid, s);
+        if (e == cudaSuccess) e = mark(A, timed, 2 * k + 1);
         if (e != cudaSuccess) break;
         FieldArgs<Real> fa = field_args<Real>(t, k & 1);
         fa.jlast = A->jlog + static_cast<int64_t>(k) * A->nz;
         fa.ez2 = reinterpret_cast<Real*>(tab_of(A, k + 1));
         fa.evlog = evlog;
         e = launch_field<Real>(fa, t->p.accumulate, s);
+        if (e == cudaSuccess) e = mark(A, timed, 2 * k + 2);
     }
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
@@ -104,13 +130,15 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
 // The K steps of a segment in reverse: per step the transposed field update,
 // then the particles.
 template <class Real>
-int capture_reverse(sclf_adjoint* A, cudaGraphExec_t* out) {
+int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
+                    cudaGraphExec_t* out) {
     sclf_tube* t = A->t;
     cudaStream_t s = t->gstream;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int k = A->K - 1; k >= 0 && e == cudaSuccess; --k) {
+    cudaError_t e = mark(A, timed, 0);
+    int i = 0;                       // reversed step index: events 2i, 2i+1, 2i+2
+    for (int k = A->K - 1; k >= 0 && e == cudaSuccess; --k, ++i) {
         AdjFieldArgs<Real> fa;
         fa.lez = A->lez;
         fa.ler_in = A->ler[(k + 1) & 1];
@@ -126,6 +154,7 @@ int capture_reverse(sclf_adjoint* A, cudaGraphExec_t* out) {
         fa.fourpi_dt = t->fc.fourpi_dt;
         fa.s_over_dt = t->fc.s_over_dt;
         e = launch_adj_field<Real>(fa, s);
+        if (e == cudaSuccess) e = mark(A, timed, 2 * i + 1);
         if (e != cudaSuccess) break;
         AdjPushArgs<Real> pa;
         pa.xi = reinterpret_cast<const Real*>(A->sx[k]);
@@ -141,6 +170,7 @@ int capture_reverse(sclf_adjoint* A, cudaGraphExec_t* out) {
         pa.dt = static_cast<Real>(t->d.dt);
         pa.cfl = static_cast<Real>(t->d.dt / t->d.dz);
         e = launch_adj_push<Real>(pa, A->adj_grid, s);
+        if (e == cudaSuccess) e = mark(A, timed, 2 * i + 2);
     }
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
@@ -148,6 +178,77 @@ int capture_reverse(sclf_adjoint* A, cudaGraphExec_t* out) {
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     CK(e);
+    return SCLF_OK;
+}
+
+// Kernel kinds of the timing totals.
+enum { kFwdPush, kFwdField, kRecPush, kRecField, kRevField, kRevPush };
+// Segment graph kinds.
+enum { kGraphFwd, kGraphFwdUser, kGraphRecompute, kGraphRev };
+
+template <class Real>
+int capture_kind(sclf_adjoint* A, int kind, const std::vector<cudaEvent_t>* ev,
+                 cudaGraphExec_t* out) {
+    switch (kind) {
+        case kGraphFwd: return capture_forward<Real>(A, A->evlog, nullptr, ev, out);
+        case kGraphFwdUser: return capture_forward<Real>(A, A->evlog, A->ulog, ev, out);
+        case kGraphRecompute: return capture_forward<Real>(A, nullptr, A->evlog, ev, out);
+        default: return capture_reverse<Real>(A, ev, out);
+    }
+}
+
+// Add a replayed timed graph's kernel durations to the totals (waits for it).
+int collect(sclf_adjoint* A, sclf_adjoint::TimedGraph& g) {
+    if (!g.pending) return SCLF_OK;
+    CK(cudaEventSynchronize(g.ev[2 * A->K]));
+    for (int k = 0; k < A->K; ++k) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, g.ev[2 * k], g.ev[2 * k + 1]));
+        CK(cudaEventElapsedTime(&b, g.ev[2 * k + 1], g.ev[2 * k + 2]));
+        A->kms[g.ka] += a;
+        A->kms[g.kb] += b;
+    }
+    A->klaunch[g.ka] += A->K;
+    A->klaunch[g.kb] += A->K;
+    g.pending = false;
+    return SCLF_OK;
+}
+
+int collect_all(sclf_adjoint* A) {
+    for (auto& pair : A->timed)
+        for (auto& g : pair) {
+            const int rc = collect(A, g);
+            if (rc) return rc;
+        }
+    return SCLF_OK;
+}
+
+// Launch one segment graph of the given kind (building it on first use). In
+// timing mode every n-th segment of a kind replays a timed instance, after
+// reading back the one replayed two timed launches ago.
+template <class Real>
+int launch_segment(sclf_adjoint* A, int kind, int ka, int kb) {
+    int rc;
+    const bool timed = A->timing > 0 && A->seg_count[kind]++ % A->timing == 0;
+    if (!timed) {
+        if (!A->plain[kind] && (rc = capture_kind<Real>(A, kind, nullptr, &A->plain[kind])))
+            return rc;
+        CK(cudaGraphLaunch(A->plain[kind], A->t->gstream));
+        return SCLF_OK;
+    }
+    auto& g = A->timed[kind][A->tnext[kind]];
+    if (!g.exec) {
+        g.ev.assign(2 * A->K + 1, nullptr);
+        for (cudaEvent_t& e : g.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return SCLF_ECUDA; }
+        if ((rc = capture_kind<Real>(A, kind, &g.ev, &g.exec))) return rc;
+    }
+    if ((rc = collect(A, g))) return rc;
+    CK(cudaGraphLaunch(g.exec, A->t->gstream));
+    g.pending = true;
+    g.ka = ka;
+    g.kb = kb;
+    A->tnext[kind] ^= 1;
     return SCLF_OK;
 }
 
@@ -219,18 +320,15 @@ int run_forward(sclf_adjoint* A, double* values) {
         if (rc) return rc;
     }
     CK(table0<Real>(A));
-    cudaGraphExec_t* g = A->use_ulog ? &A->g_fwd_user : &A->g_fwd;
-    if (!*g) {
-        rc = capture_forward<Real>(A, A->evlog, A->use_ulog ? A->ulog : nullptr, g);
-        if (rc) return rc;
-    }
+    const int kind = A->use_ulog ? kGraphFwdUser : kGraphFwd;
     CK(cudaEventRecord(A->ev[0], s));
     for (int64_t c = 0; c < A->nseg; ++c) {
         if (c > 0) {
             rc = save_checkpoint(A, c, 0);
             if (rc) return rc;
         }
-        CK(cudaGraphLaunch(*g, s));
+        rc = launch_segment<Real>(A, kind, kFwdPush, kFwdField);
+        if (rc) return rc;
         if (c + 1 < A->nseg) {
             CK(cudaMemcpyAsync(A->sx[0], A->sx[A->K], bytes, cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(A->su[0], A->su[A->K], bytes, cudaMemcpyDeviceToDevice, s));
@@ -252,6 +350,7 @@ int run_forward(sclf_adjoint* A, double* values) {
     CK(cudaMemcpyAsync(hv, A->values, sizeof(hv), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(log.data(), A->evlog, log.size() * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((rc = collect_all(A))) return rc;
     CK(cudaEventElapsedTime(&A->fwd_ms, A->ev[0], A->ev[1]));
     A->pslots = 0;
     for (int64_t n = 0; n < A->nsteps; ++n)
@@ -269,14 +368,6 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
     const int64_t nz = A->nz;
     const int64_t bytes = A->cap_pad * A->rs;
     int rc;
-    if (!A->g_recompute) {
-        rc = capture_forward<Real>(A, nullptr, A->evlog, &A->g_recompute);
-        if (rc) return rc;
-    }
-    if (!A->g_rev) {
-        rc = capture_reverse<Real>(A, &A->g_rev);
-        if (rc) return rc;
-    }
     // seeds at the end of the run (checkpoint nseg)
     CK(cudaMemsetAsync(A->lez, 0, nz * 8, s));
     CK(cudaMemsetAsync(A->ler[0], 0, (nz + 1) * 8, s));
@@ -298,12 +389,14 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
             rc = restore_checkpoint(A, c);
             if (rc) return rc;
             CK(table0<Real>(A));
-            CK(cudaGraphLaunch(A->g_recompute, s));
+            rc = launch_segment<Real>(A, kGraphRecompute, kRecPush, kRecField);
+            if (rc) return rc;
             A->current_seg = c;
         }
         CK(cudaMemcpyAsync(A->seglog, A->evlog + static_cast<int64_t>(kLogStride) * c * A->K,
                            static_cast<int64_t>(kLogStride) * A->K * 8, cudaMemcpyDeviceToDevice, s));
-        CK(cudaGraphLaunch(A->g_rev, s));
+        rc = launch_segment<Real>(A, kGraphRev, kRevField, kRevPush);
+        if (rc) return rc;
     }
     CK(cudaEventRecord(A->ev[3], s));
     // the tube shows the end of the run again
@@ -314,6 +407,7 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
     CK(cudaMemcpyAsync(lphi.data(), A->ler[0], (nz + 1) * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(lsum.data(), A->lsum, nz * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((rc = collect_all(A))) return rc;
     CK(cudaEventElapsedTime(&A->bwd_ms, A->ev[2], A->ev[3]));
     // t = 0: E_z = -(phi_{j+1} - phi_j)/dz, E_r = phi; phi from Eq. 4 with
     // source rho_GJ - rho_particles(s)
@@ -335,8 +429,14 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
 void free_adjoint(sclf_adjoint* A) {
     if (!A) return;
     if (A->t) cudaStreamSynchronize(A->t->gstream);
-    for (cudaGraphExec_t g : {A->g_fwd, A->g_fwd_user, A->g_recompute, A->g_rev})
+    for (cudaGraphExec_t g : A->plain)
         if (g) cudaGraphExecDestroy(g);
+    for (auto& pair : A->timed)
+        for (auto& g : pair) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            for (cudaEvent_t e : g.ev)
+                if (e) cudaEventDestroy(e);
+        }
     for (cudaEvent_t e : A->ev)
         if (e) cudaEventDestroy(e);
     if (A->mem) cudaFree(A->mem);
@@ -507,6 +607,26 @@ int adjoint_timing(adjoint_t a, double* forward_ms, double* backward_ms, int64_t
     if (forward_ms) *forward_ms = a->fwd_ms;
     if (backward_ms) *backward_ms = a->bwd_ms;
     if (particle_steps) *particle_steps = a->pslots;
+    return SCLF_OK;
+}
+
+int adjoint_set_timing(adjoint_t a, int every) {
+    if (!a || every < 0) return SCLF_EINVAL;
+    CK(cudaStreamSynchronize(a->t->gstream));
+    for (auto& pair : a->timed)
+        for (auto& g : pair) g.pending = false;      // discard an earlier session
+    a->timing = every;
+    for (int64_t& c : a->seg_count) c = 0;
+    for (int i = 0; i < 6; ++i) { a->kms[i] = 0.0; a->klaunch[i] = 0; }
+    return SCLF_OK;
+}
+
+int adjoint_kernel_times(adjoint_t a, double* ms, int64_t* launches) {
+    if (!a) return SCLF_EINVAL;
+    for (int i = 0; i < 6; ++i) {
+        if (ms) ms[i] = a->kms[i];
+        if (launches) launches[i] = a->klaunch[i];
+    }
     return SCLF_OK;
 }
 

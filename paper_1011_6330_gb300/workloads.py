@@ -54,6 +54,19 @@ def large_tube(n_particles=2 ** 30, Nz=2 ** 20, capacity=None, track_ids=0):
                    track_ids=track_ids)
 
 
+def adjoint_tube(n_particles=10 ** 6, Nz=16384, precision=B.SCLF_FP32):
+    """Frame-dragging tube of a B = 1e12 G, P = 0.3 s pulsar (R_* = 10 km,
+    length 2 R_*, GR rho_GJ at i = 0.5) with Nz = 16384 and 1e6 FP32
+    macro-electrons, for gradients of a 2000-step run checkpointed every
+    100 steps. dt and R are fixed explicitly (their derived values) so that
+    perturbing (B, P, R) leaves the grid alone."""
+    kw = gr_tube(B_G=1e12, P_s=0.3, Nz=Nz, n_particles=n_particles, precision=precision,
+                 accumulate=B.SCLF_ACC_FIXED64)
+    d = B.derive(B.default_params(**kw))
+    kw.update(dt=d["dt"], R_cm=d["R_cm"])
+    return kw
+
+
 def death_line_batch(n_tubes=256, seed=0, nz_min=1024, nz_max=16384, n_min=10 ** 5,
                      n_max=2 * 10 ** 6):
     """Batch of independent pulsar tubes for death-line / pair-front sweeps:

@@ -193,3 +193,27 @@ def test_adjoint_rejects_unsupported_states(gpu_lib):
     with pytest.raises(B.SclfError):
         a.tube.step()                              # the driver steps its tube
     a.close()
+
+
+def test_timed_passes_count_kernels_and_keep_the_gradient(gpu_lib):
+    """Timing mode replays graphs with event-record nodes: the launch counts
+    are those of the checkpoint schedule (the last segment is not
+    recomputed) and the gradient is unchanged."""
+    kw, z, u, nsteps, K = flat_problem(B.SCLF_FP32, n=5000, nsteps=40, K=10)
+    a, _ = gpu_run(kw, z, u, nsteps, K)
+    g0, s0 = a.backward(B.SCLF_OBJ_GAMMA)
+    a.set_timing(1)
+    a.forward()
+    g1, s1 = a.backward(B.SCLF_OBJ_GAMMA)
+    kt = a.kernel_times()
+    assert kt["forward_push"][1] == nsteps and kt["forward_field"][1] == nsteps
+    assert kt["recompute_push"][1] == nsteps - K and kt["reverse_push"][1] == nsteps
+    assert all(ms > 0.0 for ms, n in kt.values())
+    assert rel(g1, g0) <= 1e-12 and abs(s1 - s0) <= 1e-12 * abs(s0)
+    a.set_timing(2)                          # segments 0 and 2 of each kind
+    a.forward()
+    a.backward(B.SCLF_OBJ_GAMMA)
+    kt = a.kernel_times()
+    assert kt["forward_push"][1] == 2 * K and kt["reverse_push"][1] == 2 * K
+    assert kt["recompute_push"][1] == 2 * K      # 3 recomputed segments: 1st and 3rd
+    a.close()
