@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-kernel-timing", action="store_true",
+                    help="adjoint workload: no event-record nodes (for ncu runs, where "
+                         "each event node is very slow); no per-kernel times or roofline")
     return ap.parse_args()
 
 
@@ -446,16 +449,18 @@ def run_adjoint(args):
     z, u = adjoint_state(B, kw, rank_seed(rank))
     a = B.Adjoint(B.default_params(**kw), ADJ_STEPS, ADJ_EVERY)
     a.tube.add_particles(z, u)
-    n_eval = max(3, args.steps // ADJ_STEPS)
+    n_eval = max(1, args.steps // ADJ_STEPS)
+    timed = not args.no_kernel_timing
     for _ in range(max(1, args.warmup // 4)):
         a.forward()
         a.backward(B.SCLF_OBJ_GAMMA)
-    a.set_timing(1)                          # builds both timed instances of each graph
-    a.forward()
-    a.backward(B.SCLF_OBJ_GAMMA)
-    # timed region: every TIME_EVERY-th segment replays a graph with event
-    # nodes around each kernel (they cost 2-3 us each against ~10 us kernels)
-    a.set_timing(ADJ_TIME_EVERY)
+    if timed:
+        a.set_timing(1)                      # builds both timed instances of each graph
+        a.forward()
+        a.backward(B.SCLF_OBJ_GAMMA)
+        # timed region: every TIME_EVERY-th segment replays a graph with event
+        # nodes around each kernel (they cost 2-3 us each against ~10 us kernels)
+        a.set_timing(ADJ_TIME_EVERY)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
@@ -513,6 +518,8 @@ def run_adjoint(args):
     # and out, J and the float gather table out) and 76 B per cell in reverse
     slots = psteps / ADJ_STEPS
     nzc = kw["Nz"]
+    if not timed:
+        kt = {k: (0.0, 0) for k in B.Adjoint.KERNELS}
     kernels = {
         "push_kernel": (kt["forward_push"][0] + kt["recompute_push"][0],
                         kt["forward_push"][1] + kt["recompute_push"][1], 16 * slots),
@@ -526,15 +533,18 @@ def run_adjoint(args):
                 "adj_push_kernel": ADJ_STEPS, "adj_field_kernel": ADJ_STEPS}
     per_launch = {k: (ms / n if n else 0.0) for k, (ms, n, _) in kernels.items()}
     share = {k: per_launch[k] * per_eval[k] for k in kernels}
-    dom = max(share, key=share.get)
-    peak, peak_kind = measured_peaks()
-    bpl = kernels[dom][2]
-    achieved = bpl / (per_launch[dom] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": peak_kind,
-            "bytes_per_launch": bpl, "timed_launches": kernels[dom][1],
-            "note": "1e6 particles (8 MB per slot array) per launch: launch- and "
-                    "latency-bound; event brackets add ~3 us to each timed launch"}
+    roof = None
+    if timed:
+        dom = max(share, key=share.get)
+        peak, peak_kind = measured_peaks()
+        bpl = kernels[dom][2]
+        achieved = bpl / (per_launch[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": peak_kind, "bytes_per_launch": bpl,
+                "timed_launches": kernels[dom][1],
+                "note": "1e6 particles (8 MB per slot array) per launch: launch- and "
+                        "latency-bound; event brackets add ~3 us to each timed launch"}
     # end to end through the public API: theta -> objectives, .backward()
     e2e = None
     if not args.no_e2e:
@@ -574,7 +584,7 @@ def run_adjoint(args):
                          "larger than L2",
                    "parallelism": "independent tube per GPU" if ws > 1 else "one tube"},
         "adjoint": {"forward_ms": tf / n_eval, "backward_ms": tb / n_eval,
-                    "timed_segments": "every %dth" % ADJ_TIME_EVERY,
+                    "timed_segments": ("every %dth" % ADJ_TIME_EVERY) if timed else "none",
                     "untimed_forward_ms": untimed_f, "untimed_backward_ms": untimed_b,
                     "backward_ez_ms": bwd_ez_ms, "values": list(vals),
                     "grad_gamma_BPRw": [float(x) for x in grad_gamma],
@@ -582,8 +592,9 @@ def run_adjoint(args):
                     "fp64_values": list(v64), "fp32_vs_fp64_values_rel_err": val_err32,
                     "fp32_vs_fp64_grad_rel_err": err32,
                     "kernels_ms_per_launch": per_launch,
-                    "kernels_share_per_evaluation": {k: v / sum(share.values())
-                                                     for k, v in share.items()}},
+                    "kernels_share_per_evaluation": ({k: v / sum(share.values())
+                                                      for k, v in share.items()}
+                                                     if timed else None)},
         "plain_form": {"value": plain_value, "unit": UNIT, "steps": ADJ_STEPS,
                        "how": "the same tube and particles stepped by tube_run (graphs), "
                               "CUDA events around the run",
