@@ -36,7 +36,8 @@ UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 16          # FP32 xi and u, read once and written once per step
 CSRC = os.path.join(ROOT, "paper_1011_6330_gb300", "csrc")
 KERNEL_SRC = {"gr1e8": ["push.cu", "device_common.cuh", "sclf_internal.h"],
-              "large": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"]}
+              "large": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"],
+              "batch": ["push.cu", "device_common.cuh", "sclf_internal.h"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
 
 
@@ -327,6 +328,13 @@ def run_batch(args):
     slots = tm["particle_slots"] / max(tm["n_steps"], 1)
     achieved = BYTES_PER_PARTICLE * slots / (push_avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            ent = json.load(f).get("batch", {})
+        if ent.get("kernel_sha") == kernel_sha("batch") and ent.get("tubes") == len(kws) \
+                and ws == 1:
+            traffic = ent["bytes_per_launch"]
     # the plain form: the same tubes, one tube at a time
     k_plain = min(args.steps, 128)
     for t in plain:
@@ -370,7 +378,7 @@ def run_batch(args):
         "plain_form": {"value": plain_value, "unit": UNIT, "steps": k_plain,
                        "how": "the same 256 tubes, each stepped alone (tube_run, graphs)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "batch_push_kernel",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "batch_push_kernel",
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],

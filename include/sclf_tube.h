@@ -57,6 +57,11 @@ extern "C" {
 #define SCLF_RHO_GR   1      /* Eq. 6 with omega from Eq. 7, f = H = alpha = 1 */
 #define SCLF_RHO_USER 2      /* caller-supplied rho_GJ at the Nz+1 nodes      */
 
+/* Frame-dragging variants of Eq. 6 (tube_params.gr_variant) */
+#define SCLF_GR_COS  0       /* Omega -> Omega - omega on the cos i term only    */
+#define SCLF_GR_BOTH 1       /* Omega -> Omega - omega on Eq. 6's prefactor, i.e.
+                                (1 - kappa/eta^3) on both terms                 */
+
 #define SCLF_FP32 0          /* particle arithmetic in IEEE float32           */
 #define SCLF_FP64 1          /* particle arithmetic in IEEE float64           */
 #define SCLF_FIX32 2         /* int32 fixed-point positions X = xi 2^fb with
@@ -109,6 +114,18 @@ typedef struct tube_params {
                               of the slots or would add a quarter to the
                               free slots                                     */
     int32_t use_graphs;    /* 1: tube_run replays captured CUDA graphs        */
+    /* Eq. 6 in full (SCLF_RHO_GR only; ignored otherwise):
+       rho = -(Omega B / 2 pi c alpha) (f / f(1))
+             [(1 - omega/Omega) cos i + 3/2 eta^(1/2) (H / f^(1/2)) theta_* sin i]
+       with the (R_* / r)^3 factor dropped.                                   */
+    int32_t gr_variant;    /* SCLF_GR_COS (default) or SCLF_GR_BOTH           */
+    int32_t gr_alpha;      /* 1: divide by the redshift alpha = (1 - r_g/r)^(1/2);
+                              0: alpha = 1                                    */
+    const double* gr_f;    /* host, Nz+1 values of f(eta) at the nodes (f > 0),
+                              or NULL for f = 1; read by tube_create, kept by
+                              the tube (f(1) = the value at node 0)           */
+    const double* gr_H;    /* host, Nz+1 values of H(eta) at the nodes, or NULL
+                              for H = 1; read by tube_create, kept by the tube */
 } tube_params;
 
 /* Code-unit quantities derived from tube_params (all FP64). */
@@ -163,6 +180,12 @@ int tube_params_default(tube_params* p);
 /* Validate p and compute the derived code-unit quantities (host only, no
  * CUDA). Units: Sec. 3 normalisation; rho_GJ(0) from Eq. 5 or Eq. 6. */
 int tube_derive(const tube_params* p, tube_derived* d);
+
+/* rho_GJ at the Nz+1 nodes (host only, no CUDA) in code units, as
+ * tube_create builds it: Eq. 5 (flat), Eq. 6 with Eq. 7 (frame dragging,
+ * gr_variant, gr_alpha, gr_f, gr_H) or the caller's profile. rho: host,
+ * Nz+1 doubles. SCLF_EINVAL for invalid parameters. */
+int tube_rho_gj_profile(const tube_params* p, double* rho);
 
 /* Bytes of device memory a tube with these parameters needs. */
 int tube_workspace_bytes(const tube_params* p, int64_t* bytes);

@@ -120,28 +120,44 @@ def code_units(B_G, P_s, Rstar_cm, incl_rad, mass_g, R_cm=0.0):
                 R_over_Rstar=R / Rstar_cm, incl=incl_rad)
 
 
-def rho_gj_profile(mode, z, Lambda0, incl, theta_star, R_over_Rstar, kappa):
+def rho_gj_profile(mode, z, Lambda0, incl, theta_star, R_over_Rstar, kappa,
+                   variant="cos", f=None, H=None, rg_over_Rstar=None):
     """rho_GJ at heights z (in R), code units.
 
     Flat space, Eq. 5 with the (R_*/r)^3 factor dropped (constant-radius
     tube, text after Eq. 5), phi = 0 (so cos(phi) = 1):
         rho = -(Lambda0^2 / 4 pi) [cos i + 3/2 sqrt(eta) theta_* sin i]
-    Frame dragging, Eq. 6 with Omega -> Omega - omega on the cos i term,
-    omega / Omega = kappa / eta^3 (Eq. 7), f = H = alpha = 1 (the paper
-    gives them only by reference) and the (R_*/r)^3 factor dropped as in
-    the flat case:
-        rho = -(Lambda0^2 / 4 pi) [(1 - kappa/eta^3) cos i
-                                   + 3/2 sqrt(eta) theta_* sin i]
-    eta = r / R_* = 1 + z R / R_*. The unit of density is the aligned
-    surface value, so Lambda0^2 / 4 pi = Omega B / (2 pi c) in code units.
+    Frame dragging, Eq. 6 with omega / Omega = kappa / eta^3 (Eq. 7) and the
+    (R_*/r)^3 factor dropped as in the flat case:
+        rho = -(Lambda0^2 / 4 pi) (f / f(1)) / alpha
+              [(1 - kappa/eta^3) cos i + 3/2 sqrt(eta) (H / f^(1/2)) theta_* sin i]
+    with f, H the curved-space factors at the given heights (f = H = 1 when
+    None: the paper gives them only by reference; f(1), the base value, is
+    f's first entry, so z must start at the base) and alpha = (1 - r_g/r)^(1/2)
+    when rg_over_Rstar is given (else alpha = 1). variant='both' applies
+    Omega -> Omega - omega to Eq. 6's prefactor instead, so the factor
+    (1 - kappa/eta^3) multiplies both terms. eta = r / R_* = 1 + z R / R_*.
+    The unit of density is the aligned surface value, so Lambda0^2 / 4 pi =
+    Omega B / (2 pi c) in code units.
     """
     z = np.asarray(z, dtype=np.float64)
     eta = 1.0 + z * R_over_Rstar
-    sin_term = 1.5 * np.sqrt(eta) * theta_star * math.sin(incl)
     if mode == RHO_FLAT:
-        bracket = math.cos(incl) + sin_term
+        bracket = math.cos(incl) + 1.5 * np.sqrt(eta) * theta_star * math.sin(incl)
     elif mode == RHO_GR:
-        bracket = (1.0 - kappa / eta ** 3) * math.cos(incl) + sin_term
+        fz = np.ones_like(eta) if f is None else np.asarray(f, np.float64)
+        hz = np.ones_like(eta) if H is None else np.asarray(H, np.float64)
+        f1 = 1.0 if f is None else float(np.asarray(f, np.float64).ravel()[0])
+        sin_term = 1.5 * np.sqrt(eta) * (hz / np.sqrt(fz)) * theta_star * math.sin(incl)
+        drag = 1.0 - kappa / eta ** 3
+        if variant == "cos":
+            bracket = drag * math.cos(incl) + sin_term
+        elif variant == "both":
+            bracket = drag * (math.cos(incl) + sin_term)
+        else:
+            raise ValueError("variant must be 'cos' or 'both'")
+        alpha = 1.0 if rg_over_Rstar is None else np.sqrt(1.0 - rg_over_Rstar / eta)
+        bracket = (fz / f1) / alpha * bracket
     else:
         raise ValueError("mode must be RHO_FLAT or RHO_GR")
     return -(Lambda0 ** 2 / (4.0 * math.pi)) * bracket

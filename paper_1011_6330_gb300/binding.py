@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(PKG, "libsclf_tube.so")
 HEADER = os.path.join(ROOT, "include", "sclf_tube.h")
 
 SCLF_RHO_FLAT, SCLF_RHO_GR, SCLF_RHO_USER = 0, 1, 2
+SCLF_GR_COS, SCLF_GR_BOTH = 0, 1
 SCLF_FP32, SCLF_FP64, SCLF_FIX32 = 0, 1, 2
 SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
 FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
@@ -36,6 +37,8 @@ class TubeParams(C.Structure):
         ("target_particles", C.c_int64), ("capacity", C.c_int64),
         ("accumulate", C.c_int32), ("track_ids", C.c_int32),
         ("compact_interval", C.c_int32), ("use_graphs", C.c_int32),
+        ("gr_variant", C.c_int32), ("gr_alpha", C.c_int32),
+        ("gr_f", C.POINTER(C.c_double)), ("gr_H", C.POINTER(C.c_double)),
     ]
 
 
@@ -70,6 +73,7 @@ SIGNATURES = {
     "tube_params_default": (_i32, [C.POINTER(TubeParams)]),
     "tube_derive": (_i32, [C.POINTER(TubeParams), C.POINTER(TubeDerived)]),
     "tube_workspace_bytes": (_i32, [C.POINTER(TubeParams), _pi64]),
+    "tube_rho_gj_profile": (_i32, [C.POINTER(TubeParams), _pd]),
     "tube_create": (_i32, [C.POINTER(TubeParams), _vp, _i64, _vp, C.POINTER(_vp)]),
     "tube_destroy": (_i32, [_vp]),
     "tube_get_derived": (_i32, [_vp, C.POINTER(TubeDerived)]),
@@ -149,19 +153,27 @@ def _dptr(a):
     return a.ctypes.data_as(_pd) if a is not None else None
 
 
+_ARRAY_PARAMS = ("rho_gj_user", "gr_f", "gr_H")
+
+
 def default_params(**kw):
-    """tube_params_default() with keyword overrides (rho_gj_user: array)."""
+    """tube_params_default() with keyword overrides (rho_gj_user, gr_f, gr_H:
+    arrays of Nz+1 node values, or None)."""
     lib = load()
     p = TubeParams()
     _check(lib.tube_params_default(C.byref(p)), "tube_params_default")
-    keep = None
+    keep = []
     for k, v in kw.items():
-        if k == "rho_gj_user":
-            keep = np.ascontiguousarray(v, dtype=np.float64)
-            p.rho_gj_user = keep.ctypes.data_as(_pd)
+        if k in _ARRAY_PARAMS:
+            if v is None:
+                setattr(p, k, None)
+                continue
+            a = np.ascontiguousarray(v, dtype=np.float64)
+            keep.append(a)
+            setattr(p, k, a.ctypes.data_as(_pd))
         else:
             setattr(p, k, v)
-    p._keep = keep      # keep the user profile alive with the struct
+    p._keep = keep      # keep the arrays alive with the struct
     return p
 
 
@@ -170,6 +182,14 @@ def derive(params):
     d = TubeDerived()
     _check(lib.tube_derive(C.byref(params), C.byref(d)), "tube_derive")
     return {n: getattr(d, n) for n, _ in TubeDerived._fields_}
+
+
+def rho_gj_profile(params):
+    """rho_GJ at the Nz+1 nodes as the library builds it (host only)."""
+    lib = load()
+    rho = np.empty(int(params.Nz) + 1)
+    _check(lib.tube_rho_gj_profile(C.byref(params), _dptr(rho)), "tube_rho_gj_profile")
+    return rho
 
 
 def workspace_bytes(params):

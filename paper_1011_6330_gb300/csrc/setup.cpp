@@ -17,16 +17,30 @@ constexpr double kMe = 9.1093837015e-28;      // electron mass [g]
 constexpr double kG = 6.67430e-8;             // gravitational constant
 constexpr double kPi = 3.14159265358979323846;
 
-// rho_GJ / (Lambda0^2 / 4 pi) at dimensionless radius eta = r / R_*.
+// rho_GJ / (-(Lambda0^2 / 4 pi)) at dimensionless radius eta = r / R_*.
 // Flat (Eq. 5): cos i + 3/2 sqrt(eta) theta_* sin i   (cos(phi) = 1, the
 // (R_* / r)^3 factor dropped for the constant-radius tube).
-// Frame dragging (Eq. 6 with Omega -> Omega - omega on the cos i term,
-// omega / Omega = kappa / eta^3 from Eq. 7, f = H = alpha = 1).
-double bracket(int mode, double eta, const tube_params* p, const tube_derived* d) {
-    const double sin_term = 1.5 * std::sqrt(eta) * d->theta_star * std::sin(p->incl_rad);
-    if (mode == SCLF_RHO_GR)
-        return (1.0 - d->kappa / (eta * eta * eta)) * std::cos(p->incl_rad) + sin_term;
-    return std::cos(p->incl_rad) + sin_term;
+// Frame dragging (Eq. 6 with omega / Omega = kappa / eta^3 from Eq. 7):
+//   (f / f1) / alpha [(1 - kappa/eta^3) cos i + 3/2 sqrt(eta) (H / sqrt(f)) theta_* sin i]
+// or, for SCLF_GR_BOTH (Omega -> Omega - omega on the prefactor),
+//   (f / f1) / alpha (1 - kappa/eta^3) [cos i + 3/2 sqrt(eta) (H / sqrt(f)) theta_* sin i],
+// with f, H the curved-space factors at this node (1 without tables), f1 = f
+// at the base and alpha = sqrt(1 - r_g / r) when gr_alpha is set.
+double shape(const tube_params* p, const tube_derived* d, double eta, double f, double f1,
+             double H) {
+    if (p->rho_gj_mode != SCLF_RHO_GR)
+        return std::cos(p->incl_rad) + 1.5 * std::sqrt(eta) * d->theta_star * std::sin(p->incl_rad);
+    const double sin_term =
+        1.5 * std::sqrt(eta) * (H / std::sqrt(f)) * d->theta_star * std::sin(p->incl_rad);
+    const double drag = 1.0 - d->kappa / (eta * eta * eta);
+    const double bracket = p->gr_variant == SCLF_GR_BOTH ? drag * (std::cos(p->incl_rad) + sin_term)
+                                                          : drag * std::cos(p->incl_rad) + sin_term;
+    double alpha = 1.0;
+    if (p->gr_alpha) {
+        const double rg_over_rstar = 2.0 * kG * p->mass_g / (kC * kC) / p->Rstar_cm;
+        alpha = std::sqrt(1.0 - rg_over_rstar / eta);
+    }
+    return (f / f1) / alpha * bracket;
 }
 }  // namespace
 
@@ -44,6 +58,15 @@ int derive(const tube_params* p, tube_derived* d) {
     if (p->rho_gj_mode == SCLF_RHO_USER && !p->rho_gj_user) return SCLF_EINVAL;
     if (!(p->capacity >= 0 && p->capacity <= (int64_t(1) << 31) - kMaxTile)) return SCLF_EINVAL;
     if (p->compact_interval < 0) return SCLF_EINVAL;
+    if (p->gr_variant != SCLF_GR_COS && p->gr_variant != SCLF_GR_BOTH) return SCLF_EINVAL;
+    if (p->gr_alpha != 0 && p->gr_alpha != 1) return SCLF_EINVAL;
+    if (p->rho_gj_mode == SCLF_RHO_GR) {
+        for (int64_t j = 0; j <= p->Nz; ++j) {
+            if (p->gr_f && !(std::isfinite(p->gr_f[j]) && p->gr_f[j] > 0.0)) return SCLF_EINVAL;
+            if (p->gr_H && !std::isfinite(p->gr_H[j])) return SCLF_EINVAL;
+        }
+        if (p->gr_alpha && !(2.0 * kG * p->mass_g / (kC * kC) < p->Rstar_cm)) return SCLF_EINVAL;
+    }
 
     if (p->rho_gj_mode == SCLF_RHO_GR && !(p->P_s > 0.0 && p->Rstar_cm > 0.0 && p->mass_g >= 0.0))
         return SCLF_EINVAL;
@@ -77,7 +100,8 @@ int derive(const tube_params* p, tube_derived* d) {
     if (p->rho_gj_mode == SCLF_RHO_USER) {
         d->rho0 = p->rho_gj_user[0];
     } else {
-        d->rho0 = -(d->Lambda0 * d->Lambda0 / (4.0 * kPi)) * bracket(p->rho_gj_mode, 1.0, p, d);
+        const double f0 = p->gr_f ? p->gr_f[0] : 1.0, h0 = p->gr_H ? p->gr_H[0] : 1.0;
+        d->rho0 = -(d->Lambda0 * d->Lambda0 / (4.0 * kPi)) * shape(p, d, 1.0, f0, f0, h0);
     }
     if (!std::isfinite(d->rho0)) return SCLF_EINVAL;
     if (p->macro_charge != 0.0) {
@@ -101,10 +125,12 @@ int build_rho_gj(const tube_params* p, const tube_derived* d, double* rho) {
         return SCLF_OK;
     }
     const double scale = -(d->Lambda0 * d->Lambda0 / (4.0 * kPi));
+    const double f1 = p->gr_f ? p->gr_f[0] : 1.0;
     for (int64_t j = 0; j <= nz; ++j) {
         const double z = double(j) * d->dz;                 // in R
         const double eta = 1.0 + z * d->R_over_Rstar;       // r / R_*
-        rho[j] = scale * bracket(p->rho_gj_mode, eta, p, d);
+        rho[j] = scale * shape(p, d, eta, p->gr_f ? p->gr_f[j] : 1.0, f1,
+                               p->gr_H ? p->gr_H[j] : 1.0);
     }
     return SCLF_OK;
 }

@@ -381,6 +381,14 @@ int tube_params_default(tube_params* p) {
 
 int tube_derive(const tube_params* p, tube_derived* d) { return derive(p, d); }
 
+int tube_rho_gj_profile(const tube_params* p, double* rho) {
+    if (!p || !rho) return SCLF_EINVAL;
+    tube_derived d;
+    const int rc = derive(p, &d);
+    if (rc) return rc;
+    return build_rho_gj(p, &d, rho);
+}
+
 int tube_workspace_bytes(const tube_params* p, int64_t* bytes) {
     if (!p || !bytes) return SCLF_EINVAL;
     tube_derived d;
@@ -400,6 +408,11 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     t->p.rho_gj_user = nullptr;
     int rc = derive(p, &t->d);
     if (rc) { delete t; return rc; }
+    // the Eq. 6 tables stay with the tube (the adjoint's parameter chain reads them)
+    if (p->rho_gj_mode == SCLF_RHO_GR && p->gr_f) t->gr_f.assign(p->gr_f, p->gr_f + p->Nz + 1);
+    if (p->rho_gj_mode == SCLF_RHO_GR && p->gr_H) t->gr_H.assign(p->gr_H, p->gr_H + p->Nz + 1);
+    t->p.gr_f = t->gr_f.empty() ? nullptr : t->gr_f.data();
+    t->p.gr_H = t->gr_H.empty() ? nullptr : t->gr_H.data();
     t->lay = plan(p);
     t->fb = p->precision == SCLF_FIX32 ? fix32_bits(p->Nz) : 0;
     t->stream = static_cast<cudaStream_t>(stream);

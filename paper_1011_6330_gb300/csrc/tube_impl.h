@@ -43,6 +43,7 @@ struct sclf_tube {
     void* ez2 = nullptr;
     double* rho_acc = nullptr;
     std::vector<double> rho_gj;
+    std::vector<double> gr_f, gr_H;     // copies of the caller's Eq. 6 tables (p points here)
     sclf::FieldConsts fc{};
     int push_grid = 0, compact_grid = 0;
     int fb = 0;                        // fractional bits of SCLF_FIX32 positions

@@ -97,3 +97,38 @@ def test_adjoint_create_validates_before_touching_the_device():
         assert lib.adjoint_create(C.byref(p), n, k, None, C.byref(h)) == -1
     assert lib.adjoint_backward(None, 0, None, None) == -1
     assert lib.adjoint_forward(None, None) == -1
+
+
+@pytest.mark.parametrize("variant,alpha,tables", [
+    (B.SCLF_GR_COS, 0, False), (B.SCLF_GR_BOTH, 0, False),
+    (B.SCLF_GR_COS, 1, False), (B.SCLF_GR_BOTH, 1, True), (B.SCLF_GR_COS, 0, True)])
+def test_host_rho_gj_profile_matches_oracle_eq6_variants(variant, alpha, tables):
+    """The library's host rho_GJ builder (Eq. 6 variants: Omega -> Omega - omega
+    on the cos term or on both, redshift alpha, f and H tables) against the
+    oracle's profile at every node."""
+    kw = workloads.gr_tube(B_G=1e12, P_s=0.3, Nz=2048, n_particles=10 ** 5)
+    nz, L = kw["Nz"], kw["L_over_R"]
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    z = np.arange(nz + 1) * (L / nz)
+    eta = 1.0 + z * cu["R_over_Rstar"]
+    f = 1.0 + 0.2 * (1.0 - 1.0 / eta) if tables else None
+    H = 1.0 - 0.1 * (1.0 - 1.0 / eta) if tables else None
+    rho = B.rho_gj_profile(B.default_params(**kw, gr_variant=variant, gr_alpha=alpha, gr_f=f, gr_H=H))
+    ref = orc.rho_gj_profile(orc.RHO_GR, z, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"],
+                             variant="both" if variant == B.SCLF_GR_BOTH else "cos", f=f, H=H,
+                             rg_over_Rstar=cu["rg_over_Rstar"] if alpha else None)
+    assert np.max(np.abs(rho - ref)) <= 1e-13 * np.max(np.abs(ref))
+    d = B.derive(B.default_params(**kw, gr_variant=variant, gr_alpha=alpha, gr_f=f, gr_H=H))
+    assert abs(d["rho0"] - ref[0]) <= 1e-13 * abs(ref[0])
+
+
+def test_eq6_parameters_are_validated():
+    import ctypes as C
+    lib = B.load()
+    kw = workloads.gr_tube(Nz=64, n_particles=1000)
+    d = B.TubeDerived()
+    for bad in (dict(gr_variant=2), dict(gr_alpha=3), dict(gr_f=np.zeros(65)),
+                dict(gr_H=np.full(65, np.nan))):
+        p = B.default_params(**kw, **bad)
+        assert lib.tube_derive(C.byref(p), C.byref(d)) == -1, bad

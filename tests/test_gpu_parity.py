@@ -464,3 +464,39 @@ def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
     batch2.close()
     for t in alone:
         t.close()
+
+
+@pytest.mark.parametrize("variant,alpha,tables", [(B.SCLF_GR_BOTH, 0, False),
+                                                  (B.SCLF_GR_COS, 1, True)])
+def test_eq6_variant_tube_matches_oracle(gpu_lib, variant, alpha, tables):
+    """A frame-dragging tube built with an Eq. 6 variant (Omega -> Omega - omega
+    on both terms; redshift alpha with f, H tables): initial fields, injection
+    counts and 50 FP64 steps with a prefilled beam against the oracle."""
+    kw = workloads.gr_tube(B_G=1e12, P_s=0.3, Nz=2048, n_particles=20000,
+                           precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FIXED64, track_ids=1)
+    nz, L = kw["Nz"], kw["L_over_R"]
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    z = np.arange(nz + 1) * (L / nz)
+    eta = 1.0 + z * cu["R_over_Rstar"]
+    f = 1.0 + 0.2 * (1.0 - 1.0 / eta) if tables else None
+    H = 1.0 - 0.1 * (1.0 - 1.0 / eta) if tables else None
+    t = B.Tube(B.default_params(**kw, gr_variant=variant, gr_alpha=alpha, gr_f=f, gr_H=H))
+    d = t.derived
+    rho = orc.rho_gj_profile(orc.RHO_GR, z, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"],
+                             variant="both" if variant == B.SCLF_GR_BOTH else "cos", f=f, H=H,
+                             rg_over_Rstar=cu["rg_over_Rstar"] if alpha else None)
+    o = orc.Tube(nz, L, d["dt"], rho, d["s"], precision="f64", accumulate="fixed")
+    fl = t.read_fields(rho=False)
+    assert rel(fl["ez"], o.ez) < 1e-11 and rel(fl["er"], o.er) < 1e-11
+    zp, up = synth.prefilled_beam(20000, L - L / nz, 1e3, seed=4)
+    t.add_particles(zp, up)
+    t.solve_fields()
+    o.add_particles(zp, up)
+    o.solve_fields()
+    for n in range(50):
+        t.step()
+        o.step()
+        compare(t, o, TOL[B.SCLF_FP64], "variant step %d" % n)
+    assert o.xi.size >= 19000
+    t.close()

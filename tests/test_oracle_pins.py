@@ -470,3 +470,60 @@ def test_fix32_tube_tracks_the_fp64_definition_and_brute_force():
     assert np.max(np.abs(a.cells() - c.cells())) < 1e-3
     assert np.max(np.abs(a.ez - c.ez)) < 1e-4 * np.max(np.abs(c.ez))
     assert np.max(np.abs(a.gauss_residual())) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Eq. 6 variants of the frame-dragging rho_GJ
+# ---------------------------------------------------------------------------
+
+def _gr_setup(incl=0.5, mass=1.4 * orc.M_SUN):
+    cu = orc.code_units(1e12, 0.3, 1e6, incl, mass)
+    z = np.linspace(0.0, 2.0 / cu["theta_p"], 65)
+    return cu, z
+
+
+def test_gr_profile_reduces_to_flat_without_mass():
+    """Eq. 6 reduces to the flat-space Eq. 5 when r_g = 0 (kappa = 0,
+    alpha = 1), in both variants, with f = H = 1."""
+    cu, z = _gr_setup(mass=0.0)
+    args = (z, cu["Lambda0"], 0.5, cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+    flat = orc.rho_gj_profile(orc.RHO_FLAT, *args)
+    for variant in ("cos", "both"):
+        gr = orc.rho_gj_profile(orc.RHO_GR, *args, variant=variant,
+                                rg_over_Rstar=cu["rg_over_Rstar"])
+        assert np.array_equal(gr, flat)
+
+
+def test_gr_both_terms_variant_scales_the_flat_profile():
+    """Omega -> Omega - omega on the prefactor of Eq. 5: rho = (1 - kappa/eta^3)
+    rho_flat at every height."""
+    cu, z = _gr_setup()
+    args = (z, cu["Lambda0"], 0.5, cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+    eta = 1.0 + z * cu["R_over_Rstar"]
+    both = orc.rho_gj_profile(orc.RHO_GR, *args, variant="both")
+    flat = orc.rho_gj_profile(orc.RHO_FLAT, *args)
+    assert np.allclose(both, (1.0 - cu["kappa"] / eta ** 3) * flat, rtol=1e-14, atol=0)
+    # the cos-term-only reading differs from it only through the sin i term
+    cos_only = orc.rho_gj_profile(orc.RHO_GR, *args)
+    lam = cu["Lambda0"] ** 2 / (4 * math.pi)
+    sin_term = 1.5 * np.sqrt(eta) * cu["theta_star"] * math.sin(0.5)
+    assert np.allclose(cos_only - both, -lam * sin_term * cu["kappa"] / eta ** 3,
+                       rtol=1e-12, atol=1e-12 * lam)
+
+
+def test_gr_redshift_and_curved_space_factors():
+    """alpha = (1 - r_g/r)^(1/2) divides the profile; f, H enter as f/f(1) and
+    H/f^(1/2), so f = c and H = c^(1/2) (any constant c) change nothing."""
+    cu, z = _gr_setup()
+    args = (z, cu["Lambda0"], 0.5, cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+    eta = 1.0 + z * cu["R_over_Rstar"]
+    base = orc.rho_gj_profile(orc.RHO_GR, *args)
+    red = orc.rho_gj_profile(orc.RHO_GR, *args, rg_over_Rstar=cu["rg_over_Rstar"])
+    assert np.allclose(red * np.sqrt(1.0 - cu["rg_over_Rstar"] / eta), base, rtol=1e-14, atol=0)
+    c = 2.7
+    same = orc.rho_gj_profile(orc.RHO_GR, *args, f=np.full(z.size, c), H=np.full(z.size, math.sqrt(c)))
+    assert np.allclose(same, base, rtol=1e-14, atol=0)
+    # f growing with height raises |rho| by f/f(1) (H = f^(1/2) keeps the bracket)
+    f = eta ** 2
+    grown = orc.rho_gj_profile(orc.RHO_GR, *args, f=f, H=np.sqrt(f))
+    assert np.allclose(grown, base * eta ** 2, rtol=1e-14, atol=0)
