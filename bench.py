@@ -304,6 +304,9 @@ def run_batch(args):
             t.solve_fields()
         if i == 1:
             states.append((z, u))
+    # the project's autotuner picks the particle kernel's shape on this batch
+    # (its tuning steps are ordinary steps of the run)
+    chosen, tune_ms = batch.autotune(5)
     batch.run(args.warmup)
     torch.cuda.synchronize()
     n0 = sum(t.status()["n_particles"] for t in batch.tubes)
@@ -374,6 +377,11 @@ def run_batch(args):
         "config": {"workload": "death_line_batch_256_tubes", "tubes": len(kws),
                    "particles_total": int(n1), "cells_total": int(sum(kw["Nz"] for kw in kws)),
                    "l2": "inputs larger than L2 (%.0f MB of particle state)" % (8e-6 * n1),
+                   "kernel_shape": {"chosen": {"particles_per_thread": B.Batch.VARIANTS[chosen][0],
+                                               "ctas_per_sm": B.Batch.VARIANTS[chosen][1],
+                                               "runs_per_thread": B.Batch.VARIANTS[chosen][2]},
+                                    "autotune_push_ms": {"%dx%dx%d" % v: float(m) for v, m in
+                                                         zip(B.Batch.VARIANTS, tune_ms)}},
                    "parallelism": "independent batch per GPU" if ws > 1 else "one batch"},
         "plain_form": {"value": plain_value, "unit": UNIT, "steps": k_plain,
                        "how": "the same 256 tubes, each stepped alone (tube_run, graphs)"},

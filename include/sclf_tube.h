@@ -318,6 +318,28 @@ int batch_set_timing(batch_t b, int enable);
 /* Accumulated timings; particle_slots sums over all tubes. Synchronises. */
 int batch_get_timing(batch_t b, tube_timing* out);
 
+/* Shapes of the batched particle kernel (index: particles per thread, CTAs
+ * per SM in its launch bounds, per-thread current runs): 0: 8, 4, 1 (the
+ * default); 1: 8, 3, 1; 2: 4, 4, 1; 3: 8, 4, 2; 4: 8, 3, 2; 5: 16, 2, 2.
+ * Tiles are 256 threads times the particles per thread; a second run sums
+ * the current of the particles sharing the cell of a thread's last particle
+ * without a branch (for tubes with few particles per cell). Every shape
+ * computes the same results bit for bit (the current and W_0 are exact
+ * integer sums in any order). */
+#define SCLF_BATCH_VARIANTS 6
+
+/* Use shape `variant` from the next step on (SCLF_EINVAL outside
+ * [0, SCLF_BATCH_VARIANTS)). */
+int batch_set_variant(batch_t b, int32_t variant);
+
+/* Autotuner: run 2 + steps ordinary steps of the batch with each shape,
+ * timing its particle kernel with CUDA events, and keep the fastest. ms
+ * (host, SCLF_BATCH_VARIANTS doubles, may be NULL) receives each shape's
+ * mean particle-kernel time per step, chosen (may be NULL) the shape kept.
+ * The batch advances by SCLF_BATCH_VARIANTS * (steps + 2) steps; timing is
+ * left off and its totals cleared. Synchronises. */
+int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen);
+
 /* ---- discrete adjoint of a run: gradients ------------------------------------
  * An adjoint driver owns one tube (SCLF_FP32 or SCLF_FP64 particles,
  * SCLF_ACC_FIXED64 current) and differentiates an N-step run of it (the

@@ -99,6 +99,8 @@ SIGNATURES = {
     "batch_run": (_i32, [_vp, _i64]),
     "batch_set_timing": (_i32, [_vp, _i32]),
     "batch_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "batch_set_variant": (_i32, [_vp, C.c_int32]),
+    "batch_autotune": (_i32, [_vp, C.c_int32, _pd, C.POINTER(C.c_int32)]),
     "adjoint_create": (_i32, [C.POINTER(TubeParams), _i64, C.c_int32, _vp, C.POINTER(_vp)]),
     "adjoint_destroy": (_i32, [_vp]),
     "adjoint_tube": (_i32, [_vp, C.POINTER(_vp)]),
@@ -387,6 +389,21 @@ class Batch:
         t = TubeTiming()
         _check(self.lib.batch_get_timing(self.h, C.byref(t)), "batch_get_timing")
         return {n: getattr(t, n) for n, _ in TubeTiming._fields_}
+
+    # (particles per thread, CTAs per SM, per-thread current runs)
+    VARIANTS = ((8, 4, 1), (8, 3, 1), (4, 4, 1), (8, 4, 2), (8, 3, 2), (16, 2, 2))
+
+    def set_variant(self, v):
+        _check(self.lib.batch_set_variant(self.h, int(v)), "batch_set_variant")
+
+    def autotune(self, steps):
+        """Time every particle-kernel shape for `steps` steps (the batch
+        advances) and keep the fastest; returns (chosen, ms per shape)."""
+        ms = np.empty(len(self.VARIANTS))
+        ch = C.c_int32()
+        _check(self.lib.batch_autotune(self.h, int(steps), _dptr(ms), C.byref(ch)),
+               "batch_autotune")
+        return ch.value, ms
 
     def close(self):
         if getattr(self, "h", None):

@@ -30,15 +30,17 @@ struct TileCtx {
     int nz;
 };
 
-// One tile of kThreads * kPPT slots: thread t owns slots [i0, i0 + kPPT).
+// One tile of kThreads * kPPT slots: thread t owns slots [i0, i0 + kPPT)
+// (kPPT defaults to the precision's layout; the batched kernel varies it).
 // Adds the tile's base weight, removals and non-finite flag to the caller's
 // counters.
-template <class Real, int kAcc>
+template <class Real, int kAcc, int kPPT = Layout<Real>::kPPT, bool kTwoRuns = false>
 __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<kAcc>::T>& c,
                                           long long tile, long long& w0_acc, long long& removed,
                                           bool& nonfinite) {
     using L = Layout<Real>;
-    constexpr int kPPT = L::kPPT, kVec = L::kVec, kTile = L::kTile;
+    constexpr int kVec = L::kVec, kTile = kThreads * kPPT;
+    static_assert(kPPT % kVec == 0, "whole vectors per thread");
     using AccT = typename AccType<kAcc>::T;
     using Pair = typename PairOf<Real>::T;
     const Real nzf = c.nzf, dt = c.dt, cfl = c.cfl;
@@ -72,9 +74,13 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
     // particle, away from the base cell and the top: its current
     // fraction joins a per-thread run without any branch. Everything
     // else (crossing a node, the base cell, leaving the tube, another
-    // cell, a non-finite result) takes the rare branch.
+    // cell, a non-finite result) takes the rare branch. With kTwoRuns the
+    // cell of the thread's last particle keeps a second run (sorted
+    // particles at ~100 per cell often put a thread's particles in two
+    // cells).
     const Real rkey = r_floor(xs[0]);
-    AccT ra = AccT(0);
+    const Real rkey2 = kTwoRuns ? r_floor(xs[kPPT - 1]) : rkey;
+    AccT ra = AccT(0), rb = AccT(0);
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
         const Real x = xs[k];
@@ -94,9 +100,12 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
         // (a4) charge-conserving deposit into cells floor(x) and floor(x1)
         const Real x0f = r_floor(xx);
         const Real x1f = r_floor(x1);
-        const bool common = lv & (x1f == x0f) & (x1 >= Real(1)) & (x1 < nzf) & (x0f == rkey);
+        const bool first = x0f == rkey;
+        const bool common = lv & (x1f == x0f) & (x1 >= Real(1)) & (x1 < nzf) &
+                            (first | (kTwoRuns & (x0f == rkey2)));
         const AccT q0 = frac_acc_in_cell<kAcc>(xx, x1, x0f);
-        ra += common ? q0 : AccT(0);
+        ra += (common & first) ? q0 : AccT(0);
+        if constexpr (kTwoRuns) rb += (common & !first) ? q0 : AccT(0);
         if (lv & !common) {
             if (!r_finite(x1)) {                 // a non-finite u1 makes x1 non-finite
                 nonfinite = true;
@@ -139,6 +148,8 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
         }
     }
     warp_flush<AccT>(rkey >= Real(0) ? static_cast<int>(rkey) : -1, ra, jacc);
+    if constexpr (kTwoRuns)
+        warp_flush<AccT>(rkey2 >= Real(0) && rkey2 != rkey ? static_cast<int>(rkey2) : -1, rb, jacc);
 }
 
 // Injection bookkeeping of a step: the requested count (the tube's own, or
@@ -242,21 +253,27 @@ __device__ __forceinline__ void flush_tube_counters(DevState* st, long long& w0,
     nf = false;
 }
 
-__global__ void __launch_bounds__(kThreads, 4)
+template <int kPPT, int kMinBlocks, bool kTwoRuns>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
                   long long n_tiles) {
-    constexpr int kTile = Layout<float>::kTile;
+    constexpr int kTile = kThreads * kPPT;
     long long w0 = 0, removed = 0;
     bool nonfinite = false;
+    // The tube of the next tile is loaded one tile ahead; the tube's step
+    // counters come with its descriptor (batch_refresh_kernel), so a tile's
+    // particle loads wait for one descriptor read only.
+    int ti = blockIdx.x < n_tiles ? tile_tube[blockIdx.x] : 0;
     for (long long g = blockIdx.x; g < n_tiles; g += gridDim.x) {
-        const BatchTube& d = tubes[tile_tube[g]];
-        DevState* st = d.st;
+        const BatchTube& d = tubes[ti];
+        const long long gn = g + gridDim.x;
+        ti = gn < n_tiles ? tile_tube[gn] : 0;
         const long long local = g - d.tile0;
-        const long long n_inj = clipped_injection(st, d.capacity, st->n_inj);
-        if (local == 0 && threadIdx.x == 0) record_injection(st, n_inj, st->n_inj, nullptr);
         TileCtx<float, long long> c;
-        c.n_slots = st->n_slots;
-        c.n_tot = c.n_slots + n_inj;
+        c.n_slots = d.n_slots;
+        c.n_tot = d.n_tot;
+        if (local == 0 && threadIdx.x == 0)
+            record_injection(d.st, c.n_tot - c.n_slots, d.n_req, nullptr);
         if (local * kTile >= c.n_tot) continue;          // the same for the whole CTA
         c.xi = d.xi;
         c.u = d.u;
@@ -265,14 +282,42 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         c.ids = d.ids;
         c.tab = reinterpret_cast<const float2*>(d.ez2);
         c.jacc = d.jacc;
-        c.id0 = st->total_injected;
+        c.id0 = d.id0;
         c.nzf = d.nzf;
         c.dt = d.dt;
         c.cfl = d.cfl;
         c.nz = d.nz;
-        push_tile<float, kAccFixed>(c, local, w0, removed, nonfinite);
-        flush_tube_counters(st, w0, removed, nonfinite);
+        // the next tile's descriptor line into L1 while this tile computes
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
+        push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
+        flush_tube_counters(d.st, w0, removed, nonfinite);
     }
+}
+
+__global__ void batch_refresh_kernel(BatchTube* tubes, int n_tubes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tubes) return;
+    BatchTube& d = tubes[i];
+    const DevState* st = d.st;
+    const long long n_slots = st->n_slots, n_req = st->n_inj, id0 = st->total_injected;
+    long long room = d.capacity - n_slots;
+    room = room > 0 ? room : 0;
+    d.n_slots = n_slots;
+    d.n_tot = n_slots + (n_req < room ? n_req : room);
+    d.id0 = id0;
+    d.n_req = n_req;
+}
+
+// The batched kernel's shapes, (particles per thread, CTAs per SM in the
+// launch bounds, runs per thread); batch_autotune picks one per batch by
+// timing.
+template <int kPPT, int kMinBlocks, bool kTwoRuns>
+int batch_grid_of(int sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_push_kernel<kPPT, kMinBlocks, kTwoRuns>, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * sms;
 }
 
 }  // namespace
@@ -295,16 +340,35 @@ cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid, cudaS
     return cudaGetLastError();
 }
 
-int batch_push_grid_size(int device_sms) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_push_kernel, kThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    return per_sm * device_sms;
+cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s) {
+    batch_refresh_kernel<<<(n_tubes + 127) / 128, 128, 0, s>>>(tubes, n_tubes);
+    return cudaGetLastError();
+}
+
+int batch_push_grid_size(int variant, int device_sms) {
+    switch (variant) {
+        case 1: return batch_grid_of<8, 3, false>(device_sms);
+        case 2: return batch_grid_of<4, 4, false>(device_sms);
+        case 3: return batch_grid_of<8, 4, true>(device_sms);
+        case 4: return batch_grid_of<8, 3, true>(device_sms);
+        case 5: return batch_grid_of<16, 2, true>(device_sms);
+        default: return batch_grid_of<8, 4, false>(device_sms);
+    }
 }
 
 cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
-                              int grid, cudaStream_t s) {
-    batch_push_kernel<<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles);
+                              int grid, int variant, cudaStream_t s) {
+#define SCLF_BATCH_LAUNCH(P, M, T) \
+    batch_push_kernel<P, M, T><<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles)
+    switch (variant) {
+        case 1: SCLF_BATCH_LAUNCH(8, 3, false); break;
+        case 2: SCLF_BATCH_LAUNCH(4, 4, false); break;
+        case 3: SCLF_BATCH_LAUNCH(8, 4, true); break;
+        case 4: SCLF_BATCH_LAUNCH(8, 3, true); break;
+        case 5: SCLF_BATCH_LAUNCH(16, 2, true); break;
+        default: SCLF_BATCH_LAUNCH(8, 4, false); break;
+    }
+#undef SCLF_BATCH_LAUNCH
     return cudaGetLastError();
 }
 

@@ -149,18 +149,24 @@ struct CompactArgs {
 
 // One tube of a batch, as the batched kernels see it (FP32 particles,
 // fixed-point current).
-struct BatchTube {
+struct alignas(128) BatchTube {
+    // what the particle kernel reads, within one 128-byte line
     DevState* st;
     float* xi;
     float* u;
     long long* ids;
     float* ez2;                // gather table (read by the particle kernel, written by the field kernel)
     long long* jacc;
-    long long capacity;
     long long tile0;           // first tile of this tube in the batch's tile space
+    long long n_slots;         // this step: slots before the injection,
+    long long n_tot;           //   slots after it (injection clipped to the capacity),
+    long long id0;             //   first ID handed out,
+    long long n_req;           //   injection requested (refreshed before each particle launch)
     int nz;
-    int cell0;                 // first cell of this tube in the batch's cell space
     float nzf, dt, cfl;
+    // the rest
+    long long capacity;
+    int cell0;                 // first cell of this tube in the batch's cell space
     double* ez;
     double* er[2];
     double* b[2];
@@ -210,9 +216,19 @@ template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
                          cudaStream_t s);
 cudaError_t launch_push_fix32(const PushFixArgs& a, int grid, cudaStream_t s);
+// Shapes of the batched particle kernel: particles per thread (the tile is
+// kThreads times that), CTAs per SM in its launch bounds and per-thread
+// current runs (1: the first particle's cell; 2: also the last one's).
+constexpr int kBatchVariants = 6;
+constexpr int kBatchPPT[kBatchVariants] = {8, 8, 4, 8, 8, 16};
+constexpr int kBatchMinBlocks[kBatchVariants] = {4, 3, 4, 4, 3, 2};
+constexpr int kBatchRuns[kBatchVariants] = {1, 1, 1, 2, 2, 2};
 cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
-                              int grid, cudaStream_t s);
-int batch_push_grid_size(int device_sms);
+                              int grid, int variant, cudaStream_t s);
+// Copies each tube's step counters (slots, clipped injection, first ID) into
+// its descriptor before the particle launch.
+cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s);
+int batch_push_grid_size(int variant, int device_sms);
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
                                int parity, cudaStream_t s);
 int push_fix32_grid_size(int device_sms);

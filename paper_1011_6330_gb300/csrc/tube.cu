@@ -829,12 +829,15 @@ struct sclf_batch {
     cudaStream_t gstream = nullptr;
     bool own_gstream = false;
     cudaEvent_t fork = nullptr, join = nullptr;
-    BatchTube* d_desc = nullptr;
-    int* d_tile_tube = nullptr;
+    // one descriptor array and tile-to-tube table per tile size of the
+    // particle kernel's shapes (tile0 differs between them)
+    BatchTube* d_desc[3] = {nullptr, nullptr, nullptr};
+    int* d_tile_tube[3] = {nullptr, nullptr, nullptr};
     int* d_cell_tube = nullptr;
-    long long n_tiles = 0;
+    long long n_tiles[3] = {0, 0, 0};
     int n_cells = 0;
-    int push_grid = 0;
+    int push_grid[kBatchVariants] = {};
+    int variant = 0;                   // particle kernel shape (batch_autotune)
     int64_t host_step = 0;
     int steps_since_compact = 0;
     int compact_every = 64;
@@ -850,9 +853,26 @@ struct sclf_batch {
 
 namespace {
 
+// Tile-size class of a particle-kernel shape: 0 for kThreads * 8 slots, 1
+// for kThreads * 4, 2 for kThreads * 16.
+constexpr int kTileClasses = 3;
+constexpr int kClassPPT[kTileClasses] = {8, 4, 16};
+int tile_class(int variant) {
+    const int ppt = kBatchPPT[variant];
+    return ppt == 8 ? 0 : (ppt == 4 ? 1 : 2);
+}
+
+cudaError_t batch_launch_push(sclf_batch* b, cudaStream_t s) {
+    const int c = tile_class(b->variant);
+    const cudaError_t e = launch_batch_refresh(b->d_desc[c], static_cast<int>(b->tubes.size()), s);
+    if (e != cudaSuccess) return e;
+    return launch_batch_push(b->d_desc[c], b->d_tile_tube[c], b->n_tiles[c],
+                             b->push_grid[b->variant], b->variant, s);
+}
+
 int batch_enqueue_step(sclf_batch* b, cudaStream_t s, int parity) {
-    CK(launch_batch_push(b->d_desc, b->d_tile_tube, b->n_tiles, b->push_grid, s));
-    CK(launch_batch_field(b->d_desc, b->d_cell_tube, b->n_cells, parity, s));
+    CK(batch_launch_push(b, s));
+    CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, s));
     return SCLF_OK;
 }
 
@@ -902,9 +922,9 @@ int batch_one_step(sclf_batch* b) {
         const int e0 = batch_reserve(b, 3);
         if (e0 < 0) return SCLF_ECUDA;
         CK(cudaEventRecord(b->ev[e0], b->stream));
-        CK(launch_batch_push(b->d_desc, b->d_tile_tube, b->n_tiles, b->push_grid, b->stream));
+        CK(batch_launch_push(b, b->stream));
         CK(cudaEventRecord(b->ev[e0 + 1], b->stream));
-        CK(launch_batch_field(b->d_desc, b->d_cell_tube, b->n_cells, parity, b->stream));
+        CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, b->stream));
         CK(cudaEventRecord(b->ev[e0 + 2], b->stream));
         b->recs.push_back({0, e0});
     } else {
@@ -961,11 +981,12 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
     b->stream = static_cast<cudaStream_t>(stream);
     auto fail = [&](int code) { batch_destroy(b); return code; };
     std::vector<BatchTube> desc(n);
-    std::vector<int> tile_tube, cell_tube;
-    long long tiles = 0;
+    std::vector<int> tile_tube[kTileClasses], cell_tube;
+    long long tiles[kTileClasses] = {0, 0, 0};
     long long cells = 0;
     b->compact_every = params[0].compact_interval > 0 ? params[0].compact_interval : 64;
     b->chunk_steps = b->compact_every + (b->compact_every & 1);
+    std::vector<long long> tile0[kTileClasses];
     for (int32_t i = 0; i < n; ++i) {
         tube_t t = nullptr;
         const int rc = tube_create(&params[i], nullptr, 0, stream, &t);
@@ -980,7 +1001,8 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         d.ez2 = static_cast<float*>(t->ez2);
         d.jacc = static_cast<long long*>(t->jacc);
         d.capacity = t->p.capacity;
-        d.tile0 = tiles;
+        d.tile0 = 0;
+        d.n_slots = d.n_tot = d.id0 = d.n_req = 0;
         d.nz = static_cast<int>(t->p.Nz);
         d.cell0 = static_cast<int>(cells);
         d.nzf = static_cast<float>(t->p.Nz);
@@ -993,27 +1015,41 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         d.b[1] = t->b[1];
         d.jlast = t->jlast;
         d.fc = t->fc;
-        const long long nt = t->lay.cap_pad / Layout<float>::kTile;
-        tile_tube.insert(tile_tube.end(), static_cast<size_t>(nt), i);
+        for (int c = 0; c < kTileClasses; ++c) {   // cap_pad is a multiple of every tile size
+            const long long nt = t->lay.cap_pad / (kThreads * static_cast<long long>(kClassPPT[c]));
+            tile0[c].push_back(tiles[c]);
+            tile_tube[c].insert(tile_tube[c].end(), static_cast<size_t>(nt), i);
+            tiles[c] += nt;
+        }
         cell_tube.insert(cell_tube.end(), static_cast<size_t>(t->p.Nz), i);
-        tiles += nt;
         cells += t->p.Nz;
         if (cells >= (1LL << 31)) return fail(SCLF_EINVAL);
     }
-    b->n_tiles = tiles;
     b->n_cells = static_cast<int>(cells);
-    if (cudaMalloc(&b->d_desc, sizeof(BatchTube) * n) != cudaSuccess ||
-        cudaMalloc(&b->d_tile_tube, sizeof(int) * tiles) != cudaSuccess ||
-        cudaMalloc(&b->d_cell_tube, sizeof(int) * cells) != cudaSuccess)
-        return fail(SCLF_ENOMEM);
-    if (cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(BatchTube) * n, cudaMemcpyHostToDevice, b->stream) ||
-        cudaMemcpyAsync(b->d_tile_tube, tile_tube.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, b->stream) ||
-        cudaMemcpyAsync(b->d_cell_tube, cell_tube.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, b->stream) ||
+    for (int c = 0; c < kTileClasses; ++c) {
+        std::vector<BatchTube> dc(desc);
+        for (int32_t i = 0; i < n; ++i) dc[i].tile0 = tile0[c][i];
+        b->n_tiles[c] = tiles[c];
+        if (cudaMalloc(&b->d_desc[c], sizeof(BatchTube) * n) != cudaSuccess ||
+            cudaMalloc(&b->d_tile_tube[c], sizeof(int) * tiles[c]) != cudaSuccess)
+            return fail(SCLF_ENOMEM);
+        if (cudaMemcpyAsync(b->d_desc[c], dc.data(), sizeof(BatchTube) * n, cudaMemcpyHostToDevice,
+                            b->stream) ||
+            cudaMemcpyAsync(b->d_tile_tube[c], tile_tube[c].data(), sizeof(int) * tiles[c],
+                            cudaMemcpyHostToDevice, b->stream) ||
+            cudaStreamSynchronize(b->stream))
+            return fail(SCLF_ECUDA);
+    }
+    if (cudaMalloc(&b->d_cell_tube, sizeof(int) * cells) != cudaSuccess) return fail(SCLF_ENOMEM);
+    if (cudaMemcpyAsync(b->d_cell_tube, cell_tube.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, b->stream) ||
         cudaStreamSynchronize(b->stream))
         return fail(SCLF_ECUDA);
     const int sms = b->tubes[0]->sms;
-    b->push_grid = batch_push_grid_size(sms);
-    if (b->push_grid > tiles) b->push_grid = static_cast<int>(tiles);
+    for (int v = 0; v < kBatchVariants; ++v) {
+        b->push_grid[v] = batch_push_grid_size(v, sms);
+        const long long nt = b->n_tiles[tile_class(v)];
+        if (b->push_grid[v] > nt) b->push_grid[v] = static_cast<int>(nt);
+    }
     if (b->stream) {
         b->gstream = b->stream;
     } else {
@@ -1040,8 +1076,10 @@ int batch_destroy(batch_t b) {
         cudaStreamDestroy(b->gstream);
     }
     for (sclf_tube* t : b->tubes) tube_destroy(t);
-    if (b->d_desc) cudaFree(b->d_desc);
-    if (b->d_tile_tube) cudaFree(b->d_tile_tube);
+    for (int c = 0; c < kTileClasses; ++c) {
+        if (b->d_desc[c]) cudaFree(b->d_desc[c]);
+        if (b->d_tile_tube[c]) cudaFree(b->d_tile_tube[c]);
+    }
     if (b->d_cell_tube) cudaFree(b->d_cell_tube);
     delete b;
     return SCLF_OK;
@@ -1116,6 +1154,40 @@ int batch_set_timing(batch_t b, int enable) {
     const int rc = batch_drain(b);
     b->timing = false;
     return rc;
+}
+
+int batch_set_variant(batch_t b, int32_t variant) {
+    if (!b || variant < 0 || variant >= kBatchVariants) return SCLF_EINVAL;
+    if (variant != b->variant && b->chunk) {
+        CK(cudaStreamSynchronize(b->stream));
+        cudaGraphExecDestroy(b->chunk);          // captured with the previous shape
+        b->chunk = nullptr;
+    }
+    b->variant = variant;
+    return SCLF_OK;
+}
+
+int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen) {
+    if (!b || steps <= 0) return SCLF_EINVAL;
+    double best = 0.0;
+    int best_v = -1;
+    for (int v = 0; v < kBatchVariants; ++v) {
+        int rc = batch_set_variant(b, v);
+        if (rc) return rc;
+        for (int k = 0; k < 2; ++k)              // first launches of this kernel
+            if ((rc = batch_one_step(b))) return rc;
+        if ((rc = batch_set_timing(b, 1))) return rc;
+        for (int k = 0; k < steps; ++k)
+            if ((rc = batch_one_step(b))) return rc;
+        tube_timing tm;
+        if ((rc = batch_get_timing(b, &tm))) return rc;
+        if ((rc = batch_set_timing(b, 0))) return rc;
+        const double per = tm.push_ms / double(tm.n_steps > 0 ? tm.n_steps : 1);
+        if (ms) ms[v] = per;
+        if (best_v < 0 || per < best) { best = per; best_v = v; }
+    }
+    if (chosen) *chosen = best_v;
+    return batch_set_variant(b, best_v);
 }
 
 int batch_get_timing(batch_t b, tube_timing* out) {

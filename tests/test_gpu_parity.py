@@ -500,3 +500,49 @@ def test_eq6_variant_tube_matches_oracle(gpu_lib, variant, alpha, tables):
         compare(t, o, TOL[B.SCLF_FP64], "variant step %d" % n)
     assert o.xi.size >= 19000
     t.close()
+
+
+def _batch_state(batch):
+    out = []
+    for t in batch.tubes:
+        st = t.status()
+        out.append((st["step"], st["n_particles"], st["total_injected"], st["pending_injection"],
+                    t.read_particles(), t.read_fields(rho=False)))
+    return out
+
+
+def _same_state(sa, sb):
+    for a, b in zip(sa, sb):
+        assert a[:4] == b[:4]
+        for x, y in zip(a[4], b[4]):
+            assert np.array_equal(x, y)
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(a[5][k], b[5][k]), k
+
+
+def test_batch_kernel_shapes_agree_bit_for_bit_and_autotune_keeps_one(gpu_lib):
+    """Every shape of the batched particle kernel (particles per thread, CTAs
+    per SM) advances a batch to the same state bit for bit; the autotuner
+    keeps one of them and the tuned batch equals an untuned one stepped as
+    many times."""
+    kws = _small_batch_params()
+    batches = []
+    for v in range(len(B.Batch.VARIANTS)):
+        b = B.Batch([B.default_params(**kw) for kw in kws])
+        for i, kw in enumerate(kws):
+            _fill(b.tubes[i], kw, seed=i)
+        b.set_variant(v)
+        b.run(70)                      # one 64-step graph (with a compaction check) and single steps
+        batches.append(b)
+    ref = _batch_state(batches[0])
+    for b in batches[1:]:
+        _same_state(_batch_state(b), ref)
+    tuned, plain = batches[0], batches[1]
+    chosen, ms = tuned.autotune(3)
+    assert 0 <= chosen < len(B.Batch.VARIANTS) and np.all(ms > 0) and ms[chosen] == ms.min()
+    plain.run(len(B.Batch.VARIANTS) * 5)
+    tuned.run(10)
+    plain.run(10)
+    _same_state(_batch_state(tuned), _batch_state(plain))
+    for b in batches:
+        b.close()
