@@ -527,6 +527,25 @@ def run_adjoint(args):
     err32 = {name: [float(abs(x - y) / abs(y)) for x, y in zip(g32, gg)]
              for name, g32, gg in (("gamma", grad_gamma, g64[0]), ("ez", grad_ez, g64[1]))}
     val_err32 = [float(abs(x - y) / abs(y)) for x, y in zip(vals, v64)]
+    # the same run with 32-bit fixed-point positions (SCLF_FIX32): its speed
+    # (one untimed-graph evaluation after one warm-up) and its error against FP64
+    ax = B.Adjoint(B.default_params(**dict(kw, precision=B.SCLF_FIX32)), ADJ_STEPS, ADJ_EVERY)
+    ax.tube.add_particles(z, u)
+    ax.forward()
+    ax.backward(B.SCLF_OBJ_GAMMA)
+    vx = ax.forward()
+    fx_ms = ax.timing()["forward_ms"]
+    gx = [ax.param_gradient(*ax.backward(B.SCLF_OBJ_GAMMA))]
+    bx_ms = ax.timing()["backward_ms"]
+    gx.append(ax.param_gradient(*ax.backward(B.SCLF_OBJ_EZ)))
+    px = ax.timing()["particle_steps"]
+    ax.close()
+    fix32 = {"value": px / (1e-3 * (fx_ms + bx_ms)), "unit": UNIT, "forward_ms": fx_ms,
+             "backward_ms": bx_ms, "values": list(vx),
+             "vs_fp64_values_rel_err": [float(abs(x - y) / abs(y)) for x, y in zip(vx, v64)],
+             "vs_fp64_grad_rel_err": {name: [float(abs(x - y) / abs(y)) for x, y in zip(g, gg)]
+                                      for name, g, gg in (("gamma", gx[0], g64[0]),
+                                                          ("ez", gx[1], g64[1]))}}
     # per kernel: the forward and recompute passes launch the same two kernels
     # algorithmic bytes per launch: particles 16 B (x, u in and out) forward,
     # 24 B (x, u in; lambda_x, lambda_u in and out) in reverse; grid kernels
@@ -606,7 +625,7 @@ def run_adjoint(args):
                     "grad_gamma_BPRw": [float(x) for x in grad_gamma],
                     "grad_ez_BPRw": [float(x) for x in grad_ez],
                     "fp64_values": list(v64), "fp32_vs_fp64_values_rel_err": val_err32,
-                    "fp32_vs_fp64_grad_rel_err": err32,
+                    "fp32_vs_fp64_grad_rel_err": err32, "fix32": fix32,
                     "kernels_ms_per_launch": per_launch,
                     "kernels_share_per_evaluation": ({k: v / sum(share.values())
                                                       for k, v in share.items()}

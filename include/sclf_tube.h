@@ -341,8 +341,8 @@ int batch_set_variant(batch_t b, int32_t variant);
 int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen);
 
 /* ---- discrete adjoint of a run: gradients ------------------------------------
- * An adjoint driver owns one tube (SCLF_FP32 or SCLF_FP64 particles,
- * SCLF_ACC_FIXED64 current) and differentiates an N-step run of it (the
+ * An adjoint driver owns one tube (SCLF_FP32, SCLF_FP64 or SCLF_FIX32
+ * particles, SCLF_ACC_FIXED64 current) and differentiates an N-step run of it (the
  * Sec. 2 step of Figure A) that starts from the particles the tube holds at
  * the first adjoint_forward, with fields solving Eq. 4 for their charge
  * (as tube_solve_fields). The inputs it differentiates are rho_GJ at the
@@ -351,8 +351,10 @@ int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen);
  * the charge of the particles at t = 0). Held fixed: the number of
  * electrons injected at each step (recorded by the forward pass, or given by
  * adjoint_set_injections), the grid (L, Nz, dt in code units) and the
- * rounding of the particle precision. The piecewise-linear gather and
- * deposit are differentiated inside their pieces (dF_j/dx = 1 on cell j).
+ * rounding of the particle precision (including SCLF_FIX32's rounding of
+ * the displacement to its position grid). The piecewise-linear gather and
+ * deposit are differentiated inside their pieces (dF_j/dx = 1 on cell j);
+ * adjoints of positions are in cell units.
  * Particles keep their slots for the whole run (no compaction).
  *
  * The forward pass stores the state at every checkpoint_every-th step; the
@@ -373,7 +375,8 @@ typedef struct sclf_adjoint* adjoint_t;   /* opaque, library-owned */
  * (track_ids is ignored). Device memory: about checkpoint_every +
  * nsteps / checkpoint_every + 5 copies of the particle arrays
  * (2 * capacity * 4 or 8 bytes each) and checkpoint_every grid copies.
- * SCLF_EINVAL for another precision or accumulation, SCLF_ENOMEM when it
+ * SCLF_EINVAL for SCLF_ACC_FP64 (a recompute must reproduce the run bit for
+ * bit, which FP64 atomics do not promise), SCLF_ENOMEM when it
  * does not fit. Work goes to the tube's stream (stream, or a stream of its
  * own when NULL). Synchronises. */
 int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_every,

@@ -127,8 +127,10 @@ class AdjointRun:
 
     def __init__(self, nz, L, dt, rho_gj, s, z0=None, u0=None, precision="f64",
                  accumulate="fixed"):
-        if precision not in ("f64", "f32"):
-            raise ValueError("the adjoint covers the floating-point particle modes")
+        if precision not in ("f64", "f32", "fix32"):
+            raise ValueError(precision)
+        if precision == "fix32" and accumulate != "fixed":
+            raise ValueError("'fix32' positions deposit exact fixed-point fractions")
         self.nz, self.L, self.dt = int(nz), float(L), float(dt)
         self.dz = self.L / self.nz
         self.rho_gj = np.asarray(rho_gj, np.float64).copy()
@@ -197,15 +199,31 @@ class AdjointRun:
             lez = t.ez * dz / value if value > 0.0 else np.zeros(nz)
         sum_lj_j = 0.0
 
+        fix = self.precision == "fix32"
+        fb = t.fb
+        scale = 2.0 ** -fb if fix else 1.0           # cells per stored position unit
         for n in reversed(range(int(nsteps))):
             xi_pre, u_pre, ez, jn, ninj = states[n]
             x0r = np.concatenate([xi_pre, np.zeros(ninj, xi_pre.dtype)])
             u0r = np.concatenate([u_pre, np.zeros(ninj, u_pre.dtype)])
-            # the step's forward values, recomputed in the particle precision
-            ep = so.gather(ez, x0r, rt)
-            x1r, u1r = so.push(x0r, u0r, ep, dt, dz, rt)
-            finite = np.isfinite(x1r) & np.isfinite(u1r)
-            alive = finite & (x1r >= 0) & (x1r < nz)
+            # the step's forward values, recomputed as the tube computed them
+            if fix:
+                ep = so.gather_fix32(ez, x0r, fb)
+                x1r, u1r, finite = so.push_fix32(x0r, u0r, ep, dt, dz, fb)
+                alive = finite & (x1r >= 0) & (x1r < (nz << fb))
+                h = x0r + (1 << (fb - 1))
+                m = h >> fb
+                f = ((h & ((1 << fb) - 1)).astype(np.float32)
+                     * np.float32(2.0 ** -fb)).astype(np.float64)
+            else:
+                ep = so.gather(ez, x0r, rt)
+                x1r, u1r = so.push(x0r, u0r, ep, dt, dz, rt)
+                finite = np.isfinite(x1r) & np.isfinite(u1r)
+                alive = finite & (x1r >= 0) & (x1r < nz)
+                hh = x0r + rt(0.5)
+                mf = np.floor(hh)
+                f = (hh - mf).astype(np.float64)
+                m = mf.astype(np.int64)
             lx1 = np.zeros(x0r.size)
             lu1 = np.zeros(x0r.size)
             lx1[alive] = lx
@@ -214,23 +232,20 @@ class AdjointRun:
             lez, ler, lb, lj = field_update_adjoint(lez, ler, lb, dt, dz)
             sum_lj_j += float(np.dot(lj, jn))
             lS = (s / dt) * lj                       # adjoint of the fraction sums
-            # (a4) deposit: J_j = (s/dt) sum_p [F_j(x1) - F_j(x0)]
-            x0 = x0r.astype(np.float64)
-            x1 = np.where(alive, x1r, 0).astype(np.float64)
+            # (a4) deposit: J_j = (s/dt) sum_p [F_j(x1) - F_j(x0)], positions in cells
+            x0 = x0r.astype(np.float64) * scale
+            x1 = np.where(alive, x1r, 0).astype(np.float64) * scale
             c0 = np.floor(x0).astype(np.int64)
             c1 = np.floor(x1).astype(np.int64)
             lx1 = lx1 + np.where(alive, lS[np.clip(c1, 0, nz - 1)], 0.0)
             lx0 = np.where(finite, lx1 - lS[np.clip(c0, 0, nz - 1)], 0.0)
-            # (a3) Eq. 1: u1 = u0 - E_p dt, x1 = x0 + (u1 / gamma1) dt/dz
+            # (a3) Eq. 1: u1 = u0 - E_p dt, x1 = x0 + (u1 / gamma1) dt/dz (the
+            # rounding of the displacement to the position grid as the identity)
             u1 = np.where(finite, u1r, 0).astype(np.float64)
             g1 = np.sqrt(1.0 + u1 * u1)
             lu0 = np.where(finite, lu1 + lx1 * cfl_r / g1 ** 3, 0.0)
             lep = -dt_r * lu0
             # (a2) gather: E_p = (1 - f) E_{m-1/2} + f E_{m+1/2}, f = x + 1/2 - m
-            h = x0r + rt(0.5)
-            mf = np.floor(h)
-            f = (h - mf).astype(np.float64)
-            m = mf.astype(np.int64)
             ia = np.clip(m - 1, 0, nz - 1)
             ib = np.clip(m, 0, nz - 1)
             e = np.asarray(ez, np.float64).astype(rt).astype(np.float64)
@@ -243,7 +258,8 @@ class AdjointRun:
 
         # t = 0: fields from Eq. 4 with source rho_GJ - rho_particles(s)
         d_rho = initial_fields_adjoint(lez, ler, dz)
-        cells0 = np.asarray(states[0][0], np.float64) if nsteps else self.z0 / dz
+        cells0 = (np.asarray(states[0][0], np.float64) * scale if nsteps
+                  else t.cells())
         rho_p = so.rho_nodes(cells0, s, dz, nz)
         d_s = sum_lj_j / s - float(np.dot(d_rho, rho_p)) / s
         return value, d_rho, d_s, inj_log, rem_log

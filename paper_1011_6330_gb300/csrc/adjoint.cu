@@ -157,6 +157,102 @@ __global__ void __launch_bounds__(kThreads) adj_push_kernel(const AdjPushArgs<Re
         adj_push_tile<Real>(a, tile, n_slots, n_tot);
 }
 
+// The same for SCLF_FIX32 positions: the forward step is recomputed exactly
+// (displacement d rounded half-even to the 2^-fb grid), the rounding is
+// differentiated as the identity, adjoints are in cell units.
+__device__ __forceinline__ void adj_push_fix32_tile(const AdjPushFixArgs& a, long long tile,
+                                                    long long n_slots, long long n_tot) {
+    constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
+    const int nz = a.nz, fb = a.fb;
+    const long long top = static_cast<long long>(nz) << fb;
+    const unsigned half = 1u << (fb - 1), mask = (1u << fb) - 1u;
+    const float dt = a.dt, cfl = a.cfl, scale = a.scale, two_fb = a.two_fb;
+    const float2* __restrict__ tab = reinterpret_cast<const float2*>(a.ez2);
+    const float* __restrict__ ls = a.ls_tab;
+
+    const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
+    int xs[kPPT];
+    float us[kPPT], lxs[kPPT], lus[kPPT];
+#pragma unroll
+    for (int v = 0; v < kPPT; v += kVec) {
+        vload(a.X + i0 + v, xs + v);
+        vload(a.u + i0 + v, us + v);
+        vload(a.lx + i0 + v, lxs + v);
+        vload(a.lu + i0 + v, lus + v);
+    }
+    const long long r_slots = n_slots - i0, r_tot = n_tot - i0;
+    const int k_real = r_slots <= 0 ? 0 : (r_slots >= kPPT ? kPPT : int(r_slots));
+    const int k_tot = r_tot <= 0 ? 0 : (r_tot >= kPPT ? kPPT : int(r_tot));
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+        if (k >= k_real && k < k_tot) {
+            xs[k] = 0;
+            us[k] = 0.0f;
+        }
+    }
+    const unsigned rkey = (k_tot > 0 && xs[0] >= 0)
+                              ? (static_cast<unsigned>(xs[0]) + half) >> fb : 0xffffffffu;
+    float ra = 0.0f, rb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+        const bool lv = (k < k_tot) & (xs[k] >= 0);
+        const unsigned U = lv ? static_cast<unsigned>(xs[k]) : 0u;
+        const unsigned h = U + half;
+        const unsigned m = h >> fb;
+        const float f = __uint2float_rn(h & mask) * scale;
+        const float2 e = tab[m];
+        const float ep = (1.0f - f) * e.x + f * e.y;
+        const float u1 = us[k] - ep * dt;
+        const float g = __fsqrt_rn(1.0f + u1 * u1);
+        const float d = __fdiv_rn(u1, g) * cfl;
+        const bool fin = lv & isfinite(d);
+        const int inc = fin ? __float2int_rn(d * two_fb) : 0;
+        const long long X1 = static_cast<long long>(U) + inc;
+        const bool stay = fin & (X1 >= 0) & (X1 < top);
+        const int c1 = stay ? static_cast<int>(X1 >> fb) : 0;
+        const int c0 = static_cast<int>(U >> fb);
+        const float lx1 = stay ? lxs[k] + ls[c1] : 0.0f;
+        const float lu1 = stay ? lus[k] : 0.0f;
+        float lx0 = fin ? lx1 - ls[c0] : 0.0f;
+        const float ig = __fdiv_rn(1.0f, g);
+        const float lu0 = fin ? lu1 + lx1 * cfl * (ig * ig * ig) : 0.0f;
+        const float lep = -dt * lu0;
+        lx0 += lep * (e.y - e.x);
+        const float wa = (1.0f - f) * lep, wb = f * lep;
+        const bool common = lv & (m == rkey) & (m >= 1u) & (m <= static_cast<unsigned>(nz - 1));
+        ra += common ? wa : 0.0f;
+        rb += common ? wb : 0.0f;
+        if (lv & !common & (lep != 0.0f)) {
+            const int ia = m < 1u ? 0 : static_cast<int>(m) - 1;
+            const int ib = m > static_cast<unsigned>(nz - 1) ? nz - 1 : static_cast<int>(m);
+            atomicAdd(a.lez + ia, static_cast<double>(wa));
+            atomicAdd(a.lez + ib, static_cast<double>(wb));
+        }
+        lxs[k] = lx0;
+        lus[k] = lu0;
+    }
+#pragma unroll
+    for (int v = 0; v < kPPT; v += kVec) {
+        if (i0 + v < n_tot) {
+            vstore(a.lx + i0 + v, lxs + v);
+            vstore(a.lu + i0 + v, lus + v);
+        }
+    }
+    const int kb = (rkey != 0xffffffffu && rkey >= 1u && rkey <= static_cast<unsigned>(nz - 1))
+                       ? static_cast<int>(rkey) : -1;
+    warp_flush<double>(kb >= 0 ? kb - 1 : -1, static_cast<double>(ra), a.lez);
+    warp_flush<double>(kb, static_cast<double>(rb), a.lez);
+}
+
+__global__ void __launch_bounds__(kThreads) adj_push_fix32_kernel(const AdjPushFixArgs a) {
+    constexpr int kTile = Layout<int>::kTile;
+    const long long n_slots = a.log[kLogSlots];
+    const long long n_tot = n_slots + a.log[kLogInjected];
+    const long long ntiles = (n_tot + kTile - 1) / kTile;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        adj_push_fix32_tile(a, tile, n_slots, n_tot);
+}
+
 // ---------------------------------------------------------------------------
 // Objectives and seeds
 // ---------------------------------------------------------------------------
@@ -174,8 +270,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // Per block: sum of gamma over the live slots and of E_z^2 over the cells
 // (fixed grid-stride assignment, so the result does not depend on timing).
-template <class Real>
-__global__ void __launch_bounds__(256) objective_partials(const Real* xi, const Real* u,
+template <class Pos, class Mom>
+__global__ void __launch_bounds__(256) objective_partials(const Pos* xi, const Mom* u,
                                                           const DevState* st, const double* ez,
                                                           int nz, double* part) {
     __shared__ double sh[8];
@@ -184,7 +280,7 @@ __global__ void __launch_bounds__(256) objective_partials(const Real* xi, const 
     double sg = 0.0, se = 0.0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += stride) {
-        if (xi[i] >= Real(0)) {
+        if (xi[i] >= Pos(0)) {
             const double v = static_cast<double>(u[i]);
             sg += sqrt(1.0 + v * v);
         }
@@ -213,18 +309,18 @@ __global__ void objective_finish(const double* part, int nblocks, const DevState
     out[1] = sqrt(se * dz);
 }
 
-template <class Real>
-__global__ void seed_gamma_kernel(const Real* xi, const Real* u, const DevState* st, Real* lx,
-                                  Real* lu) {
+template <class Pos, class Mom>
+__global__ void seed_gamma_kernel(const Pos* xi, const Mom* u, const DevState* st, Mom* lx,
+                                  Mom* lu) {
     const long long n = st->n_slots;
     const long long live = st->n_live;
     const double inv = live > 0 ? 1.0 / static_cast<double>(live) : 0.0;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const bool live_slot = xi[i] >= Real(0);
+        const bool live_slot = xi[i] >= Pos(0);
         const double v = static_cast<double>(u[i]);
-        lx[i] = Real(0);
-        lu[i] = live_slot ? static_cast<Real>(v / sqrt(1.0 + v * v) * inv) : Real(0);
+        lx[i] = Mom(0);
+        lu[i] = live_slot ? static_cast<Mom>(v / sqrt(1.0 + v * v) * inv) : Mom(0);
     }
 }
 
@@ -258,19 +354,31 @@ cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s
     return cudaGetLastError();
 }
 
-template <class Real>
-cudaError_t launch_objectives(const Real* xi, const Real* u, const DevState* st,
+template <class Pos, class Mom>
+cudaError_t launch_objectives(const Pos* xi, const Mom* u, const DevState* st,
                               const double* ez, int nz, double dz, double* part,
                               double* out, cudaStream_t s) {
-    objective_partials<Real><<<kObjBlocks, 256, 0, s>>>(xi, u, st, ez, nz, part);
+    objective_partials<Pos, Mom><<<kObjBlocks, 256, 0, s>>>(xi, u, st, ez, nz, part);
     objective_finish<<<1, 32, 0, s>>>(part, kObjBlocks, st, dz, out);
     return cudaGetLastError();
 }
 
-template <class Real>
-cudaError_t launch_seed_gamma(const Real* xi, const Real* u, const DevState* st, Real* lx,
-                              Real* lu, cudaStream_t s) {
-    seed_gamma_kernel<Real><<<1024, 256, 0, s>>>(xi, u, st, lx, lu);
+template <class Pos, class Mom>
+cudaError_t launch_seed_gamma(const Pos* xi, const Mom* u, const DevState* st, Mom* lx,
+                              Mom* lu, cudaStream_t s) {
+    seed_gamma_kernel<Pos, Mom><<<1024, 256, 0, s>>>(xi, u, st, lx, lu);
+    return cudaGetLastError();
+}
+
+int adj_push_fix32_grid_size(int device_sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_push_fix32_kernel, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * device_sms;
+}
+
+cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s) {
+    adj_push_fix32_kernel<<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -286,15 +394,21 @@ template cudaError_t launch_adj_push<float>(const AdjPushArgs<float>&, int, cuda
 template cudaError_t launch_adj_push<double>(const AdjPushArgs<double>&, int, cudaStream_t);
 template int adj_push_grid_size<float>(int);
 template int adj_push_grid_size<double>(int);
-template cudaError_t launch_objectives<float>(const float*, const float*, const DevState*,
-                                              const double*, int, double, double*, double*,
-                                              cudaStream_t);
-template cudaError_t launch_objectives<double>(const double*, const double*, const DevState*,
-                                               const double*, int, double, double*, double*,
-                                               cudaStream_t);
-template cudaError_t launch_seed_gamma<float>(const float*, const float*, const DevState*, float*,
-                                              float*, cudaStream_t);
-template cudaError_t launch_seed_gamma<double>(const double*, const double*, const DevState*,
-                                               double*, double*, cudaStream_t);
+template cudaError_t launch_objectives<float, float>(const float*, const float*, const DevState*,
+                                                     const double*, int, double, double*, double*,
+                                                     cudaStream_t);
+template cudaError_t launch_objectives<double, double>(const double*, const double*,
+                                                       const DevState*, const double*, int, double,
+                                                       double*, double*, cudaStream_t);
+template cudaError_t launch_objectives<int, float>(const int*, const float*, const DevState*,
+                                                   const double*, int, double, double*, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_seed_gamma<float, float>(const float*, const float*, const DevState*,
+                                                     float*, float*, cudaStream_t);
+template cudaError_t launch_seed_gamma<double, double>(const double*, const double*,
+                                                       const DevState*, double*, double*,
+                                                       cudaStream_t);
+template cudaError_t launch_seed_gamma<int, float>(const int*, const float*, const DevState*,
+                                                   float*, float*, cudaStream_t);
 
 }  // namespace sclf

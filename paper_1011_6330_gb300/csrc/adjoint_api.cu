@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "tube_impl.h"
@@ -90,7 +91,9 @@ cudaError_t mark(sclf_adjoint* A, const std::vector<cudaEvent_t>* ev, int i) {
 }
 
 // K forward steps from snapshot 0: step k reads snapshot k and writes k+1.
-template <class Real>
+// Pos is the stored position type (float, double, or int for SCLF_FIX32),
+// Real the precision of the gather table and the particle adjoints.
+template <class Pos, class Real>
 int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
                     const std::vector<cudaEvent_t>* timed, cudaGraphExec_t* out) {
     sclf_tube* t = A->t;
@@ -99,16 +102,29 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = mark(A, timed, 0);
     for (int k = 0; k < A->K && e == cudaSuccess; ++k) {
-        PushArgs<Real> pa = push_args<Real>(t);
-        pa.xi = reinterpret_cast<Real*>(A->sx[k]);
-        pa.u = reinterpret_cast<Real*>(A->su[k]);
-        pa.xo = reinterpret_cast<Real*>(A->sx[k + 1]);
-        pa.uo = reinterpret_cast<Real*>(A->su[k + 1]);
-        pa.ids = nullptr;
-        pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
-        pa.evlog = evlog;
-        pa.replay = replay;
-        e = launch_push<Real>(pa, t->p.accumulate, t->push_grid, s);
+        if constexpr (std::is_same<Pos, int>::value) {
+            PushFixArgs pa = push_fix_args(t);
+            pa.X = reinterpret_cast<int*>(A->sx[k]);
+            pa.u = reinterpret_cast<float*>(A->su[k]);
+            pa.Xo = reinterpret_cast<int*>(A->sx[k + 1]);
+            pa.uo = reinterpret_cast<float*>(A->su[k + 1]);
+            pa.ids = nullptr;
+            pa.ez2 = reinterpret_cast<const float*>(tab_of(A, k));
+            pa.evlog = evlog;
+            pa.replay = replay;
+            e = launch_push_fix32(pa, t->push_grid, s);
+        } else {
+            PushArgs<Real> pa = push_args<Real>(t);
+            pa.xi = reinterpret_cast<Real*>(A->sx[k]);
+            pa.u = reinterpret_cast<Real*>(A->su[k]);
+            pa.xo = reinterpret_cast<Real*>(A->sx[k + 1]);
+            pa.uo = reinterpret_cast<Real*>(A->su[k + 1]);
+            pa.ids = nullptr;
+            pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
+            pa.evlog = evlog;
+            pa.replay = replay;
+            e = launch_push<Real>(pa, t->p.accumulate, t->push_grid, s);
+        }
         if (e == cudaSuccess) e = mark(A, timed, 2 * k + 1);
         if (e != cudaSuccess) break;
         FieldArgs<Real> fa = field_args<Real>(t, k & 1);
@@ -129,7 +145,7 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
 
 // The K steps of a segment in reverse: per step the transposed field update,
 // then the particles.
-template <class Real>
+template <class Pos, class Real>
 int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
                     cudaGraphExec_t* out) {
     sclf_tube* t = A->t;
@@ -156,20 +172,39 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
         e = launch_adj_field<Real>(fa, s);
         if (e == cudaSuccess) e = mark(A, timed, 2 * i + 1);
         if (e != cudaSuccess) break;
-        AdjPushArgs<Real> pa;
-        pa.xi = reinterpret_cast<const Real*>(A->sx[k]);
-        pa.u = reinterpret_cast<const Real*>(A->su[k]);
-        pa.lx = reinterpret_cast<Real*>(A->lx);
-        pa.lu = reinterpret_cast<Real*>(A->lu);
-        pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
-        pa.ls_tab = reinterpret_cast<const Real*>(A->ls_tab);
-        pa.lez = A->lez;
-        pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
-        pa.nz = A->nz;
-        pa.nzf = static_cast<Real>(A->nz);
-        pa.dt = static_cast<Real>(t->d.dt);
-        pa.cfl = static_cast<Real>(t->d.dt / t->d.dz);
-        e = launch_adj_push<Real>(pa, A->adj_grid, s);
+        if constexpr (std::is_same<Pos, int>::value) {
+            AdjPushFixArgs pa;
+            pa.X = reinterpret_cast<const int*>(A->sx[k]);
+            pa.u = reinterpret_cast<const float*>(A->su[k]);
+            pa.lx = reinterpret_cast<float*>(A->lx);
+            pa.lu = reinterpret_cast<float*>(A->lu);
+            pa.ez2 = reinterpret_cast<const float*>(tab_of(A, k));
+            pa.ls_tab = reinterpret_cast<const float*>(A->ls_tab);
+            pa.lez = A->lez;
+            pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
+            pa.nz = A->nz;
+            pa.fb = t->fb;
+            pa.dt = static_cast<float>(t->d.dt);
+            pa.cfl = static_cast<float>(t->d.dt / t->d.dz);
+            pa.scale = std::ldexp(1.0f, -t->fb);
+            pa.two_fb = std::ldexp(1.0f, t->fb);
+            e = launch_adj_push_fix32(pa, A->adj_grid, s);
+        } else {
+            AdjPushArgs<Real> pa;
+            pa.xi = reinterpret_cast<const Real*>(A->sx[k]);
+            pa.u = reinterpret_cast<const Real*>(A->su[k]);
+            pa.lx = reinterpret_cast<Real*>(A->lx);
+            pa.lu = reinterpret_cast<Real*>(A->lu);
+            pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
+            pa.ls_tab = reinterpret_cast<const Real*>(A->ls_tab);
+            pa.lez = A->lez;
+            pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
+            pa.nz = A->nz;
+            pa.nzf = static_cast<Real>(A->nz);
+            pa.dt = static_cast<Real>(t->d.dt);
+            pa.cfl = static_cast<Real>(t->d.dt / t->d.dz);
+            e = launch_adj_push<Real>(pa, A->adj_grid, s);
+        }
         if (e == cudaSuccess) e = mark(A, timed, 2 * i + 2);
     }
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -186,14 +221,14 @@ enum { kFwdPush, kFwdField, kRecPush, kRecField, kRevField, kRevPush };
 // Segment graph kinds.
 enum { kGraphFwd, kGraphFwdUser, kGraphRecompute, kGraphRev };
 
-template <class Real>
+template <class Pos, class Real>
 int capture_kind(sclf_adjoint* A, int kind, const std::vector<cudaEvent_t>* ev,
                  cudaGraphExec_t* out) {
     switch (kind) {
-        case kGraphFwd: return capture_forward<Real>(A, A->evlog, nullptr, ev, out);
-        case kGraphFwdUser: return capture_forward<Real>(A, A->evlog, A->ulog, ev, out);
-        case kGraphRecompute: return capture_forward<Real>(A, nullptr, A->evlog, ev, out);
-        default: return capture_reverse<Real>(A, ev, out);
+        case kGraphFwd: return capture_forward<Pos, Real>(A, A->evlog, nullptr, ev, out);
+        case kGraphFwdUser: return capture_forward<Pos, Real>(A, A->evlog, A->ulog, ev, out);
+        case kGraphRecompute: return capture_forward<Pos, Real>(A, nullptr, A->evlog, ev, out);
+        default: return capture_reverse<Pos, Real>(A, ev, out);
     }
 }
 
@@ -226,12 +261,12 @@ int collect_all(sclf_adjoint* A) {
 // Launch one segment graph of the given kind (building it on first use). In
 // timing mode every n-th segment of a kind replays a timed instance, after
 // reading back the one replayed two timed launches ago.
-template <class Real>
+template <class Pos, class Real>
 int launch_segment(sclf_adjoint* A, int kind, int ka, int kb) {
     int rc;
     const bool timed = A->timing > 0 && A->seg_count[kind]++ % A->timing == 0;
     if (!timed) {
-        if (!A->plain[kind] && (rc = capture_kind<Real>(A, kind, nullptr, &A->plain[kind])))
+        if (!A->plain[kind] && (rc = capture_kind<Pos, Real>(A, kind, nullptr, &A->plain[kind])))
             return rc;
         CK(cudaGraphLaunch(A->plain[kind], A->t->gstream));
         return SCLF_OK;
@@ -241,7 +276,7 @@ int launch_segment(sclf_adjoint* A, int kind, int ka, int kb) {
         g.ev.assign(2 * A->K + 1, nullptr);
         for (cudaEvent_t& e : g.ev)
             if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return SCLF_ECUDA; }
-        if ((rc = capture_kind<Real>(A, kind, &g.ev, &g.exec))) return rc;
+        if ((rc = capture_kind<Pos, Real>(A, kind, &g.ev, &g.exec))) return rc;
     }
     if ((rc = collect(A, g))) return rc;
     CK(cudaGraphLaunch(g.exec, A->t->gstream));
@@ -296,7 +331,7 @@ cudaError_t table0(sclf_adjoint* A) {
                                  A->t->gstream);
 }
 
-template <class Real>
+template <class Pos, class Real>
 int run_forward(sclf_adjoint* A, double* values) {
     sclf_tube* t = A->t;
     cudaStream_t s = t->gstream;
@@ -327,7 +362,7 @@ int run_forward(sclf_adjoint* A, double* values) {
             rc = save_checkpoint(A, c, 0);
             if (rc) return rc;
         }
-        rc = launch_segment<Real>(A, kind, kFwdPush, kFwdField);
+        rc = launch_segment<Pos, Real>(A, kind, kFwdPush, kFwdField);
         if (rc) return rc;
         if (c + 1 < A->nseg) {
             CK(cudaMemcpyAsync(A->sx[0], A->sx[A->K], bytes, cudaMemcpyDeviceToDevice, s));
@@ -340,9 +375,9 @@ int run_forward(sclf_adjoint* A, double* values) {
     // the end of the run: checkpoint nseg, the objectives, the tube's own arrays
     rc = save_checkpoint(A, A->nseg, A->K);
     if (rc) return rc;
-    CK(launch_objectives<Real>(reinterpret_cast<const Real*>(A->sx[A->K]),
-                               reinterpret_cast<const Real*>(A->su[A->K]), t->st, t->ez,
-                               static_cast<int>(nz), t->d.dz, A->part, A->values, s));
+    CK((launch_objectives<Pos, Real>(reinterpret_cast<const Pos*>(A->sx[A->K]),
+                                     reinterpret_cast<const Real*>(A->su[A->K]), t->st, t->ez,
+                                     static_cast<int>(nz), t->d.dz, A->part, A->values, s)));
     CK(cudaMemcpyAsync(t->xi, A->sx[A->K], bytes, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(t->u, A->su[A->K], bytes, cudaMemcpyDeviceToDevice, s));
     double hv[2];
@@ -361,7 +396,7 @@ int run_forward(sclf_adjoint* A, double* values) {
     return SCLF_OK;
 }
 
-template <class Real>
+template <class Pos, class Real>
 int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
     sclf_tube* t = A->t;
     cudaStream_t s = t->gstream;
@@ -376,10 +411,10 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
     CK(cudaMemsetAsync(A->lx, 0, bytes, s));
     CK(cudaMemsetAsync(A->lu, 0, bytes, s));
     if (objective == SCLF_OBJ_GAMMA) {
-        CK(launch_seed_gamma<Real>(reinterpret_cast<const Real*>(A->ck_x + A->nseg * bytes),
-                                   reinterpret_cast<const Real*>(A->ck_u + A->nseg * bytes),
-                                   A->ck_st + A->nseg, reinterpret_cast<Real*>(A->lx),
-                                   reinterpret_cast<Real*>(A->lu), s));
+        CK((launch_seed_gamma<Pos, Real>(reinterpret_cast<const Pos*>(A->ck_x + A->nseg * bytes),
+                                         reinterpret_cast<const Real*>(A->ck_u + A->nseg * bytes),
+                                         A->ck_st + A->nseg, reinterpret_cast<Real*>(A->lx),
+                                         reinterpret_cast<Real*>(A->lu), s)));
     } else {
         CK(launch_seed_ez(ckf_of(A, A->nseg), static_cast<int>(nz), t->d.dz, A->values, A->lez, s));
     }
@@ -389,13 +424,13 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
             rc = restore_checkpoint(A, c);
             if (rc) return rc;
             CK(table0<Real>(A));
-            rc = launch_segment<Real>(A, kGraphRecompute, kRecPush, kRecField);
+            rc = launch_segment<Pos, Real>(A, kGraphRecompute, kRecPush, kRecField);
             if (rc) return rc;
             A->current_seg = c;
         }
         CK(cudaMemcpyAsync(A->seglog, A->evlog + static_cast<int64_t>(kLogStride) * c * A->K,
                            static_cast<int64_t>(kLogStride) * A->K * 8, cudaMemcpyDeviceToDevice, s));
-        rc = launch_segment<Real>(A, kGraphRev, kRevField, kRevPush);
+        rc = launch_segment<Pos, Real>(A, kGraphRev, kRevField, kRevPush);
         if (rc) return rc;
     }
     CK(cudaEventRecord(A->ev[3], s));
@@ -452,7 +487,8 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
                    adjoint_t* out) {
     if (!p || !out) return SCLF_EINVAL;
     *out = nullptr;
-    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64) return SCLF_EINVAL;
+    if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64 && p->precision != SCLF_FIX32)
+        return SCLF_EINVAL;
     if (p->accumulate != SCLF_ACC_FIXED64) return SCLF_EINVAL;
     if (checkpoint_every <= 0 || (checkpoint_every & 1) || nsteps <= 0 ||
         nsteps % checkpoint_every != 0)
@@ -532,7 +568,8 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
     for (cudaEvent_t& e : A->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; free_adjoint(A); return SCLF_ECUDA; }
     const int64_t tiles = A->cap_pad / (A->rs == 8 ? Layout<double>::kTile : Layout<float>::kTile);
-    A->adj_grid = A->rs == 8 ? adj_push_grid_size<double>(t->sms) : adj_push_grid_size<float>(t->sms);
+    A->adj_grid = fix32(t) ? adj_push_fix32_grid_size(t->sms)
+                : A->rs == 8 ? adj_push_grid_size<double>(t->sms) : adj_push_grid_size<float>(t->sms);
     if (A->adj_grid > tiles) A->adj_grid = static_cast<int>(tiles);
     *out = A;
     return SCLF_OK;
@@ -570,7 +607,8 @@ int adjoint_set_injections(adjoint_t a, const int64_t* n_inj) {
 int adjoint_forward(adjoint_t a, double* values) {
     if (!a) return SCLF_EINVAL;
     CK(cudaStreamSynchronize(a->t->stream));
-    return a->rs == 8 ? run_forward<double>(a, values) : run_forward<float>(a, values);
+    if (fix32(a->t)) return run_forward<int, float>(a, values);
+    return a->rs == 8 ? run_forward<double, double>(a, values) : run_forward<float, float>(a, values);
 }
 
 int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_slots) {
@@ -590,8 +628,9 @@ int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_s
 int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s) {
     if (!a || (objective != SCLF_OBJ_GAMMA && objective != SCLF_OBJ_EZ)) return SCLF_EINVAL;
     if (!a->forward_done) return SCLF_ESTATE;
-    return a->rs == 8 ? run_backward<double>(a, objective, d_rho_gj, d_s)
-                      : run_backward<float>(a, objective, d_rho_gj, d_s);
+    if (fix32(a->t)) return run_backward<int, float>(a, objective, d_rho_gj, d_s);
+    return a->rs == 8 ? run_backward<double, double>(a, objective, d_rho_gj, d_s)
+                      : run_backward<float, float>(a, objective, d_rho_gj, d_s);
 }
 
 int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double* grad) {

@@ -1,5 +1,6 @@
 // (a1)-(a5) of one PIC step (Sec. 2, Figure A of arXiv:1011.6330) for tubes
-// whose particle positions are 32-bit fixed point (SCLF_FIX32).
+// whose particle positions are 32-bit fixed point (SCLF_FIX32). The slots are
+// streamed in place or (for a recorded run) into a separate output array.
 #include "device_common.cuh"
 
 namespace sclf {
@@ -18,7 +19,7 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
     DevState* st = a.st;
     const long long n_slots = st->n_slots;
-    const long long n_req = st->n_inj;
+    const long long n_req = a.replay ? a.replay[kLogStride * st->step + kLogInjected] : st->n_inj;
     long long room = a.capacity - n_slots;
     room = room > 0 ? room : 0;
     const long long n_inj = n_req < room ? n_req : room;
@@ -26,6 +27,10 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
         st->inj_done = n_inj;
         st->slots_processed += static_cast<unsigned long long>(n_slots + n_inj);
         if (n_inj < n_req) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
+        if (a.evlog) {
+            a.evlog[kLogStride * st->step + kLogSlots] = n_slots;
+            a.evlog[kLogStride * st->step + kLogInjected] = n_inj;
+        }
     }
     const long long n_tot = n_slots + n_inj;
     const long long id0 = st->total_injected;
@@ -140,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
 #pragma unroll
         for (int v = 0; v < kPPT; v += kVec) {
             if (i0 + v < n_tot) {
-                vstore(a.X + i0 + v, xs + v);
-                vstore(a.u + i0 + v, us + v);
+                vstore(a.Xo + i0 + v, xs + v);
+                vstore(a.uo + i0 + v, us + v);
             }
         }
         const int key = rkey == 0xffffffffu ? -1 : static_cast<int>(rkey);

@@ -124,8 +124,12 @@ struct PushFixArgs {
     DevState* st;
     int* X;
     float* u;
+    int* Xo;                   // where the pushed slots go (X itself: in place)
+    float* uo;
     long long* ids;            // may be null
     const float* ez2;          // gather table, float32
+    long long* evlog;          // may be null: records slots and injections per step
+    const long long* replay;   // may be null: injection counts to use instead
     long long* jacc;           // nz accumulators, 2^-32 units
     long long capacity;
     int nz;
@@ -206,6 +210,21 @@ struct AdjPushArgs {
     Real nzf, dt, cfl;
 };
 
+// The same for SCLF_FIX32 positions (X = xi 2^fb, holes < 0); adjoints in
+// cell units, float32.
+struct AdjPushFixArgs {
+    const int* X;
+    const float* u;
+    float* lx;
+    float* lu;
+    const float* ez2;
+    const float* ls_tab;
+    double* lez;
+    const long long* log;
+    int nz, fb;
+    float dt, cfl, scale, two_fb;
+};
+
 // Launchers. All return cudaGetLastError() after the launch.
 template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid,
@@ -260,19 +279,21 @@ template <class Real>
 cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s);
 template <class Real>
 int adj_push_grid_size(int device_sms);
+cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s);
+int adj_push_fix32_grid_size(int device_sms);
 // Sums over the final state of a recorded run: out[0] = mean gamma of the
 // live slots, out[1] = ||E_z||_2 = sqrt(sum E_z^2 dz). part holds
 // 2 * kObjBlocks doubles.
 constexpr int kObjBlocks = 256;
-template <class Real>
-cudaError_t launch_objectives(const Real* xi, const Real* u, const DevState* st,
+template <class Pos, class Mom>
+cudaError_t launch_objectives(const Pos* xi, const Mom* u, const DevState* st,
                               const double* ez, int nz, double dz, double* part,
                               double* out, cudaStream_t s);
 // Adjoint seeds: lambda_u = u / gamma / N_live (mean gamma), lambda_E =
 // E dz / ||E|| (field norm).
-template <class Real>
-cudaError_t launch_seed_gamma(const Real* xi, const Real* u, const DevState* st, Real* lx,
-                              Real* lu, cudaStream_t s);
+template <class Pos, class Mom>
+cudaError_t launch_seed_gamma(const Pos* xi, const Mom* u, const DevState* st, Mom* lx,
+                              Mom* lu, cudaStream_t s);
 cudaError_t launch_seed_ez(const double* ez, int nz, double dz, const double* values,
                            double* lez, cudaStream_t s);
 

@@ -64,23 +64,6 @@ CompactArgs<Pos, Mom> compact_args(sclf_tube* t, int force) {
 }
 
 
-PushFixArgs push_fix_args(sclf_tube* t) {
-    PushFixArgs a;
-    a.st = t->st;
-    a.X = static_cast<int*>(t->xi);
-    a.u = static_cast<float*>(t->u);
-    a.ids = t->ids;
-    a.ez2 = static_cast<const float*>(t->ez2);
-    a.jacc = static_cast<long long*>(t->jacc);
-    a.capacity = t->p.capacity;
-    a.nz = static_cast<int>(t->p.Nz);
-    a.fb = t->fb;
-    a.dt = static_cast<float>(t->d.dt);
-    a.cfl = static_cast<float>(t->d.dt / t->d.dz);
-    a.scale = std::ldexp(1.0f, -t->fb);
-    a.two_fb = std::ldexp(1.0f, t->fb);
-    return a;
-}
 
 // Per-precision launches of the small kernels.
 cudaError_t do_append(sclf_tube* t, long long first, long long n, bool zero) {

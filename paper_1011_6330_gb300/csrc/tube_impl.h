@@ -124,6 +124,28 @@ inline FieldArgs<Real> field_args(sclf_tube* t, int parity) {
     return a;
 }
 
+inline PushFixArgs push_fix_args(sclf_tube* t) {
+    PushFixArgs a;
+    a.st = t->st;
+    a.X = static_cast<int*>(t->xi);
+    a.u = static_cast<float*>(t->u);
+    a.Xo = a.X;
+    a.uo = a.u;
+    a.ids = t->ids;
+    a.ez2 = static_cast<const float*>(t->ez2);
+    a.evlog = nullptr;
+    a.replay = nullptr;
+    a.jacc = static_cast<long long*>(t->jacc);
+    a.capacity = t->p.capacity;
+    a.nz = static_cast<int>(t->p.Nz);
+    a.fb = t->fb;
+    a.dt = static_cast<float>(t->d.dt);
+    a.cfl = static_cast<float>(t->d.dt / t->d.dz);
+    a.scale = std::ldexp(1.0f, -t->fb);
+    a.two_fb = std::ldexp(1.0f, t->fb);
+    return a;
+}
+
 inline cudaError_t do_ez_table(sclf_tube* t) {
     const int nz = static_cast<int>(t->p.Nz);
     return fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), nz, t->stream)

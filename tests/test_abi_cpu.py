@@ -85,12 +85,13 @@ def test_workspace_grows_with_capacity_and_grid(lib):
 
 
 def test_adjoint_create_validates_before_touching_the_device():
-    """adjoint_create rejects FIX32 particles, FP64 atomics and bad
-    checkpoint intervals with SCLF_EINVAL before any CUDA call."""
+    """adjoint_create rejects FP64 atomics (the recompute must reproduce the
+    run bit for bit) and bad checkpoint intervals with SCLF_EINVAL before
+    any CUDA call."""
     import ctypes as C
     lib = B.load()
     h = C.c_void_p()
-    for kw, n, k in ((dict(precision=B.SCLF_FIX32, Nz=1024), 100, 10),
+    for kw, n, k in ((dict(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FP64), 100, 10),
                      (dict(accumulate=B.SCLF_ACC_FP64), 100, 10),
                      (dict(), 100, 7), (dict(), 100, 0), (dict(), 105, 10), (dict(), 0, 10)):
         p = B.default_params(**kw)

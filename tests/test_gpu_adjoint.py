@@ -21,7 +21,8 @@ from paper_1011_6330_gb300 import synth, workloads
 
 pytestmark = pytest.mark.gpu
 
-TOL = {B.SCLF_FP64: 1e-9, B.SCLF_FP32: 1e-6}
+TOL = {B.SCLF_FP64: 1e-9, B.SCLF_FP32: 1e-6, B.SCLF_FIX32: 1e-6}
+OPREC = {B.SCLF_FP64: "f64", B.SCLF_FP32: "f32", B.SCLF_FIX32: "fix32"}
 M_STAR = 1.4 * orc.M_SUN
 
 
@@ -67,15 +68,15 @@ def oracle_run(kw, z, u, prec):
         zz = np.arange(nz + 1) * (L / nz)
         rho = orc.rho_gj_profile(kw["rho_gj_mode"], zz, cu["Lambda0"], kw["incl_rad"],
                                  cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
-    return oadj.AdjointRun(nz, L, d["dt"], rho, d["s"], z, u,
-                           precision="f64" if prec == B.SCLF_FP64 else "f32",
+    return oadj.AdjointRun(nz, L, d["dt"], rho, d["s"], z, u, precision=OPREC[prec],
                            accumulate="fixed")
 
 
-@pytest.mark.parametrize("prec", [B.SCLF_FP64, B.SCLF_FP32])
+@pytest.mark.parametrize("prec", [B.SCLF_FP64, B.SCLF_FP32, B.SCLF_FIX32])
 def test_adjoint_matches_oracle_flat_tube(gpu_lib, prec):
     """Flat SCLF tube (Nz = 1024, rho_GJ = -1), 2e4 prefilled electrons plus
-    injection, 60 steps in 6 checkpointed segments."""
+    injection, 60 steps in 6 checkpointed segments; FP64, FP32 and 32-bit
+    fixed-point particles."""
     kw, z, u, nsteps, K = flat_problem(prec)
     a, vals = gpu_run(kw, z, u, nsteps, K)
     run = oracle_run(kw, z, u, prec)
@@ -84,7 +85,7 @@ def test_adjoint_matches_oracle_flat_tube(gpu_lib, prec):
         v, d_rho, d_s, inj, rem = run.gradient(which, nsteps)
         assert np.array_equal(ev["injected"], inj)
         assert np.array_equal(ev["removed"], [len(r) for r in rem])
-        assert abs(vals[i] - v) <= 1e-12 * abs(v) + (1e-6 * abs(v) if prec == B.SCLF_FP32 and i == 1 else 0)
+        assert abs(vals[i] - v) <= 1e-12 * abs(v) + (1e-6 * abs(v) if prec != B.SCLF_FP64 and i == 1 else 0)
         g_rho, g_s = a.backward(i)
         e_rho, e_s = rel(g_rho, d_rho), abs(g_s - d_s) / abs(d_s)
         print(which, "prec", prec, "d_rho err", e_rho, "d_s err", e_s)
@@ -217,3 +218,22 @@ def test_timed_passes_count_kernels_and_keep_the_gradient(gpu_lib):
     assert kt["forward_push"][1] == 2 * K and kt["reverse_push"][1] == 2 * K
     assert kt["recompute_push"][1] == 2 * K      # 3 recomputed segments: 1st and 3rd
     a.close()
+
+
+def test_fix32_gradient_against_fp64_is_stated(gpu_lib):
+    """Frame-dragging tube of config 4 at Nz = 1024 with 5e4 electrons, 100
+    steps: the FP32 and 32-bit fixed-point gradients against the FP64 one
+    (printed; the fixed-point positions must be at least as close)."""
+    errs = {}
+    grads = {}
+    for prec in (B.SCLF_FP64, B.SCLF_FP32, B.SCLF_FIX32):
+        kw, z, u, nsteps, K = gr_problem(prec)
+        a, vals = gpu_run(kw, z, u, nsteps, K)
+        grads[prec] = [a.param_gradient(*a.backward(i)) for i in range(2)]
+        a.close()
+    for prec in (B.SCLF_FP32, B.SCLF_FIX32):
+        errs[prec] = max(float(np.max(np.abs(g - r) / np.abs(r)))
+                         for g, r in zip(grads[prec], grads[B.SCLF_FP64]))
+    print("max rel gradient error vs FP64: fp32 %.3e fix32 %.3e" % (errs[B.SCLF_FP32],
+                                                                  errs[B.SCLF_FIX32]))
+    assert errs[B.SCLF_FIX32] <= max(errs[B.SCLF_FP32], 1e-6)

@@ -172,3 +172,17 @@ def test_float32_trajectory_gradient_is_close_to_float64():
     assert abs(v32 - v64) <= 1e-6 * v64
     assert np.max(np.abs(g32 - g64)) <= 1e-3 * np.max(np.abs(g64))
     assert abs(s32 - s64) <= 1e-3 * abs(s64)
+
+
+def test_fix32_trajectory_gradient_is_close_to_float64():
+    """The adjoint of the 32-bit fixed-point run (displacement rounding
+    differentiated as the identity, reverse sweep in FP64) stays close to the
+    FP64 run's on a short run."""
+    run, n = flat_case()
+    v64, g64, s64, inj, _ = run.gradient("gamma", n)
+    runx = adj.AdjointRun(run.nz, run.L, run.dt, run.rho_gj, run.s, run.z0, run.u0,
+                          precision="fix32", accumulate="fixed")
+    vx, gx, sx, _, _ = runx.gradient("gamma", n, injections=inj)
+    assert abs(vx - v64) <= 1e-7 * v64
+    assert np.max(np.abs(gx - g64)) <= 1e-5 * np.max(np.abs(g64))
+    assert abs(sx - s64) <= 1e-5 * abs(s64)
