@@ -240,14 +240,20 @@ int tube_read_particles(tube_t t, int64_t cap, int64_t* n, double* z,
 /* Raw particle state in the tube's precision, live particles only, ID order:
  * positions xi = z / dz as float (SCLF_FP32) or double (SCLF_FP64), or as
  * int32 X = xi / pos_unit (SCLF_FIX32); u as float (FP32, FIX32) or double.
- * Host buffers of capacity cap; *n receives the live count. Synchronises.
+ * Host buffers of capacity cap (pinned memory makes the copies fastest);
+ * *n receives the live count. The slots are compacted on the device first
+ * (the order and every result stay as they were). Synchronises.
  * (Checkpointing.) */
 int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u,
                         int64_t* id);
 
 /* Replace all particles by n raw particles (host, layout as
- * tube_save_particles; id may be NULL to number them 0..n-1). Holes are
- * not allowed (every xi in [0, Nz)). Synchronises. */
+ * tube_save_particles; id may be NULL to number them 0..n-1, and must be
+ * NULL for a tube without IDs). Holes are not allowed: every position must
+ * lie in [0, Nz) cells, every u be finite and every ID be >= 0; the arrays
+ * are copied to the device and checked there, and on SCLF_EINVAL the tube
+ * is left without particles. IDs continue after the largest loaded one.
+ * Synchronises. */
 int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u,
                         const int64_t* id);
 

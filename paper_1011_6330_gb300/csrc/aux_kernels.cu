@@ -45,6 +45,30 @@ __global__ void base_weight_fix32_kernel(DevState* st, const int* X, long long n
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
 }
 
+template <class Pos, class Mom>
+__global__ void validate_kernel(DevState* st, const Pos* xi, const Mom* u, const long long* ids,
+                                long long n, double top) {
+    bool bad = false;
+    long long mx = -1;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double x = static_cast<double>(xi[i]);        // exact for every Pos
+        if (!(x >= 0.0 && x < top) || !isfinite(static_cast<double>(u[i]))) bad = true;
+        if (ids) {
+            const long long id = ids[i];
+            if (id < 0) bad = true;
+            mx = id > mx ? id : mx;
+        }
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->load_bad, 1u);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long o = __shfl_xor_sync(kFull, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx >= 0) atomicMax(&st->max_id, mx);
+}
+
 __global__ void finish_append_kernel(DevState* st, const double* ez, long long n_added,
                                      FieldConsts c) {
     st->n_slots += n_added;
@@ -116,6 +140,14 @@ cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots, 
     return cudaGetLastError();
 }
 
+template <class Pos, class Mom>
+cudaError_t launch_validate(DevState* st, const Pos* xi, const Mom* u, const long long* ids,
+                            long long n, double top, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    validate_kernel<Pos, Mom><<<grid_for(n, 256, 4096), 256, 0, s>>>(st, xi, u, ids, n, top);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish_append(DevState* st, const double* ez, long long n_added,
                                  FieldConsts c, cudaStream_t s) {
     finish_append_kernel<<<1, 1, 0, s>>>(st, ez, n_added, c);
@@ -142,6 +174,13 @@ template cudaError_t launch_append<double, double>(DevState*, double*, double*, 
                                                   long long, long long, bool, cudaStream_t);
 template cudaError_t launch_append<int, float>(DevState*, int*, float*, long long*, long long,
                                               long long, bool, cudaStream_t);
+template cudaError_t launch_validate<float, float>(DevState*, const float*, const float*,
+                                                  const long long*, long long, double, cudaStream_t);
+template cudaError_t launch_validate<double, double>(DevState*, const double*, const double*,
+                                                    const long long*, long long, double,
+                                                    cudaStream_t);
+template cudaError_t launch_validate<int, float>(DevState*, const int*, const float*,
+                                                const long long*, long long, double, cudaStream_t);
 template cudaError_t launch_base_weight<float>(DevState*, const float*, long long, cudaStream_t);
 template cudaError_t launch_base_weight<double>(DevState*, const double*, long long, cudaStream_t);
 template cudaError_t launch_ez_table<float>(const double*, float*, int, cudaStream_t);

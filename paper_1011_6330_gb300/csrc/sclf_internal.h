@@ -57,7 +57,7 @@ struct DevState {
     long long last_removed;
     double surface_field;       // E_s that produced n_inj
     unsigned int flags;         // SCLF_FLAG_* (sticky)
-    unsigned int pad0;
+    unsigned int load_bad;      // set by the validation of loaded particles
     // accumulated by the particle kernel during a step
     unsigned long long acc_w0;
     unsigned long long acc_removed;
@@ -66,7 +66,8 @@ struct DevState {
     unsigned int ticket;        // tile ticket of the compaction kernel
     unsigned int compact_epoch; // tags tile states of one compaction
     unsigned long long slots_processed;  // running sum of slots pushed
-    long long pad1[3];
+    long long max_id;           // largest loaded particle ID
+    long long pad1[2];
 };
 
 // Per-step event log of a recorded run: kLogStride entries per step, indexed
@@ -264,6 +265,12 @@ cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots,
                                cudaStream_t s);
 cudaError_t launch_base_weight_fix32(DevState* st, const int* X, long long n_slots,
                                      int fb, cudaStream_t s);
+// Checks n loaded slots: 0 <= position < top (in stored position units, as a
+// double so that Nz 2^fb = 2^31 fits), finite momentum, IDs >= 0
+// (sets st->load_bad), and the largest ID (st->max_id).
+template <class Pos, class Mom>
+cudaError_t launch_validate(DevState* st, const Pos* xi, const Mom* u, const long long* ids,
+                            long long n, double top, cudaStream_t s);
 cudaError_t launch_finish_append(DevState* st, const double* ez,
                                  long long n_added, FieldConsts c,
                                  cudaStream_t s);

@@ -611,39 +611,44 @@ int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi, double* J, 
     return SCLF_OK;
 }
 
+// Live particles in ID order: a forced (stable) compaction on the device
+// first, so that slots [0, n_live) hold them without holes; then one copy per
+// array straight into the caller's memory (convert: z = xi dz and u as
+// double, through host staging).
 static int read_raw(tube_t t, int64_t cap, int64_t* n, void* xo, void* uo, int64_t* ido,
                     bool convert) {
+    CK(enqueue_compact(t, t->stream, 1));
+    t->steps_since_compact = 0;
     DevState h;
     int rc = read_state(t, &h);
     if (rc) return rc;
-    const int64_t ns = h.n_slots;
+    if (h.flags & SCLF_FLAG_TIMEOUT) return SCLF_ETIMEOUT;
+    const int64_t ns = h.n_slots;                    // == live particles after compaction
+    const int64_t m = ns < cap ? ns : cap;
     const int64_t rs = fp64(t) ? 8 : 4;
-    std::vector<char> xs(ns * rs), us(ns * rs);
-    std::vector<long long> is(t->ids ? ns : 0);
-    if (ns > 0) {
-        CK(cudaMemcpyAsync(xs.data(), t->xi, ns * rs, cudaMemcpyDeviceToHost, t->stream));
-        CK(cudaMemcpyAsync(us.data(), t->u, ns * rs, cudaMemcpyDeviceToHost, t->stream));
-        if (t->ids) CK(cudaMemcpyAsync(is.data(), t->ids, ns * 8, cudaMemcpyDeviceToHost, t->stream));
-        CK(cudaStreamSynchronize(t->stream));
-    }
-    int64_t k = 0;
-    for (int64_t i = 0; i < ns; ++i) {
-        const double x = raw_cells(t, xs.data(), i);
-        if (!(x >= 0.0)) continue;                       // hole
-        if (k < cap) {
-            const double uu = raw_mom(t, us.data(), i);
-            if (convert) {
-                if (xo) static_cast<double*>(xo)[k] = x * t->d.dz;
-                if (uo) static_cast<double*>(uo)[k] = uu;
-            } else {
-                if (xo) std::memcpy(static_cast<char*>(xo) + k * rs, xs.data() + i * rs, rs);
-                if (uo) std::memcpy(static_cast<char*>(uo) + k * rs, us.data() + i * rs, rs);
+    if (m > 0) {
+        if (convert) {
+            std::vector<char> xs(m * rs), us(m * rs);
+            CK(cudaMemcpyAsync(xs.data(), t->xi, m * rs, cudaMemcpyDeviceToHost, t->stream));
+            CK(cudaMemcpyAsync(us.data(), t->u, m * rs, cudaMemcpyDeviceToHost, t->stream));
+            if (ido && t->ids)
+                CK(cudaMemcpyAsync(ido, t->ids, m * 8, cudaMemcpyDeviceToHost, t->stream));
+            CK(cudaStreamSynchronize(t->stream));
+            for (int64_t i = 0; i < m; ++i) {
+                if (xo) static_cast<double*>(xo)[i] = raw_cells(t, xs.data(), i) * t->d.dz;
+                if (uo) static_cast<double*>(uo)[i] = raw_mom(t, us.data(), i);
             }
-            if (ido) ido[k] = t->ids ? is[i] : -1;
+        } else {
+            if (xo) CK(cudaMemcpyAsync(xo, t->xi, m * rs, cudaMemcpyDeviceToHost, t->stream));
+            if (uo) CK(cudaMemcpyAsync(uo, t->u, m * rs, cudaMemcpyDeviceToHost, t->stream));
+            if (ido && t->ids)
+                CK(cudaMemcpyAsync(ido, t->ids, m * 8, cudaMemcpyDeviceToHost, t->stream));
+            CK(cudaStreamSynchronize(t->stream));
         }
-        ++k;
+        if (ido && !t->ids)
+            for (int64_t i = 0; i < m; ++i) ido[i] = -1;
     }
-    if (n) *n = k;
+    if (n) *n = ns;
     return SCLF_OK;
 }
 
@@ -659,13 +664,9 @@ int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u, in
 
 int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, const int64_t* id) {
     if (!t || n < 0 || n > t->p.capacity || (n > 0 && (!xi || !u))) return SCLF_EINVAL;
-    int64_t max_id = n - 1;
-    for (int64_t i = 0; i < n; ++i) {
-        const double x = raw_cells(t, xi, i);
-        const double v = raw_mom(t, u, i);
-        if (!(x >= 0.0 && x < double(t->p.Nz)) || !std::isfinite(v)) return SCLF_EINVAL;
-        if (id && id[i] > max_id) max_id = id[i];
-    }
+    if (id && !t->ids) return SCLF_EINVAL;
+    // the counters start from an empty tube; the raw arrays go straight to
+    // the slots and are checked on the device
     DevState h;
     int rc = read_state(t, &h);
     if (rc) return rc;
@@ -673,14 +674,48 @@ int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, cons
     h.n_live = 0;
     h.total_injected = 0;
     h.w0 = 0;
+    h.acc_w0 = 0;
+    h.load_bad = 0;
+    h.max_id = -1;
     CK(cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream));
-    rc = append_raw(t, n, xi, u, id);
+    const int64_t rs = fp64(t) ? 8 : 4;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(t->xi, xi, n * rs, cudaMemcpyHostToDevice, t->stream));
+        CK(cudaMemcpyAsync(t->u, u, n * rs, cudaMemcpyHostToDevice, t->stream));
+        if (id) CK(cudaMemcpyAsync(t->ids, id, n * 8, cudaMemcpyHostToDevice, t->stream));
+        else if (t->ids) CK(do_append(t, 0, n, false));       // IDs 0..n-1
+        const long long* dev_ids = id ? t->ids : nullptr;
+        if (fp64(t)) {
+            CK((launch_validate<double, double>(t->st, static_cast<const double*>(t->xi),
+                                                static_cast<const double*>(t->u), dev_ids, n,
+                                                double(t->p.Nz), t->stream)));
+        } else if (fix32(t)) {
+            CK((launch_validate<int, float>(t->st, static_cast<const int*>(t->xi),
+                                            static_cast<const float*>(t->u), dev_ids, n,
+                                            std::ldexp(double(t->p.Nz), t->fb), t->stream)));
+        } else {
+            CK((launch_validate<float, float>(t->st, static_cast<const float*>(t->xi),
+                                              static_cast<const float*>(t->u), dev_ids, n,
+                                              double(t->p.Nz), t->stream)));
+        }
+        CK(do_base_weight(t, 0, n));
+    }
+    CK(launch_finish_append(t->st, t->ez, n, t->fc, t->stream));
+    rc = read_state(t, &h);
     if (rc) return rc;
-    if (id) {   // IDs continue after the largest loaded one
-        rc = read_state(t, &h);
-        if (rc) return rc;
-        h.total_injected = max_id + 1;
+    if (h.load_bad) {
+        // leave an empty tube rather than particles that failed the check
+        h.n_slots = h.n_live = h.total_injected = h.w0 = 0;
+        h.load_bad = 0;
         CK(cudaMemcpyAsync(t->st, &h, sizeof(h), cudaMemcpyHostToDevice, t->stream));
+        CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
+        CK(cudaStreamSynchronize(t->stream));
+        return SCLF_EINVAL;
+    }
+    if (id && h.max_id + 1 > h.total_injected) {   // IDs continue after the largest loaded one
+        h.total_injected = h.max_id + 1;
+        CK(cudaMemcpyAsync(&t->st->total_injected, &h.total_injected, sizeof(long long),
+                           cudaMemcpyHostToDevice, t->stream));
         CK(cudaStreamSynchronize(t->stream));
     }
     return SCLF_OK;

@@ -228,9 +228,38 @@ def test_inject_call_save_load_and_invalid_input(gpu_lib):
     assert t.status()["pending_injection"] == st["pending_injection"]
     with pytest.raises(B.SclfError):
         t.load_particles(np.array([1.0], np.float32), np.array([np.inf], np.float32))
+    assert t.status()["n_particles"] == 0       # a rejected load leaves no particles
+    with pytest.raises(B.SclfError):
+        t.load_particles(np.array([1.0, 1024.0], np.float32), np.zeros(2, np.float32))
     with pytest.raises(B.SclfError):
         t.add_particles([8.0], [0.0])        # z = L is outside the tube
     t.close()
+
+
+def test_save_with_holes_compacts_and_keeps_id_order(gpu_lib):
+    """Saving a tube whose slots hold holes (particles that left) returns the
+    live particles in ID order (a device-side compaction), the same as
+    read_particles and the oracle; loading them back resumes identically."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    kw["compact_interval"] = 100000                 # no compaction check during the run
+    t, o = pair(gpu_lib, kw, "f32", "fixed")
+    z, u = synth.prefilled_beam(30000, 8.0 - 8.0 / 1024, 5.0, seed=2)
+    t.add_particles(z, u)
+    o.add_particles(z, u)
+    for _ in range(150):
+        t.step()
+        o.step()
+    st = t.status()
+    assert st["n_slots"] > st["n_particles"]         # holes are there
+    xi, uu, ids = t.save_particles()
+    assert np.array_equal(ids, o.ids) and np.array_equal(xi, o.xi) and np.array_equal(uu, o.u)
+    assert t.status()["n_slots"] == t.status()["n_particles"]
+    t2 = B.Tube(B.default_params(**kw))
+    t2.load_particles(xi, uu, ids)
+    t2.solve_fields()
+    assert t2.status()["total_injected"] == int(ids.max()) + 1
+    t.close()
+    t2.close()
 
 
 def test_full_size_gr_step_against_oracle_on_all_particles(gpu_lib):
