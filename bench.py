@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--sort-interval", type=int, default=0,
+                    help="gr1e8/large: re-sort the slots by cell (tube_sort) once before the "
+                         "run and every this many steps (0: never)")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="adjoint workload: no event-record nodes (for ncu runs, where "
                          "each event node is very slow); no per-kernel times or roofline")
@@ -165,7 +168,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_tube(B, workloads, workload, n, acc, order, seed):
+def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0):
     """Create the workload's tube and fill it with its seeded synthetic state.
     Returns (tube, params, derived, sample_z, sample_u, stride): every
     stride-th particle of the state, for the CPU baseline."""
@@ -174,6 +177,7 @@ def build_tube(B, workloads, workload, n, acc, order, seed):
         kw = workloads.large_tube(n_particles=n)
     else:
         kw = workloads.gr_tube(n_particles=n, accumulate=acc)
+    kw["sort_interval"] = sort_interval
     t = B.Tube(B.default_params(**kw))
     d = t.derived
     # frame-dragging ramp for the initial momenta: gamma_far = Lambda0^2 kappa cos i
@@ -670,8 +674,14 @@ def main():
     large = args.workload == "large"
     n = int(args.particles or (2 ** 30 if large else 1e8))
     t, kw, d, zs, us, stride = build_tube(B, workloads, args.workload, n, acc, args.order,
-                                          seed=rank_seed(rank))
+                                          seed=rank_seed(rank), sort_interval=args.sort_interval)
     t.solve_fields()
+    sort_ms = None
+    if args.sort_interval > 0:                       # a stable re-sort by cell up front
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        t.sort()
+        sort_ms = 1e3 * (time.perf_counter() - w0)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -775,6 +785,9 @@ def main():
                    "particles_per_gpu": n, "Nz": kw["Nz"], "Lambda0": d["Lambda0"],
                    "dt_R_over_c": d["dt"], "order": args.order,
                    "current_accumulator": args.accumulate,
+                   "sort_by_cell": ({"interval_steps": args.sort_interval,
+                                     "first_sort_ms_wall": sort_ms}
+                                    if args.sort_interval > 0 else None),
                    "l2": "inputs larger than L2 (particle state %.0f MB per GPU)" % (8 * n / 1e6),
                    "parallelism": "independent tube per GPU" if ws > 1 else "single tube"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -126,6 +126,10 @@ typedef struct tube_params {
                               the tube (f(1) = the value at node 0)           */
     const double* gr_H;    /* host, Nz+1 values of H(eta) at the nodes, or NULL
                               for H = 1; read by tube_create, kept by the tube */
+    int32_t sort_interval; /* > 0: tube_run re-sorts the slots by position
+                              (tube_sort) every sort_interval steps or more
+                              (between graph chunks); 0: never           */
+    int32_t reserved0;
 } tube_params;
 
 /* Code-unit quantities derived from tube_params (all FP64). */
@@ -231,13 +235,15 @@ int tube_run(tube_t t, int64_t nsteps);
 int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi,
                      double* J, double* rho);
 
-/* Copy live particles in ID order to host arrays of capacity cap: z in R,
+/* Copy live particles in slot order (ID order unless the tube was re-sorted
+ * by cell: tube_sort, sort_interval) to host arrays of capacity cap: z in R,
  * u = gamma beta, id (any of z, u, id may be NULL). *n receives the number
  * of live particles; min(cap, *n) are written. Synchronises. */
 int tube_read_particles(tube_t t, int64_t cap, int64_t* n, double* z,
                         double* u, int64_t* id);
 
-/* Raw particle state in the tube's precision, live particles only, ID order:
+/* Raw particle state in the tube's precision, live particles only, slot
+ * order (as tube_read_particles):
  * positions xi = z / dz as float (SCLF_FP32) or double (SCLF_FP64), or as
  * int32 X = xi / pos_unit (SCLF_FIX32); u as float (FP32, FIX32) or double.
  * Host buffers of capacity cap (pinned memory makes the copies fastest);
@@ -275,6 +281,18 @@ int tube_check(tube_t t);
 /* Compact the particle slots now, whatever the number of holes (removes
  * holes, keeps ID order). Async. */
 int tube_compact(tube_t t);
+
+/* Re-sort the particle slots by position, stably (particles in one of 256
+ * bins per cell keep their slot order; fewer bins above 2^23 cells), and
+ * drop the holes: a radix sort of (position bin, slot) pairs with 8-bit
+ * digits and a gather of positions, momenta and IDs. The results
+ * of every later step are unchanged (the current and the base-cell weight
+ * are exact integer sums, independent of the order); the particle kernel
+ * gets back its per-cell runs. Afterwards the slot order, and so the order
+ * of tube_read_particles / tube_save_particles, is cell order rather than ID
+ * order. The first call allocates scratch of about 24 bytes per slot of
+ * capacity (plus 8 with IDs). Synchronises. */
+int tube_sort(tube_t t);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing of steps; enabling
  * clears the accumulated numbers. Graph replays then carry event-record

@@ -39,6 +39,7 @@ class TubeParams(C.Structure):
         ("compact_interval", C.c_int32), ("use_graphs", C.c_int32),
         ("gr_variant", C.c_int32), ("gr_alpha", C.c_int32),
         ("gr_f", C.POINTER(C.c_double)), ("gr_H", C.POINTER(C.c_double)),
+        ("sort_interval", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -89,6 +90,7 @@ SIGNATURES = {
     "tube_status": (_i32, [_vp, C.POINTER(TubeStats)]),
     "tube_check": (_i32, [_vp]),
     "tube_compact": (_i32, [_vp]),
+    "tube_sort": (_i32, [_vp]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
     "batch_create": (_i32, [C.c_int32, C.POINTER(TubeParams), _vp, C.POINTER(_vp)]),
@@ -256,6 +258,10 @@ class Tube:
 
     def compact(self):
         _check(self.lib.tube_compact(self.h), "tube_compact")
+
+    def sort(self):
+        """Re-sort the slots by cell (stable), dropping holes."""
+        _check(self.lib.tube_sort(self.h), "tube_sort")
 
     # -- particles -------------------------------------------------------
     def add_particles(self, z, u):

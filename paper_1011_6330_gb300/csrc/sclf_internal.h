@@ -304,6 +304,15 @@ cudaError_t launch_seed_gamma(const Pos* xi, const Mom* u, const DevState* st, M
 cudaError_t launch_seed_ez(const double* ez, int nz, double dz, const double* values,
                            double* lez, cudaStream_t s);
 
+// Stable sort of n slots by cell (sort.cu): keys = cell (holes: nz, last),
+// LSD radix with 8-bit digits; xo/uo/io receive the permuted slots. scale
+// converts a stored position to cells (2^-fb for SCLF_FIX32, else 1).
+long long sort_scratch_bytes(long long n);
+template <class Pos, class Mom>
+cudaError_t launch_sort_by_cell(const Pos* xi, const Mom* u, const long long* ids, long long n,
+                                int nz, double scale, void* scratch, Pos* xo, Mom* uo,
+                                long long* io, cudaStream_t s);
+
 // Host set-up (setup.cpp).
 int derive(const tube_params* p, tube_derived* d);
 int build_rho_gj(const tube_params* p, const tube_derived* d, double* rho);

@@ -505,6 +505,7 @@ int tube_destroy(tube_t t) {
         cudaStreamDestroy(t->gstream);
     }
     if (t->owns_ws && t->ws) cudaFree(t->ws);
+    if (t->sort_ws) cudaFree(t->sort_ws);
     delete t;
     return SCLF_OK;
 }
@@ -566,6 +567,10 @@ int tube_run(tube_t t, int64_t nsteps) {
     if (!t || nsteps < 0) return SCLF_EINVAL;
     if (t->owned) return SCLF_ESTATE;
     while (nsteps > 0) {
+        if (t->p.sort_interval > 0 && t->steps_since_sort >= t->p.sort_interval) {
+            const int rc = tube_sort(t);
+            if (rc) return rc;
+        }
         if (t->p.use_graphs && (t->host_step & 1) == 0 &&
             t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
             int rc;
@@ -577,12 +582,64 @@ int tube_run(tube_t t, int64_t nsteps) {
             }
             if (rc) return rc;
             nsteps -= t->chunk_steps;
+            t->steps_since_sort += t->chunk_steps;
             continue;
         }
         const int rc = one_step(t);
         if (rc) return rc;
         nsteps -= 1;
+        t->steps_since_sort += 1;
     }
+    return SCLF_OK;
+}
+
+int tube_sort(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    const int64_t n = h.n_slots;
+    t->steps_since_sort = 0;
+    if (n == 0) return SCLF_OK;
+    const int64_t rs = fp64(t) ? 8 : 4;
+    const int64_t cap = t->lay.cap_pad;
+    const int64_t sb = (sort_scratch_bytes(cap) + 255) / 256 * 256;
+    const int64_t gb = (cap * rs + 255) / 256 * 256;
+    if (!t->sort_ws) {
+        const int64_t bytes = sb + 2 * gb + (t->ids ? cap * 8 : 0);
+        if (cudaMalloc(&t->sort_ws, bytes) != cudaSuccess) { t->sort_ws = nullptr; return SCLF_ENOMEM; }
+    }
+    void* gx = t->sort_ws + sb;
+    void* gu = t->sort_ws + sb + gb;
+    long long* gi = t->ids ? reinterpret_cast<long long*>(t->sort_ws + sb + 2 * gb) : nullptr;
+    const int nz = static_cast<int>(t->p.Nz);
+    cudaError_t e;
+    if (fp64(t))
+        e = launch_sort_by_cell<double, double>(static_cast<const double*>(t->xi),
+                                                static_cast<const double*>(t->u), t->ids, n, nz,
+                                                1.0, t->sort_ws, static_cast<double*>(gx),
+                                                static_cast<double*>(gu), gi, t->stream);
+    else if (fix32(t))
+        e = launch_sort_by_cell<int, float>(static_cast<const int*>(t->xi),
+                                            static_cast<const float*>(t->u), t->ids, n, nz,
+                                            std::ldexp(1.0, -t->fb), t->sort_ws,
+                                            static_cast<int*>(gx), static_cast<float*>(gu), gi,
+                                            t->stream);
+    else
+        e = launch_sort_by_cell<float, float>(static_cast<const float*>(t->xi),
+                                              static_cast<const float*>(t->u), t->ids, n, nz,
+                                              1.0, t->sort_ws, static_cast<float*>(gx),
+                                              static_cast<float*>(gu), gi, t->stream);
+    CK(e);
+    // the live particles now fill slots [0, n_live) in cell order; holes drop out
+    const int64_t live = h.n_live;
+    CK(cudaMemcpyAsync(t->xi, gx, live * rs, cudaMemcpyDeviceToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->u, gu, live * rs, cudaMemcpyDeviceToDevice, t->stream));
+    if (gi) CK(cudaMemcpyAsync(t->ids, gi, live * 8, cudaMemcpyDeviceToDevice, t->stream));
+    CK(cudaMemcpyAsync(&t->st->n_slots, &live, sizeof(long long), cudaMemcpyHostToDevice,
+                       t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    t->steps_since_compact = 0;
     return SCLF_OK;
 }
 

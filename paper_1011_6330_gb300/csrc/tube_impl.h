@@ -70,6 +70,8 @@ struct sclf_tube {
     int ev_next = 0;
     tube_timing acc{};
     unsigned long long slots_base = 0;
+    char* sort_ws = nullptr;           // scratch of tube_sort (allocated on first use)
+    int steps_since_sort = 0;
     bool owned = false;                // stepped by a batch or an adjoint driver,
                                        // not by tube_step / tube_run
 };
