@@ -54,6 +54,9 @@ def parse():
                          "gradients of a 2000-step run of a P = 0.3 s tube, Nz = 16384, "
                          "1e6 FP32 particles")
     ap.add_argument("--particles", type=float, default=None)
+    ap.add_argument("--nz", type=int, default=None,
+                    help="gr1e8/large: grid cells (default 65536 / 2^20), e.g. for a smaller "
+                         "profiling case with the same particles per cell")
     ap.add_argument("--order", choices=["descending", "shuffled"], default="descending")
     ap.add_argument("--accumulate", choices=["fixed64", "fp64"], default="fixed64")
     ap.add_argument("--no-e2e", action="store_true")
@@ -168,15 +171,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0):
+def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=None):
     """Create the workload's tube and fill it with its seeded synthetic state.
     Returns (tube, params, derived, sample_z, sample_u, stride): every
     stride-th particle of the state, for the CPU baseline."""
     from paper_1011_6330_gb300 import synth
     if workload == "large":
-        kw = workloads.large_tube(n_particles=n)
+        kw = workloads.large_tube(n_particles=n, **({"Nz": nz} if nz else {}))
     else:
-        kw = workloads.gr_tube(n_particles=n, accumulate=acc)
+        kw = workloads.gr_tube(n_particles=n, accumulate=acc, **({"Nz": nz} if nz else {}))
     kw["sort_interval"] = sort_interval
     t = B.Tube(B.default_params(**kw))
     d = t.derived
@@ -674,7 +677,8 @@ def main():
     large = args.workload == "large"
     n = int(args.particles or (2 ** 30 if large else 1e8))
     t, kw, d, zs, us, stride = build_tube(B, workloads, args.workload, n, acc, args.order,
-                                          seed=rank_seed(rank), sort_interval=args.sort_interval)
+                                          seed=rank_seed(rank), sort_interval=args.sort_interval,
+                                          nz=args.nz)
     t.solve_fields()
     sort_ms = None
     if args.sort_interval > 0:                       # a stable re-sort by cell up front
@@ -734,10 +738,12 @@ def main():
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e and not large:
+    if not args.no_e2e:
         xi_h, u_h, _ = t.save_particles()
-        pin_x = torch.empty(xi_h.size, dtype=torch.float32, pin_memory=True)
-        pin_u = torch.empty(u_h.size, dtype=torch.float32, pin_memory=True)
+        tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64,
+               np.dtype(np.int32): torch.int32}
+        pin_x = torch.empty(xi_h.size, dtype=tdt[xi_h.dtype], pin_memory=True)
+        pin_u = torch.empty(u_h.size, dtype=tdt[u_h.dtype], pin_memory=True)
         pin_x.numpy()[:] = xi_h
         pin_u.numpy()[:] = u_h
         del xi_h, u_h
@@ -763,10 +769,11 @@ def main():
         torch.cuda.synchronize()
         el_e2e = time.perf_counter() - h0
         n_all, el_e2e = combine_ranks(n_e2e, el_e2e, device="cuda")
-        state_bytes = 8 * pin_x.numel()
+        state_bytes = pin_x.numel() * pin_x.element_size() + pin_u.numel() * pin_u.element_size()
         e2e = {"value": n_all / el_e2e, "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / ksteps,
-               "d2h_bytes_per_step": (8 * min(cap, nout.value) + ksteps * 88) / ksteps,
+               "d2h_bytes_per_step": (state_bytes * min(cap, nout.value) / max(cap, 1)
+                                      + ksteps * 88) / ksteps,
                "path": "tube_load_particles(pinned) + K x (tube_status, tube_step) + "
                        "tube_save_particles(pinned)", "rc": int(rc)}
 
