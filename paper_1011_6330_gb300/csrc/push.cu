@@ -15,6 +15,22 @@ namespace {
 template <class Real> struct PairOf { using T = float2; };
 template <> struct PairOf<double> { using T = double2; };
 
+// Current fraction of a particle that stays in cell j >= 1 (the common path):
+// F_j(x1) - F_j(x0). For float32 positions x0, x1 lie in one binade (cells
+// never straddle a power of two for j >= 1), so x1 - x0 is exact, and it is a
+// multiple of 2^-23: (x1 - x0) 2^31 is an exact float32 integer and one 32-bit
+// conversion gives the same 2^-32-unit difference as quantising both F first.
+template <int kAcc>
+__device__ __forceinline__ typename AccType<kAcc>::T common_frac(float x0, float x1, float jf) {
+    if constexpr (kAcc == kAccFixed)
+        return static_cast<long long>(__float2int_rn((x1 - x0) * 2147483648.0f)) * 2;
+    else return frac_acc_in_cell<kAcc>(x0, x1, jf);
+}
+template <int kAcc>
+__device__ __forceinline__ typename AccType<kAcc>::T common_frac(double x0, double x1, double jf) {
+    return frac_acc_in_cell<kAcc>(x0, x1, jf);
+}
+
 // What one tile of one tube needs.
 template <class Real, class AccT>
 struct TileCtx {
@@ -103,7 +119,7 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
         const bool first = x0f == rkey;
         const bool common = lv & (x1f == x0f) & (x1 >= Real(1)) & (x1 < nzf) &
                             (first | (kTwoRuns & (x0f == rkey2)));
-        const AccT q0 = frac_acc_in_cell<kAcc>(xx, x1, x0f);
+        const AccT q0 = common_frac<kAcc>(xx, x1, x0f);
         ra += (common & first) ? q0 : AccT(0);
         if constexpr (kTwoRuns) rb += (common & !first) ? q0 : AccT(0);
         if (lv & !common) {
@@ -114,7 +130,7 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
                 us[k] = Real(0);
             } else {
                 const int c0 = static_cast<int>(x0f);
-                AccT qa = q0;
+                AccT qa = frac_acc_in_cell<kAcc>(xx, x1, x0f);
                 if (x1f != x0f) {
                     qa = frac_acc<kAcc>(xx, x1, c0);
                     const int c1 = static_cast<int>(x1f);
