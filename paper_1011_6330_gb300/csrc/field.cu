@@ -9,29 +9,51 @@ namespace {
 // ---------------------------------------------------------------------------
 // (a6): the field kernel, one thread per cell
 // ---------------------------------------------------------------------------
-// Cell j of one tube (0 <= j < Nz); cell 0 also commits the tube's step.
+// The inputs of cell j: its accumulated current, E_z, B_phi at j and its
+// neighbours, E_r at nodes j and j + 1. Loading them apart from the update
+// lets a thread have several cells' loads in flight.
+template <class AccT>
+struct CellIn {
+    AccT q;
+    double ez, bj, bm, bp, er0, er1;
+};
+
 template <class Real, int kAcc>
-__device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
+__device__ __forceinline__ void field_load(const FieldArgs<Real>& a, int j,
+                                           CellIn<typename AccType<kAcc>::T>& in) {
     using AccT = typename AccType<kAcc>::T;
     const int nz = a.c.nz;
-    AccT* jacc = static_cast<AccT*>(a.jacc);
-    const AccT q = jacc[j];
-    jacc[j] = AccT(0);
+    in.q = static_cast<const AccT*>(a.jacc)[j];
+    in.bj = a.b_in[j];
+    in.bm = j >= 1 ? a.b_in[j - 1] : 0.0;
+    in.bp = j + 1 < nz ? a.b_in[j + 1] : 0.0;
+    in.ez = a.ez[j];
+    in.er0 = a.er_in[j];
+    in.er1 = a.er_in[j + 1];
+}
+
+// Cell j of one tube (0 <= j < Nz) from its loaded inputs; cell 0 also
+// commits the tube's step.
+template <class Real, int kAcc>
+__device__ __forceinline__ void field_store(const FieldArgs<Real>& a, int j,
+                                            const CellIn<typename AccType<kAcc>::T>& in) {
+    using AccT = typename AccType<kAcc>::T;
+    const int nz = a.c.nz;
+    static_cast<AccT*>(a.jacc)[j] = AccT(0);
     double ssum;
-    if constexpr (kAcc == kAccFixed) ssum = double(q) * kFixedInv;
-    else ssum = q;
+    if constexpr (kAcc == kAccFixed) ssum = double(in.q) * kFixedInv;
+    else ssum = in.q;
     const double J = a.c.s_over_dt * ssum;                 // J^{n+1/2}_{j+1/2}
     a.jlast[j] = J;
 
-    const double bj = a.b_in[j];
-    const double ez1 = a.ez[j] + a.c.dt * bj - a.c.fourpi_dt * J;
+    const double bj = in.bj;
+    const double ez1 = in.ez + a.c.dt * bj - a.c.fourpi_dt * J;
     a.ez[j] = ez1;
     // E_r at node j (node 0 stays: phi = 0 on the conducting base) ...
-    const double erj = (j == 0) ? a.er_in[0]
-                                : a.er_in[j] - a.c.cdt * (bj - a.b_in[j - 1]);
+    const double erj = (j == 0) ? in.er0 : in.er0 - a.c.cdt * (bj - in.bm);
     // ... and at node j + 1, with the ghost B_{Nz+1/2} = B_{Nz-1/2} on top
-    const double bjp = (j + 1 < nz) ? a.b_in[j + 1] : bj;
-    const double erj1 = a.er_in[j + 1] - a.c.cdt * (bjp - bj);
+    const double bjp = (j + 1 < nz) ? in.bp : bj;
+    const double erj1 = in.er1 - a.c.cdt * (bjp - bj);
     a.er_out[j] = erj;
     if (j == nz - 1) a.er_out[nz] = erj1;
     a.b_out[j] = bj - a.c.cdt * (erj1 - erj) - a.c.dt * ez1;
@@ -69,19 +91,26 @@ __device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
 }
 
 template <class Real, int kAcc>
+__device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
+    CellIn<typename AccType<kAcc>::T> in;
+    field_load<Real, kAcc>(a, j, in);
+    field_store<Real, kAcc>(a, j, in);
+}
+
+template <class Real, int kAcc>
 __global__ void __launch_bounds__(256) field_kernel(const FieldArgs<Real> a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.c.nz) return;
     field_cell<Real, kAcc>(a, j);
 }
 
-// All tubes of a batch: one thread per cell of the batch's cell space.
-__global__ void __launch_bounds__(256)
-batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ cell_tube,
-                   int n_cells, int parity) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_cells) return;
-    const BatchTube& d = tubes[cell_tube[g]];
+// All tubes of a batch: kBatchCells cells per thread of the batch's cell
+// space, strided by the block size so that each round is coalesced. The
+// batch's grids are larger than what stays in L2 next to the particles, so a
+// thread issues all its cells' loads before it updates them.
+constexpr int kBatchCells = 2;
+
+__device__ __forceinline__ FieldArgs<float> batch_field_args(const BatchTube& d, int parity) {
     FieldArgs<float> a;
     a.st = d.st;
     a.ez = d.ez;
@@ -94,7 +123,40 @@ batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ 
     a.ez2 = d.ez2;
     a.evlog = nullptr;
     a.c = d.fc;
-    field_cell<float, kAccFixed>(a, g - d.cell0);
+    return a;
+}
+
+__global__ void __launch_bounds__(256)
+batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ cell_tube,
+                   int n_cells, int parity) {
+    const long long base = static_cast<long long>(blockIdx.x) * blockDim.x * kBatchCells +
+                           threadIdx.x;
+    int ti[kBatchCells];
+#pragma unroll
+    for (int k = 0; k < kBatchCells; ++k) {
+        const long long g = base + static_cast<long long>(k) * blockDim.x;
+        ti[k] = g < n_cells ? cell_tube[g] : -1;
+    }
+    // cells are numbered tube by tube, so equal first and last tubes mean
+    // all of this thread's cells belong to one tube
+    if (ti[kBatchCells - 1] >= 0 && ti[0] == ti[kBatchCells - 1]) {
+        const BatchTube& d = tubes[ti[0]];
+        const FieldArgs<float> a = batch_field_args(d, parity);
+        CellIn<long long> in[kBatchCells];
+#pragma unroll
+        for (int k = 0; k < kBatchCells; ++k)
+            field_load<float, kAccFixed>(a, static_cast<int>(base + k * blockDim.x) - d.cell0, in[k]);
+#pragma unroll
+        for (int k = 0; k < kBatchCells; ++k)
+            field_store<float, kAccFixed>(a, static_cast<int>(base + k * blockDim.x) - d.cell0, in[k]);
+    } else {
+        for (int k = 0; k < kBatchCells; ++k) {
+            if (ti[k] < 0) continue;
+            const BatchTube& d = tubes[ti[k]];
+            field_cell<float, kAccFixed>(batch_field_args(d, parity),
+                                         static_cast<int>(base + k * blockDim.x) - d.cell0);
+        }
+    }
 }
 
 }  // namespace
@@ -109,7 +171,9 @@ cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate, cudaStream_t 
 
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
                                int parity, cudaStream_t s) {
-    batch_field_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(tubes, cell_tube, n_cells, parity);
+    const int per_block = 256 * kBatchCells;
+    batch_field_kernel<<<(n_cells + per_block - 1) / per_block, 256, 0, s>>>(tubes, cell_tube,
+                                                                            n_cells, parity);
     return cudaGetLastError();
 }
 
