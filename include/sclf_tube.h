@@ -278,6 +278,25 @@ int tube_status(tube_t t, tube_stats* out);
 /* SCLF_OK, or the error code of the most severe sticky flag. Synchronises. */
 int tube_check(tube_t t);
 
+/* Diagnostics of the current state (code units, per unit cross-section):
+ * the live particles' largest and mean gamma and kinetic energy
+ * |s| sum (gamma - 1) (a deterministic device reduction), the field energy
+ * sum (E_z^2 + B_phi^2) dz / 8 pi over the cells plus sum E_r^2 dz / 8 pi over
+ * the nodes (half weight at the two ends), and the residual of Gauss's law
+ * (Eq. 2 with d/dr -> 1/R) on the interior nodes,
+ * G_j = (E_{j+1/2} - E_{j-1/2}) / dz + E_r,j - 4 pi (rho_j - rho_GJ,j), with the
+ * scale max 4 pi |rho_j - rho_GJ,j| to compare it with. Synchronises. */
+typedef struct tube_diag {
+    int64_t n_particles;
+    double gamma_max;
+    double gamma_mean;
+    double kinetic;
+    double field_energy;
+    double gauss_max;
+    double gauss_scale;
+} tube_diag;
+int tube_diagnostics(tube_t t, tube_diag* out);
+
 /* Compact the particle slots now, whatever the number of holes (removes
  * holes, keeps ID order). Async. */
 int tube_compact(tube_t t);

@@ -58,6 +58,11 @@ class TubeStats(C.Structure):
     ]
 
 
+class TubeDiag(C.Structure):
+    _fields_ = [("n_particles", C.c_int64)] + [(n, C.c_double) for n in (
+        "gamma_max", "gamma_mean", "kinetic", "field_energy", "gauss_max", "gauss_scale")]
+
+
 class TubeTiming(C.Structure):
     _fields_ = [
         ("push_ms", C.c_double), ("field_ms", C.c_double), ("compact_ms", C.c_double),
@@ -89,6 +94,7 @@ SIGNATURES = {
     "tube_solve_fields": (_i32, [_vp]),
     "tube_status": (_i32, [_vp, C.POINTER(TubeStats)]),
     "tube_check": (_i32, [_vp]),
+    "tube_diagnostics": (_i32, [_vp, C.POINTER(TubeDiag)]),
     "tube_compact": (_i32, [_vp]),
     "tube_sort": (_i32, [_vp]),
     "tube_set_timing": (_i32, [_vp, _i32]),
@@ -329,6 +335,11 @@ class Tube:
 
     def check(self):
         return self.lib.tube_check(self.h)
+
+    def diagnostics(self):
+        d = TubeDiag()
+        _check(self.lib.tube_diagnostics(self.h, C.byref(d)), "tube_diagnostics")
+        return {n: getattr(d, n) for n, _ in TubeDiag._fields_}
 
     def set_timing(self, enable):
         _check(self.lib.tube_set_timing(self.h, 1 if enable else 0), "tube_set_timing")

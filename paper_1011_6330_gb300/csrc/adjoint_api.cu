@@ -605,6 +605,7 @@ int adjoint_set_injections(adjoint_t a, const int64_t* n_inj) {
 }
 
 int adjoint_forward(adjoint_t a, double* values) {
+    NvtxRange nvtx_range("adjoint_forward");
     if (!a) return SCLF_EINVAL;
     CK(cudaStreamSynchronize(a->t->stream));
     if (fix32(a->t)) return run_forward<int, float>(a, values);
@@ -626,6 +627,7 @@ int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_s
 }
 
 int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s) {
+    NvtxRange nvtx_range("adjoint_backward");
     if (!a || (objective != SCLF_OBJ_GAMMA && objective != SCLF_OBJ_EZ)) return SCLF_EINVAL;
     if (!a->forward_done) return SCLF_ESTATE;
     if (fix32(a->t)) return run_backward<int, float>(a, objective, d_rho_gj, d_s);

@@ -108,6 +108,59 @@ __global__ void ez_table_kernel(const double* ez, Real* ez2, int nz) {
     ez2[2 * m + 1] = static_cast<Real>(ez[hi]);
 }
 
+// Per block over the live slots: count, sum of gamma, max gamma (fixed grid
+// and a fixed-order finish, so the result does not depend on timing).
+template <class Pos, class Mom>
+__global__ void __launch_bounds__(256) particle_diag_kernel(const Pos* xi, const Mom* u,
+                                                            long long n, double* part) {
+    __shared__ double s_sum[8], s_max[8], s_cnt[8];
+    double cnt = 0.0, sum = 0.0, mx = 0.0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (xi[i] >= Pos(0)) {
+            const double v = static_cast<double>(u[i]);
+            const double g = sqrt(1.0 + v * v);
+            cnt += 1.0;
+            sum += g;
+            mx = g > mx ? g : mx;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        cnt += __shfl_xor_sync(kFull, cnt, off);
+        sum += __shfl_xor_sync(kFull, sum, off);
+        const double o = __shfl_xor_sync(kFull, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_cnt[w] = cnt; s_sum[w] = sum; s_max[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c = 0.0, su = 0.0, m = 0.0;
+        for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
+            c += s_cnt[k];
+            su += s_sum[k];
+            m = s_max[k] > m ? s_max[k] : m;
+        }
+        part[3 * blockIdx.x] = c;
+        part[3 * blockIdx.x + 1] = su;
+        part[3 * blockIdx.x + 2] = m;
+    }
+}
+
+__global__ void particle_diag_finish(const double* part, int nblocks, double* out) {
+    if (threadIdx.x != 0) return;
+    double c = 0.0, su = 0.0, m = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        c += part[3 * b];
+        su += part[3 * b + 1];
+        m = part[3 * b + 2] > m ? part[3 * b + 2] : m;
+    }
+    out[0] = c;
+    out[1] = su;
+    out[2] = m;
+}
+
 int grid_for(long long n, int block, int cap) {
     long long g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -137,6 +190,14 @@ template <class Real>
 cudaError_t launch_base_weight(DevState* st, const Real* xi, long long n_slots, cudaStream_t s) {
     if (n_slots <= 0) return cudaSuccess;
     base_weight_kernel<Real><<<grid_for(n_slots, 256, 4096), 256, 0, s>>>(st, xi, n_slots);
+    return cudaGetLastError();
+}
+
+template <class Pos, class Mom>
+cudaError_t launch_particle_diag(const Pos* xi, const Mom* u, long long n, double* part,
+                                 double* out, cudaStream_t s) {
+    particle_diag_kernel<Pos, Mom><<<kDiagBlocks, 256, 0, s>>>(xi, u, n, part);
+    particle_diag_finish<<<1, 32, 0, s>>>(part, kDiagBlocks, out);
     return cudaGetLastError();
 }
 
@@ -174,6 +235,12 @@ template cudaError_t launch_append<double, double>(DevState*, double*, double*, 
                                                   long long, long long, bool, cudaStream_t);
 template cudaError_t launch_append<int, float>(DevState*, int*, float*, long long*, long long,
                                               long long, bool, cudaStream_t);
+template cudaError_t launch_particle_diag<float, float>(const float*, const float*, long long,
+                                                       double*, double*, cudaStream_t);
+template cudaError_t launch_particle_diag<double, double>(const double*, const double*, long long,
+                                                         double*, double*, cudaStream_t);
+template cudaError_t launch_particle_diag<int, float>(const int*, const float*, long long,
+                                                     double*, double*, cudaStream_t);
 template cudaError_t launch_validate<float, float>(DevState*, const float*, const float*,
                                                   const long long*, long long, double, cudaStream_t);
 template cudaError_t launch_validate<double, double>(DevState*, const double*, const double*,

@@ -271,6 +271,12 @@ cudaError_t launch_base_weight_fix32(DevState* st, const int* X, long long n_slo
 template <class Pos, class Mom>
 cudaError_t launch_validate(DevState* st, const Pos* xi, const Mom* u, const long long* ids,
                             long long n, double top, cudaStream_t s);
+// Over the live slots [0, n): out[0] = count, out[1] = sum of gamma,
+// out[2] = max gamma (part: 3 * kDiagBlocks doubles of scratch).
+constexpr int kDiagBlocks = 128;
+template <class Pos, class Mom>
+cudaError_t launch_particle_diag(const Pos* xi, const Mom* u, long long n, double* part,
+                                 double* out, cudaStream_t s);
 cudaError_t launch_finish_append(DevState* st, const double* ez,
                                  long long n_added, FieldConsts c,
                                  cudaStream_t s);

@@ -38,6 +38,7 @@ TubeLayout plan(const tube_params* p) {
     l.off_jlast = take(nz * 8);
     l.off_ez2 = take(2 * (nz + 1) * rs);
     l.off_rho = take((nz + 1) * 8);
+    l.off_diag = take((3 * kDiagBlocks + 4) * 8);
     l.total = o;
     return l;
 }
@@ -430,6 +431,7 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     t->jlast = reinterpret_cast<double*>(t->ws + l.off_jlast);
     t->ez2 = t->ws + l.off_ez2;
     t->rho_acc = reinterpret_cast<double*>(t->ws + l.off_rho);
+    t->diag = reinterpret_cast<double*>(t->ws + l.off_diag);
 
     // (a7) rho_GJ, Eq. 4 and the initial fields
     const int64_t nz = p->Nz;
@@ -558,12 +560,14 @@ int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
 }
 
 int tube_step(tube_t t) {
+    NvtxRange nvtx_range("tube_step");
     if (!t) return SCLF_EINVAL;
     if (t->owned) return SCLF_ESTATE;
     return one_step(t);
 }
 
 int tube_run(tube_t t, int64_t nsteps) {
+    NvtxRange nvtx_range("tube_run");
     if (!t || nsteps < 0) return SCLF_EINVAL;
     if (t->owned) return SCLF_ESTATE;
     while (nsteps > 0) {
@@ -594,6 +598,7 @@ int tube_run(tube_t t, int64_t nsteps) {
 }
 
 int tube_sort(tube_t t) {
+    NvtxRange nvtx_range("tube_sort");
     if (!t) return SCLF_EINVAL;
     DevState h;
     int rc = read_state(t, &h);
@@ -674,6 +679,7 @@ int tube_read_fields(tube_t t, double* Ez, double* Er, double* Bphi, double* J, 
 // double, through host staging).
 static int read_raw(tube_t t, int64_t cap, int64_t* n, void* xo, void* uo, int64_t* ido,
                     bool convert) {
+    NvtxRange nvtx_range("tube_read_particles");
     CK(enqueue_compact(t, t->stream, 1));
     t->steps_since_compact = 0;
     DevState h;
@@ -720,6 +726,7 @@ int tube_save_particles(tube_t t, int64_t cap, int64_t* n, void* xi, void* u, in
 }
 
 int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, const int64_t* id) {
+    NvtxRange nvtx_range("tube_load_particles");
     if (!t || n < 0 || n > t->p.capacity || (n > 0 && (!xi || !u))) return SCLF_EINVAL;
     if (id && !t->ids) return SCLF_EINVAL;
     // the counters start from an empty tube; the raw arrays go straight to
@@ -779,6 +786,7 @@ int tube_load_particles(tube_t t, int64_t n, const void* xi, const void* u, cons
 }
 
 int tube_solve_fields(tube_t t) {
+    NvtxRange nvtx_range("tube_solve_fields");
     if (!t) return SCLF_EINVAL;
     const int64_t nz = t->p.Nz;
     std::vector<double> rho(nz + 1), src(nz + 1), phi(nz + 1), ez0(nz);
@@ -800,6 +808,57 @@ int tube_solve_fields(tube_t t) {
     CK(do_base_weight(t, 0, h.n_slots));
     CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
     CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+int tube_diagnostics(tube_t t, tube_diag* out) {
+    if (!t || !out) return SCLF_EINVAL;
+    NvtxRange nvtx_range("tube_diagnostics");
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    double pd[3] = {0.0, 0.0, 0.0};
+    if (h.n_slots > 0) {
+        cudaError_t e;
+        double* part = t->diag;
+        double* res = t->diag + 3 * kDiagBlocks;
+        if (fp64(t))
+            e = launch_particle_diag<double, double>(static_cast<const double*>(t->xi),
+                                                     static_cast<const double*>(t->u), h.n_slots,
+                                                     part, res, t->stream);
+        else if (fix32(t))
+            e = launch_particle_diag<int, float>(static_cast<const int*>(t->xi),
+                                                 static_cast<const float*>(t->u), h.n_slots, part,
+                                                 res, t->stream);
+        else
+            e = launch_particle_diag<float, float>(static_cast<const float*>(t->xi),
+                                                   static_cast<const float*>(t->u), h.n_slots,
+                                                   part, res, t->stream);
+        CK(e);
+        CK(cudaMemcpyAsync(pd, res, sizeof(pd), cudaMemcpyDeviceToHost, t->stream));
+    }
+    const int64_t nz = t->p.Nz;
+    std::vector<double> ez(nz), er(nz + 1), b(nz), rho(nz + 1);
+    rc = tube_read_fields(t, ez.data(), er.data(), b.data(), nullptr, rho.data());
+    if (rc) return rc;
+    const double dz = t->d.dz;
+    double fe = 0.0;
+    for (int64_t j = 0; j < nz; ++j) fe += (ez[j] * ez[j] + b[j] * b[j]) * dz;
+    for (int64_t j = 0; j <= nz; ++j) fe += er[j] * er[j] * dz * ((j == 0 || j == nz) ? 0.5 : 1.0);
+    double gmax = 0.0, gscale = 0.0;
+    for (int64_t j = 1; j < nz; ++j) {
+        const double src = 4.0 * kPi * (rho[j] - t->rho_gj[j]);
+        const double g = (ez[j] - ez[j - 1]) / dz + er[j] - src;
+        gmax = std::fmax(gmax, std::fabs(g));
+        gscale = std::fmax(gscale, std::fabs(src));
+    }
+    out->n_particles = static_cast<int64_t>(pd[0]);
+    out->gamma_max = pd[2];
+    out->gamma_mean = pd[0] > 0.0 ? pd[1] / pd[0] : 0.0;
+    out->kinetic = (pd[1] - pd[0]) * std::fabs(t->d.s);
+    out->field_energy = fe / (8.0 * kPi);
+    out->gauss_max = gmax;
+    out->gauss_scale = gscale;
     return SCLF_OK;
 }
 
@@ -1173,11 +1232,13 @@ int batch_tube(batch_t b, int32_t i, tube_t* out) {
 }
 
 int batch_step(batch_t b) {
+    NvtxRange nvtx_range("batch_step");
     if (!b) return SCLF_EINVAL;
     return batch_one_step(b);
 }
 
 int batch_run(batch_t b, int64_t nsteps) {
+    NvtxRange nvtx_range("batch_run");
     if (!b || nsteps < 0) return SCLF_EINVAL;
     while (nsteps > 0) {
         if (!b->timing && (b->host_step & 1) == 0 && b->steps_since_compact == 0 &&
@@ -1243,6 +1304,7 @@ int batch_set_variant(batch_t b, int32_t variant) {
 }
 
 int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen) {
+    NvtxRange nvtx_range("batch_autotune");
     if (!b || steps <= 0) return SCLF_EINVAL;
     double best = 0.0;
     int best_v = -1;

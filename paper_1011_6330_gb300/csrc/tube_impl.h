@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sclf_internal.h"
 
 namespace sclf {
@@ -15,7 +17,7 @@ struct TubeLayout {
     int64_t cap_pad = 0, ntiles = 0;
     int64_t off_state = 0, off_xi = 0, off_u = 0, off_ids = 0, off_tiles = 0;
     int64_t off_ez = 0, off_er = 0, off_b = 0, off_jacc = 0, off_jlast = 0;
-    int64_t off_ez2 = 0, off_rho = 0, total = 0;
+    int64_t off_ez2 = 0, off_rho = 0, off_diag = 0, total = 0;
 };
 
 }  // namespace sclf
@@ -42,6 +44,7 @@ struct sclf_tube {
     double* jlast = nullptr;
     void* ez2 = nullptr;
     double* rho_acc = nullptr;
+    double* diag = nullptr;            // scratch of tube_diagnostics
     std::vector<double> rho_gj;
     std::vector<double> gr_f, gr_H;     // copies of the caller's Eq. 6 tables (p points here)
     sclf::FieldConsts fc{};
@@ -77,6 +80,15 @@ struct sclf_tube {
 };
 
 namespace sclf {
+
+// An NVTX range over a host entry point (visible to ncu --nvtx and to any
+// timeline profiler; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 inline int cuda_fail(cudaError_t e) {
     if (e == cudaSuccess) return SCLF_OK;

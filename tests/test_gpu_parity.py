@@ -610,3 +610,31 @@ def test_sort_by_cell_changes_no_result(gpu_lib, prec):
     assert np.array_equal(np.sort(ids), np.sort(ia))
     a.close()
     b.close()
+
+
+def test_diagnostics_match_the_oracle(gpu_lib):
+    """tube_diagnostics (gamma max and mean, kinetic and field energy, Gauss
+    residual) against the same quantities from the oracle's state after 150
+    FP64 steps of the flat SCLF tube (to 1e-10: the two FP64 runs start from
+    Eq. 4 solutions that differ in the last bits -- a Thomas sweep and LAPACK's
+    banded solver -- and 150 steps amplify that to ~1e-11); the Gauss residual
+    stays at rounding level (charge conservation of the step)."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FIXED64)
+    t, o = pair(gpu_lib, kw, "f64", "fixed")
+    for _ in range(150):
+        t.step()
+        o.step()
+    dg = t.diagnostics()
+    g = o.gamma()
+    assert dg["n_particles"] == o.xi.size
+    assert abs(dg["gamma_max"] - g.max()) <= 1e-10 * g.max()
+    assert abs(dg["gamma_mean"] - g.mean()) <= 1e-10 * g.mean()
+    assert abs(dg["kinetic"] - abs(o.s) * np.sum(g - 1.0)) <= 1e-10 * abs(o.s) * np.sum(g - 1.0)
+    w = np.ones(o.nz + 1)
+    w[0] = w[-1] = 0.5
+    fe = (np.sum(o.ez ** 2 + o.b ** 2) * o.dz + np.sum(w * o.er ** 2) * o.dz) / (8 * math.pi)
+    assert abs(dg["field_energy"] - fe) <= 1e-10 * fe
+    res = o.gauss_residual()
+    assert dg["gauss_max"] <= 1e-9 * dg["gauss_scale"]
+    assert abs(dg["gauss_max"] - np.max(np.abs(res))) <= 1e-9 * dg["gauss_scale"]
+    t.close()
