@@ -301,6 +301,17 @@ int tube_diagnostics(tube_t t, tube_diag* out);
  * holes, keeps ID order). Async. */
 int tube_compact(tube_t t);
 
+/* Self-test of the failure path of a bounded device-side wait (no paper
+ * counterpart): runs one forced compaction in which the first tile publishes
+ * nothing, so the decoupled look-back of the second tile gives up after 4096
+ * polls, sets SCLF_FLAG_TIMEOUT and the kernel finishes; nothing faults or
+ * hangs and the CUDA context stays usable. Returns SCLF_ETIMEOUT when the
+ * device reported the timeout (the expected result), SCLF_EINVAL when the
+ * tube has at most one tile of slots. The tube's particle slots and counters
+ * are unspecified afterwards and its TIMEOUT flag stays set: use a scratch
+ * tube. Synchronises. */
+int tube_selftest_wait_timeout(tube_t t);
+
 /* Re-sort the particle slots by position, stably (particles in one of 256
  * bins per cell keep their slot order; fewer bins above 2^23 cells), and
  * drop the holes: a radix sort of (position bin, slot) pairs with 8-bit

@@ -97,6 +97,7 @@ SIGNATURES = {
     "tube_diagnostics": (_i32, [_vp, C.POINTER(TubeDiag)]),
     "tube_compact": (_i32, [_vp]),
     "tube_sort": (_i32, [_vp]),
+    "tube_selftest_wait_timeout": (_i32, [_vp]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
     "batch_create": (_i32, [C.c_int32, C.POINTER(TubeParams), _vp, C.POINTER(_vp)]),

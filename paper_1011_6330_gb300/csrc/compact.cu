@@ -9,7 +9,6 @@ namespace {
 // In-place stable compaction (decoupled look-back)
 // ---------------------------------------------------------------------------
 constexpr unsigned kFlagAgg = 1u, kFlagIncl = 2u;
-constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ unsigned long long pack_state(unsigned epoch, unsigned flag,
                                                          unsigned value) {
@@ -53,6 +52,10 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Pos
         __syncthreads();
         const long long tile = s_tile;
         if (tile >= ntiles) break;
+        if (a.withhold_first && tile == 0) {      // self-test: publish nothing for tile 0
+            __syncthreads();
+            continue;
+        }
         const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
         Pos xs[kPPT];
         Mom us[kPPT];
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const CompactArgs<Pos
                     const unsigned long long w = load_acquire(ts + t);
                     const unsigned we = unsigned(w >> 34), wf = unsigned(w >> 32) & 3u;
                     if (we != (epoch & 0x3fffffffu) || wf == 0u) {
-                        if (++spins > kSpinLimit) {
+                        if (++spins > a.spin_limit) {
                             atomicOr(&st->flags, SCLF_FLAG_TIMEOUT);
                             break;
                         }

@@ -150,7 +150,11 @@ struct CompactArgs {
     unsigned long long* tile_state;  // one word per tile
     long long capacity;
     int force;                       // 0: only when holes or capacity call for it
+    int withhold_first;              // self-test: tile 0 publishes nothing, so the
+                                     // look-back of tile 1 must give up
+    long long spin_limit;            // polls of a look-back before it gives up
 };
+constexpr long long kCompactSpinLimit = 1LL << 22;   // x >= 64 ns: about a quarter second
 
 // One tube of a batch, as the batched kernels see it (FP32 particles,
 // fixed-point current).

@@ -55,6 +55,8 @@ template <class Pos, class Mom>
 CompactArgs<Pos, Mom> compact_args(sclf_tube* t, int force) {
     CompactArgs<Pos, Mom> a;
     a.force = force;
+    a.withhold_first = 0;
+    a.spin_limit = kCompactSpinLimit;
     a.st = t->st;
     a.xi = static_cast<Pos*>(t->xi);
     a.u = static_cast<Mom*>(t->u);
@@ -595,6 +597,37 @@ int tube_run(tube_t t, int64_t nsteps) {
         t->steps_since_sort += 1;
     }
     return SCLF_OK;
+}
+
+int tube_selftest_wait_timeout(tube_t t) {
+    if (!t) return SCLF_EINVAL;
+    DevState h;
+    int rc = read_state(t, &h);
+    if (rc) return rc;
+    const int64_t tile = fp64(t) ? Layout<double>::kTile : Layout<float>::kTile;
+    if (h.n_slots <= tile) return SCLF_EINVAL;          // needs a second tile to wait
+    CK(cudaMemsetAsync(&t->st->ticket, 0, sizeof(unsigned int), t->stream));
+    cudaError_t e;
+    if (fix32(t)) {
+        auto a = compact_args<int, float>(t, 1);
+        a.withhold_first = 1;
+        a.spin_limit = 4096;
+        e = launch_compact<int, float>(a, t->compact_grid, t->stream);
+    } else if (fp64(t)) {
+        auto a = compact_args<double, double>(t, 1);
+        a.withhold_first = 1;
+        a.spin_limit = 4096;
+        e = launch_compact<double, double>(a, t->compact_grid, t->stream);
+    } else {
+        auto a = compact_args<float, float>(t, 1);
+        a.withhold_first = 1;
+        a.spin_limit = 4096;
+        e = launch_compact<float, float>(a, t->compact_grid, t->stream);
+    }
+    CK(e);
+    rc = read_state(t, &h);
+    if (rc) return rc;
+    return (h.flags & SCLF_FLAG_TIMEOUT) ? SCLF_ETIMEOUT : SCLF_OK;
 }
 
 int tube_sort(tube_t t) {

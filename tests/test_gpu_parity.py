@@ -638,3 +638,26 @@ def test_diagnostics_match_the_oracle(gpu_lib):
     assert dg["gauss_max"] <= 1e-9 * dg["gauss_scale"]
     assert abs(dg["gauss_max"] - np.max(np.abs(res))) <= 1e-9 * dg["gauss_scale"]
     t.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(gpu_lib):
+    """The compaction look-back's wait is bounded: with the first tile's state
+    withheld (a flag nothing sets) the second tile gives up, the device reports
+    SCLF_ETIMEOUT through the sticky flags, and the CUDA context keeps
+    working -- a fresh tube then steps exactly like the oracle."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    t = B.Tube(B.default_params(**kw))
+    assert t.lib.tube_selftest_wait_timeout(t.h) == -1      # one tile: nothing to wait for
+    z, u = synth.prefilled_beam(10000, 7.9, 5.0, seed=8)
+    t.add_particles(z, u)
+    assert t.lib.tube_selftest_wait_timeout(t.h) == -6      # SCLF_ETIMEOUT
+    assert t.status()["flags"] & B.FLAG_TIMEOUT
+    assert t.check() == -6
+    t.close()
+    t2, o = pair(gpu_lib, kw, "f32", "fixed")
+    for n in range(20):
+        t2.step()
+        o.step()
+        compare(t2, o, TOL[B.SCLF_FP32], "after the timeout, step %d" % n)
+    assert t2.check() == 0
+    t2.close()
