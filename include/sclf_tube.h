@@ -423,6 +423,11 @@ typedef struct sclf_adjoint* adjoint_t;   /* opaque, library-owned */
                               after the last step                            */
 #define SCLF_OBJ_EZ    1   /* ||E_z||_2 = sqrt(sum_j E_z,j^2 dz) after the last
                               step                                           */
+#define SCLF_OBJ_EZ_WEIGHTED 2 /* sum_j w_j E_z,j after the last step, with the
+                              cell weights of adjoint_set_weights: any
+                              projection of the E_z profile (unit weights give
+                              one cell's sensitivity); its value is the dot
+                              product of w with tube_read_fields' E_z     */
 
 /* Create a driver for runs of nsteps steps (> 0, a multiple of
  * checkpoint_every, which is even and > 0) of a tube with parameters p
@@ -451,6 +456,9 @@ int adjoint_tube(adjoint_t a, tube_t* out);
  * to the tube's own rule. A negative count is SCLF_EINVAL. */
 int adjoint_set_injections(adjoint_t a, const int64_t* n_inj);
 
+/* w: host, Nz finite cell weights of SCLF_OBJ_EZ_WEIGHTED (copied). */
+int adjoint_set_weights(adjoint_t a, const double* w);
+
 /* Run the nsteps steps from the initial state (the tube's particles at the
  * first call), storing checkpoints and the per-step events. values: host,
  * 2 doubles or NULL, receives the objectives SCLF_OBJ_GAMMA and
@@ -463,7 +471,8 @@ int adjoint_forward(adjoint_t a, double* values);
  * before the first forward pass. Synchronises. */
 int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_slots);
 
-/* Gradient of one objective of the last forward pass: d_rho_gj (host,
+/* Gradient of one objective (SCLF_OBJ_*) of the last forward pass
+ * (SCLF_ESTATE for SCLF_OBJ_EZ_WEIGHTED before adjoint_set_weights): d_rho_gj (host,
  * Nz+1 doubles or NULL) = d objective / d rho_GJ at the nodes (node 0 is
  * 0: it enters only the frozen injection count), d_s (host or NULL) =
  * d objective / d s. SCLF_ESTATE before the first forward pass.

@@ -27,6 +27,8 @@ derivative is taken inside the pieces: dF_j(x)/dx = 1 for j <= x < j + 1
 Objectives at the end of the run:
   'gamma': mean over the live particles of gamma = sqrt(1 + u^2)
   'ez'   : ||E_z||_2 = sqrt(sum_j E_z,j^2 dz)
+  'ez_weighted': sum_j w_j E_z,j for given cell weights w (any projection of
+           the E_z profile; unit weights give one cell's sensitivity)
 """
 
 from __future__ import annotations
@@ -38,7 +40,7 @@ from scipy.linalg import solve_banded
 
 from . import sclf_oracle as so
 
-OBJECTIVES = ("gamma", "ez")
+OBJECTIVES = ("gamma", "ez", "ez_weighted")
 
 
 # ---------------------------------------------------------------------------
@@ -106,7 +108,9 @@ def initial_fields_adjoint(lez0, ler0, dz):
 # Objectives
 # ---------------------------------------------------------------------------
 
-def objective_value(which, u, ez, dz):
+def objective_value(which, u, ez, dz, weights=None):
+    if which == "ez_weighted":
+        return float(np.dot(np.asarray(weights, np.float64), np.asarray(ez, np.float64)))
     if which == "gamma":
         u = np.asarray(u, np.float64)
         return float(np.mean(np.sqrt(1.0 + u * u))) if u.size else 0.0
@@ -174,10 +178,11 @@ class AdjointRun:
                 states[-1] += [t.j.copy(), inj]
         return t, inj_log, rem_log, states
 
-    def gradient(self, which, nsteps, injections=None):
+    def gradient(self, which, nsteps, injections=None, weights=None):
         """Objective and its gradient with respect to rho_GJ (nodes 0..Nz)
-        and s, by the discrete adjoint of the recorded run. Returns
-        (value, d_rho_gj, d_s, injected per step, removed IDs per step)."""
+        and s, by the discrete adjoint of the recorded run ('ez_weighted'
+        takes the cell weights). Returns (value, d_rho_gj, d_s, injected per
+        step, removed IDs per step)."""
         if which not in OBJECTIVES:
             raise ValueError(which)
         t, inj_log, rem_log, states = self.forward(nsteps, injections=injections, keep=True)
@@ -186,7 +191,7 @@ class AdjointRun:
         dt_r = float(rt(dt))                 # the constants the push used
         cfl_r = float(rt(dt / dz))
         u_end = t.u.astype(np.float64)
-        value = objective_value(which, u_end, t.ez, dz)
+        value = objective_value(which, u_end, t.ez, dz, weights)
 
         lez = np.zeros(nz)
         ler = np.zeros(nz + 1)
@@ -194,9 +199,12 @@ class AdjointRun:
         lx = np.zeros(u_end.size)
         if which == "gamma":
             lu = u_end / np.sqrt(1.0 + u_end * u_end) / max(u_end.size, 1)
-        else:
+        elif which == "ez":
             lu = np.zeros(u_end.size)
             lez = t.ez * dz / value if value > 0.0 else np.zeros(nz)
+        else:
+            lu = np.zeros(u_end.size)
+            lez = np.array(weights, np.float64)
         sum_lj_j = 0.0
 
         fix = self.precision == "fix32"

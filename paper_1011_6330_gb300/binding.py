@@ -23,7 +23,7 @@ SCLF_GR_COS, SCLF_GR_BOTH = 0, 1
 SCLF_FP32, SCLF_FP64, SCLF_FIX32 = 0, 1, 2
 SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
 FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
-SCLF_OBJ_GAMMA, SCLF_OBJ_EZ = 0, 1
+SCLF_OBJ_GAMMA, SCLF_OBJ_EZ, SCLF_OBJ_EZ_WEIGHTED = 0, 1, 2
 
 
 class TubeParams(C.Structure):
@@ -115,6 +115,7 @@ SIGNATURES = {
     "adjoint_tube": (_i32, [_vp, C.POINTER(_vp)]),
     "adjoint_set_injections": (_i32, [_vp, _pi64]),
     "adjoint_forward": (_i32, [_vp, _pd]),
+    "adjoint_set_weights": (_i32, [_vp, _pd]),
     "adjoint_events": (_i32, [_vp, _pi64, _pi64, _pi64]),
     "adjoint_backward": (_i32, [_vp, C.c_int32, _pd, _pd]),
     "adjoint_param_gradient": (_i32, [_vp, _pd, C.c_double, _pd]),
@@ -467,6 +468,12 @@ class Adjoint:
         assert a.size == self.nsteps
         _check(self.lib.adjoint_set_injections(self.h, a.ctypes.data_as(_pi64)),
                "adjoint_set_injections")
+
+    def set_weights(self, w):
+        """Cell weights of the SCLF_OBJ_EZ_WEIGHTED objective sum_j w_j E_z,j."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.size == self.nz
+        _check(self.lib.adjoint_set_weights(self.h, _dptr(w)), "adjoint_set_weights")
 
     def forward(self):
         """(mean terminal gamma, ||E_z||_2) of the run."""

@@ -44,6 +44,8 @@ struct sclf_adjoint {
     char* ls_tab = nullptr;         // per cell: (s/dt) lambda_J in the particle precision
     double* part = nullptr;
     double* values = nullptr;       // the two objectives of the last forward pass
+    double* weights = nullptr;      // nz cell weights of SCLF_OBJ_EZ_WEIGHTED
+    bool have_weights = false;
     int adj_grid = 0;
     std::vector<double> rho_p0;     // particles' charge density at t = 0 (nodes)
     bool started = false;           // checkpoint 0 holds the initial state
@@ -415,8 +417,10 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
                                          reinterpret_cast<const Real*>(A->ck_u + A->nseg * bytes),
                                          A->ck_st + A->nseg, reinterpret_cast<Real*>(A->lx),
                                          reinterpret_cast<Real*>(A->lu), s)));
-    } else {
+    } else if (objective == SCLF_OBJ_EZ) {
         CK(launch_seed_ez(ckf_of(A, A->nseg), static_cast<int>(nz), t->d.dz, A->values, A->lez, s));
+    } else {                                      // d(sum_j w_j E_z,j)/dE_z = w
+        CK(cudaMemcpyAsync(A->lez, A->weights, nz * 8, cudaMemcpyDeviceToDevice, s));
     }
     CK(cudaEventRecord(A->ev[2], s));
     for (int64_t c = A->nseg - 1; c >= 0; --c) {
@@ -530,6 +534,7 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
     const int64_t o_lstab = take(nz * A->rs);
     const int64_t o_part = take(2 * kObjBlocks * 8);
     const int64_t o_values = take(2 * 8);
+    const int64_t o_weights = take(nz * 8);
     if (cudaMalloc(&A->mem, o) != cudaSuccess) {
         A->mem = nullptr;
         free_adjoint(A);
@@ -560,6 +565,7 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
     A->ls_tab = m + o_lstab;
     A->part = reinterpret_cast<double*>(m + o_part);
     A->values = reinterpret_cast<double*>(m + o_values);
+    A->weights = reinterpret_cast<double*>(m + o_weights);
     if (cudaMemsetAsync(A->mem, 0, o, t->gstream) != cudaSuccess ||
         cudaStreamSynchronize(t->gstream) != cudaSuccess) {
         free_adjoint(A);
@@ -604,6 +610,17 @@ int adjoint_set_injections(adjoint_t a, const int64_t* n_inj) {
     return SCLF_OK;
 }
 
+int adjoint_set_weights(adjoint_t a, const double* w) {
+    if (!a || !w) return SCLF_EINVAL;
+    for (int j = 0; j < a->nz; ++j)
+        if (!std::isfinite(w[j])) return SCLF_EINVAL;
+    CK(cudaMemcpyAsync(a->weights, w, static_cast<size_t>(a->nz) * 8, cudaMemcpyHostToDevice,
+                       a->t->gstream));
+    CK(cudaStreamSynchronize(a->t->gstream));
+    a->have_weights = true;
+    return SCLF_OK;
+}
+
 int adjoint_forward(adjoint_t a, double* values) {
     NvtxRange nvtx_range("adjoint_forward");
     if (!a) return SCLF_EINVAL;
@@ -628,8 +645,11 @@ int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_s
 
 int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s) {
     NvtxRange nvtx_range("adjoint_backward");
-    if (!a || (objective != SCLF_OBJ_GAMMA && objective != SCLF_OBJ_EZ)) return SCLF_EINVAL;
-    if (!a->forward_done) return SCLF_ESTATE;
+    if (!a || (objective != SCLF_OBJ_GAMMA && objective != SCLF_OBJ_EZ &&
+               objective != SCLF_OBJ_EZ_WEIGHTED))
+        return SCLF_EINVAL;
+    if (!a->forward_done || (objective == SCLF_OBJ_EZ_WEIGHTED && !a->have_weights))
+        return SCLF_ESTATE;
     if (fix32(a->t)) return run_backward<int, float>(a, objective, d_rho_gj, d_s);
     return a->rs == 8 ? run_backward<double, double>(a, objective, d_rho_gj, d_s)
                       : run_backward<float, float>(a, objective, d_rho_gj, d_s);

@@ -237,3 +237,24 @@ def test_fix32_gradient_against_fp64_is_stated(gpu_lib):
     print("max rel gradient error vs FP64: fp32 %.3e fix32 %.3e" % (errs[B.SCLF_FP32],
                                                                   errs[B.SCLF_FIX32]))
     assert errs[B.SCLF_FIX32] <= max(errs[B.SCLF_FP32], 1e-6)
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FP64, B.SCLF_FP32])
+def test_weighted_ez_profile_gradient_matches_oracle(gpu_lib, prec):
+    """The projection sum_j w_j E_z,j of the final E_z profile (random
+    weights) on the flat tube: GPU gradient against the oracle's adjoint."""
+    kw, z, u, nsteps, K = flat_problem(prec)
+    a, _ = gpu_run(kw, z, u, nsteps, K)
+    w = np.random.default_rng(3).standard_normal(kw["Nz"])
+    with pytest.raises(B.SclfError) as e:
+        a.backward(B.SCLF_OBJ_EZ_WEIGHTED)            # no weights yet
+    assert e.value.code == -7
+    a.set_weights(w)
+    g_rho, g_s = a.backward(B.SCLF_OBJ_EZ_WEIGHTED)
+    run = oracle_run(kw, z, u, prec)
+    v, d_rho, d_s, _, _ = run.gradient("ez_weighted", nsteps, weights=w)
+    ez = a.tube.read_fields(rho=False)["ez"]
+    scale = float(np.sum(np.abs(w) * np.abs(ez)))
+    assert abs(float(np.dot(w, ez)) - v) <= (1e-12 if prec == B.SCLF_FP64 else 1e-6) * scale
+    assert rel(g_rho, d_rho) <= TOL[prec] and abs(g_s - d_s) <= TOL[prec] * abs(d_s)
+    a.close()

@@ -186,3 +186,24 @@ def test_fix32_trajectory_gradient_is_close_to_float64():
     assert abs(vx - v64) <= 1e-7 * v64
     assert np.max(np.abs(gx - g64)) <= 1e-5 * np.max(np.abs(g64))
     assert abs(sx - s64) <= 1e-5 * abs(s64)
+
+
+def test_weighted_ez_gradient_matches_central_differences():
+    """The projection sum_j w_j E_z,j of the final E_z profile (random
+    weights): gradient along a random rho_GJ direction and in s against
+    central differences; with no particles and no injection it is linear in
+    rho_GJ, so its gradient dotted with rho_GJ is the value itself."""
+    run, n = flat_case()
+    w = np.random.default_rng(9).standard_normal(run.nz)
+    value, d_rho, d_s, inj, rem = run.gradient("ez_weighted", n, weights=w)
+    d = np.random.default_rng(10).standard_normal(run.nz + 1)
+    vals = []
+    for sg in (1.0, -1.0):
+        t, _, rem2, _ = run.forward(n, rho_gj=run.rho_gj + sg * 1e-4 * d, injections=inj)
+        assert all(np.array_equal(a, b) for a, b in zip(rem, rem2))
+        vals.append(float(np.dot(w, t.ez)))
+    fd = (vals[0] - vals[1]) / 2e-4
+    assert abs(float(np.dot(d_rho, d)) - fd) <= 1e-6 * abs(fd)
+    empty = adj.AdjointRun(run.nz, run.L, run.dt, run.rho_gj * 1.3, run.s)
+    v0, g0, s0, _, _ = empty.gradient("ez_weighted", 30, injections=[0] * 30, weights=w)
+    assert abs(float(np.dot(g0, empty.rho_gj)) - v0) <= 1e-10 * abs(v0)
