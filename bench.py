@@ -345,6 +345,59 @@ def run_batch(args):
         if ent.get("kernel_sha") == kernel_sha("batch") and ent.get("tubes") == len(kws) \
                 and ws == 1:
             traffic = ent["bytes_per_launch"]
+    # end to end through the C ABI: every tube's particles from pinned host
+    # memory, K batch steps each followed by the batch's counters read back
+    # (batch_status), every tube's particles back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        import ctypes as C
+        lib = B.load()
+        saved = [t.save_particles()[:2] for t in batch.tubes]
+        counts = [x.size for x, _ in saved]
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        caps = [int(t.params.capacity) for t in batch.tubes]
+        pin_x = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+        pin_u = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+        for i, (x, u) in enumerate(saved):
+            pin_x.numpy()[offs[i]:offs[i + 1]] = x
+            pin_u.numpy()[offs[i]:offs[i + 1]] = u
+        del saved
+        ocaps = np.concatenate([[0], np.cumsum(caps)])
+        out_x = torch.empty(int(ocaps[-1]), dtype=torch.float32, pin_memory=True)
+        out_u = torch.empty(int(ocaps[-1]), dtype=torch.float32, pin_memory=True)
+        nout = C.c_int64()
+        ksteps = args.steps
+        barrier()
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        for i, t in enumerate(batch.tubes):
+            rc = lib.tube_load_particles(t.h, counts[i],
+                                         C.c_void_p(pin_x.data_ptr() + 4 * int(offs[i])),
+                                         C.c_void_p(pin_u.data_ptr() + 4 * int(offs[i])), None)
+            if rc:
+                raise RuntimeError("tube_load_particles: %d" % rc)
+        n_e2e = 0
+        for _ in range(ksteps):
+            st = batch.status()                        # per-step D2H of every tube's counters
+            n_e2e += sum(x["n_particles"] + x["pending_injection"] for x in st)
+            batch.step()
+        n_back = 0
+        for i, t in enumerate(batch.tubes):
+            rc = lib.tube_save_particles(t.h, caps[i], C.byref(nout),
+                                         C.c_void_p(out_x.data_ptr() + 4 * int(ocaps[i])),
+                                         C.c_void_p(out_u.data_ptr() + 4 * int(ocaps[i])), None)
+            if rc:
+                raise RuntimeError("tube_save_particles: %d" % rc)
+            n_back += nout.value
+        torch.cuda.synchronize()
+        el_e2e = time.perf_counter() - h0
+        n_all, el_e2e = combine_ranks(n_e2e, el_e2e, device="cuda")
+        stats_bytes = C.sizeof(B.TubeStats) * len(kws)
+        e2e = {"value": n_all / el_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 8.0 * offs[-1] / ksteps,
+               "d2h_bytes_per_step": (8.0 * n_back + ksteps * stats_bytes) / ksteps,
+               "path": "per tube tube_load_particles(pinned) + K x (batch_status, batch_step) + "
+                       "per tube tube_save_particles(pinned)"}
     # the plain form: the same tubes, one tube at a time
     k_plain = min(args.steps, 128)
     for t in plain:
@@ -398,7 +451,7 @@ def run_batch(args):
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],
                      "bytes_per_launch": BYTES_PER_PARTICLE * slots},
-        "cpu_baseline": cpu, "e2e": None,
+        "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(2 * tm["n_steps"] + tm["n_compactions"] * len(kws)),
         "clocks": clk,
         "status": {"check": int(max(t.check() for t in batch.tubes))},

@@ -359,6 +359,12 @@ int batch_size(batch_t b, int32_t* n);
  * on it; tube_step and tube_run return SCLF_ESTATE (the batch steps it). */
 int batch_tube(batch_t b, int32_t i, tube_t* out);
 
+/* The counters of all n tubes (n must equal batch_size) in one call: one
+ * gather kernel and one device-to-host copy into out[0..n-1] (caller-owned
+ * host memory), the same fields tube_status gives for each tube.
+ * Synchronises the batch's stream. */
+int batch_status(batch_t b, int32_t n, tube_stats* out);
+
 /* One step of every tube. Asynchronous. */
 int batch_step(batch_t b);
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "batch_destroy": (_i32, [_vp]),
     "batch_size": (_i32, [_vp, C.POINTER(C.c_int32)]),
     "batch_tube": (_i32, [_vp, C.c_int32, C.POINTER(_vp)]),
+    "batch_status": (_i32, [_vp, C.c_int32, C.POINTER(TubeStats)]),
     "batch_step": (_i32, [_vp]),
     "batch_run": (_i32, [_vp, _i64]),
     "batch_set_timing": (_i32, [_vp, _i32]),
@@ -397,6 +398,14 @@ class Batch:
 
     def step(self):
         _check(self.lib.batch_step(self.h), "batch_step")
+
+    def status(self):
+        """Every tube's counters from one gather and one copy: a list of
+        dicts with the fields of Tube.status()."""
+        n = len(self.tubes)
+        arr = (TubeStats * n)()
+        _check(self.lib.batch_status(self.h, n, arr), "batch_status")
+        return [{f: getattr(arr[i], f) for f, _ in TubeStats._fields_} for i in range(n)]
 
     def run(self, n):
         _check(self.lib.batch_run(self.h, int(n)), "batch_run")

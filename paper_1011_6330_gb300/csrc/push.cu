@@ -324,6 +324,26 @@ __global__ void batch_refresh_kernel(BatchTube* tubes, int n_tubes) {
     d.n_req = n_req;
 }
 
+// Every tube's committed counters in the public tube_stats layout, one
+// thread per tube, for a single device-to-host copy.
+__global__ void batch_status_kernel(const BatchTube* tubes, int n_tubes, tube_stats* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tubes) return;
+    const DevState* st = tubes[i].st;
+    tube_stats s;
+    s.step = st->step;
+    s.n_particles = st->n_live;
+    s.n_slots = st->n_slots;
+    s.total_injected = st->total_injected;
+    s.last_injected = st->last_injected;
+    s.last_removed = st->last_removed;
+    s.pending_injection = st->n_inj;
+    s.surface_field = st->surface_field;
+    s.flags = st->flags;
+    s.reserved = 0;
+    out[i] = s;
+}
+
 // The batched kernel's shapes, (particles per thread, CTAs per SM in the
 // launch bounds, runs per thread); batch_autotune picks one per batch by
 // timing.
@@ -358,6 +378,12 @@ cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid, cudaS
 
 cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s) {
     batch_refresh_kernel<<<(n_tubes + 127) / 128, 128, 0, s>>>(tubes, n_tubes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_status(const BatchTube* tubes, int n_tubes, tube_stats* out,
+                                cudaStream_t s) {
+    batch_status_kernel<<<(n_tubes + 127) / 128, 128, 0, s>>>(tubes, n_tubes, out);
     return cudaGetLastError();
 }
 

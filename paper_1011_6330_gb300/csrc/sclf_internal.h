@@ -252,6 +252,8 @@ cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long
 // Copies each tube's step counters (slots, clipped injection, first ID) into
 // its descriptor before the particle launch.
 cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s);
+cudaError_t launch_batch_status(const BatchTube* tubes, int n_tubes, tube_stats* out,
+                                cudaStream_t s);
 int batch_push_grid_size(int variant, int device_sms);
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
                                int parity, cudaStream_t s);

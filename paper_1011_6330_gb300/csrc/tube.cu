@@ -1001,6 +1001,7 @@ struct sclf_batch {
     BatchTube* d_desc[3] = {nullptr, nullptr, nullptr};
     int* d_tile_tube[3] = {nullptr, nullptr, nullptr};
     int* d_cell_tube = nullptr;
+    tube_stats* d_stats = nullptr;     // batch_status gathers every tube's counters here
     long long n_tiles[3] = {0, 0, 0};
     int n_cells = 0;
     int push_grid[kBatchVariants] = {};
@@ -1208,6 +1209,7 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
             return fail(SCLF_ECUDA);
     }
     if (cudaMalloc(&b->d_cell_tube, sizeof(int) * cells) != cudaSuccess) return fail(SCLF_ENOMEM);
+    if (cudaMalloc(&b->d_stats, sizeof(tube_stats) * n) != cudaSuccess) return fail(SCLF_ENOMEM);
     if (cudaMemcpyAsync(b->d_cell_tube, cell_tube.data(), sizeof(int) * cells, cudaMemcpyHostToDevice, b->stream) ||
         cudaStreamSynchronize(b->stream))
         return fail(SCLF_ECUDA);
@@ -1248,6 +1250,7 @@ int batch_destroy(batch_t b) {
         if (b->d_tile_tube[c]) cudaFree(b->d_tile_tube[c]);
     }
     if (b->d_cell_tube) cudaFree(b->d_cell_tube);
+    if (b->d_stats) cudaFree(b->d_stats);
     delete b;
     return SCLF_OK;
 }
@@ -1261,6 +1264,15 @@ int batch_size(batch_t b, int32_t* n) {
 int batch_tube(batch_t b, int32_t i, tube_t* out) {
     if (!b || !out || i < 0 || i >= static_cast<int32_t>(b->tubes.size())) return SCLF_EINVAL;
     *out = b->tubes[i];
+    return SCLF_OK;
+}
+
+int batch_status(batch_t b, int32_t n, tube_stats* out) {
+    if (!b || !out || n != static_cast<int32_t>(b->tubes.size())) return SCLF_EINVAL;
+    CK(launch_batch_status(b->d_desc[0], n, b->d_stats, b->stream));
+    CK(cudaMemcpyAsync(out, b->d_stats, sizeof(tube_stats) * n, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     return SCLF_OK;
 }
 

@@ -453,9 +453,12 @@ def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
     batch.run(25)
     for t in alone:
         t.run(66)
+    gathered = batch.status()                   # one gather for the whole batch
+    assert len(gathered) == len(kws)
     for i in range(len(kws)):
         a, b = batch.tubes[i], alone[i]
         sa, sb = a.status(), b.status()
+        assert gathered[i] == sa, i
         for k in ("step", "n_particles", "total_injected", "last_injected", "last_removed",
                   "pending_injection", "flags"):
             assert sa[k] == sb[k], (i, k)
@@ -547,6 +550,38 @@ def _same_state(sa, sb):
             assert np.array_equal(x, y)
         for k in ("ez", "er", "b", "j"):
             assert np.array_equal(a[5][k], b[5][k]), k
+
+
+def test_batch_members_survive_a_save_and_load_round_trip(gpu_lib):
+    """Saving every tube of a batch to host memory and loading it back (the
+    end-to-end path: tube_save_particles, tube_load_particles on batch
+    members) changes nothing the batch computes afterwards: fields bit for
+    bit, live particles in slot order, injection counts."""
+    kws = _small_batch_params()
+    a = B.Batch([B.default_params(**kw) for kw in kws])
+    b = B.Batch([B.default_params(**kw) for kw in kws])
+    for bb in (a, b):
+        for i, kw in enumerate(kws):
+            _fill(bb.tubes[i], kw, seed=10 + i)
+        bb.run(20)
+    for t in a.tubes:
+        xi, u, _ = t.save_particles()
+        t.load_particles(xi, u)
+    a.run(75)
+    b.run(75)
+    sa, sb = a.status(), b.status()
+    for i in range(len(kws)):
+        for k in ("step", "n_particles", "last_injected", "last_removed", "pending_injection",
+                  "surface_field", "flags"):
+            assert sa[i][k] == sb[i][k], (i, k)
+        pa, pb = a.tubes[i].read_particles(), b.tubes[i].read_particles()
+        for x, y in zip(pa[:2], pb[:2]):
+            assert np.array_equal(x, y), i
+        fa, fb = a.tubes[i].read_fields(rho=False), b.tubes[i].read_fields(rho=False)
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(fa[k], fb[k]), (i, k)
+    a.close()
+    b.close()
 
 
 def test_batch_kernel_shapes_agree_bit_for_bit_and_autotune_keeps_one(gpu_lib):
