@@ -93,6 +93,13 @@ def combine_ranks(work, seconds, device="cpu"):
     return float(w.item()), float(t.item())
 
 
+def barrier(ws):
+    """Barrier over the ranks of a multi-GPU run (no-op on one GPU)."""
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def rank_seed(rank, base=0):
     """Seed of a rank's independent tube (distinct per rank)."""
     return base + 1000003 * rank
@@ -324,10 +331,13 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
+    barrier(ws)
+    torch.cuda.synchronize()
     e0.record(stream)
     batch.run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier(ws)
     clk = clocks.stop()
     tm = batch.timing()
     batch.set_timing(False)
@@ -367,7 +377,7 @@ def run_batch(args):
         out_u = torch.empty(int(ocaps[-1]), dtype=torch.float32, pin_memory=True)
         nout = C.c_int64()
         ksteps = args.steps
-        barrier()
+        barrier(ws)
         torch.cuda.synchronize()
         h0 = time.perf_counter()
         for i, t in enumerate(batch.tubes):
@@ -394,7 +404,7 @@ def run_batch(args):
         n_all, el_e2e = combine_ranks(n_e2e, el_e2e, device="cuda")
         stats_bytes = C.sizeof(B.TubeStats) * len(kws)
         e2e = {"value": n_all / el_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": 8.0 * offs[-1] / ksteps,
+               "h2d_bytes_per_step": 8.0 * float(offs[-1]) / ksteps,
                "d2h_bytes_per_step": (8.0 * n_back + ksteps * stats_bytes) / ksteps,
                "path": "per tube tube_load_particles(pinned) + K x (batch_status, batch_step) + "
                        "per tube tube_save_particles(pinned)"}
@@ -741,10 +751,6 @@ def main():
         sort_ms = 1e3 * (time.perf_counter() - w0)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
     # warm-up
     t.run(args.warmup)
     torch.cuda.synchronize()
@@ -752,7 +758,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize()
     t.set_timing(True)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -761,7 +767,7 @@ def main():
     t.run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    barrier()
+    barrier(ws)
     clk = clocks.stop()
     el_ms = e0.elapsed_time(e1)
     tm = t.timing()
@@ -806,7 +812,7 @@ def main():
         lib = B.load()
         nout = C.c_int64()
         ksteps = args.steps
-        barrier()
+        barrier(ws)
         torch.cuda.synchronize()
         h0 = time.perf_counter()
         lib.tube_load_particles(t.h, pin_x.numel(), C.c_void_p(pin_x.data_ptr()),

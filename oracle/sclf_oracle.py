@@ -524,12 +524,16 @@ class Tube:
             return base_weight_fix32(self.xi, self.fb)
         return base_weight_fixed(self.xi, self.rt)
 
-    def solve_fields(self):
+    def solve_fields(self, rho=None):
         """Eq. 4 with the tube's current charge: phi'' - phi = -4 pi (rho - rho_GJ)
         with rho the cloud-in-cell density of the particles at the nodes,
         phi(0) = 0, phi'(L) = 0; E_z = -phi', E_r = phi, B_phi = 0 (the
-        Sec. 2 initialisation applied to a prefilled tube)."""
-        rho = self.rho_nodes()
+        Sec. 2 initialisation applied to a prefilled tube). `rho` replaces
+        the tube's own density, for a state held outside the tube (e.g. the
+        sum of rho_nodes over chunks of a very large one)."""
+        if rho is None:
+            rho = self.rho_nodes()
+        rho = np.asarray(rho, np.float64)
         phi = poisson_potential(self.rho_gj - rho, self.dz)
         self.ez = -(phi[1:] - phi[:-1]) / self.dz
         self.er = phi.copy()

@@ -262,12 +262,52 @@ def test_save_with_holes_compacts_and_keeps_id_order(gpu_lib):
     t2.close()
 
 
-def test_full_size_gr_step_against_oracle_on_all_particles(gpu_lib):
+def _state_against_oracle(t, o, cells_per_unit, what=""):
+    """A tube's state against the oracle's, both stepped from the same seeded
+    synthetic state with their own Eq. 4 solves. The two initial solves
+    agree to ~1e-12 (different tridiagonal solvers), so the float32 gather
+    tables may differ in the last bit of a few entries: the counts must match
+    exactly, the fields norm-wise, the particles to an ulp-level bound, and
+    nearly all particles bit for bit."""
+    st = t.status()
+    assert st["step"] == o.step_count, what
+    assert st["last_injected"] == o.last_injected, what
+    assert st["last_removed"] == o.last_removed, what
+    assert st["n_particles"] == o.xi.size, what
+    assert st["pending_injection"] == o.injection_count(), what
+    f = t.read_fields(rho=False)
+    scale = float(np.max(np.abs(o.ez)))
+    assert rel(f["ez"], o.ez) < 1e-9, what
+    assert rel(f["er"], o.er, scale) < 1e-9 and rel(f["b"], o.b, scale) < 1e-9, what
+    assert rel(f["j"], o.j) < 1e-6, what
+    x, u, _ = t.save_particles()                      # slot order = ID order
+    same = np.count_nonzero((x.astype(o.xi.dtype) == o.xi) & (u == o.u))
+    dx = float(np.max(np.abs(x.astype(np.float64) - o.xi.astype(np.float64)), initial=0.0))
+    du = float(np.max(np.abs(u.astype(np.float64) - o.u) / np.sqrt(1.0 + o.u.astype(np.float64) ** 2),
+                      initial=0.0))
+    print("%s: %d of %d particles bit for bit, max |dxi| %.3g cells, max |du|/gamma %.3g"
+          % (what, same, x.size, dx / cells_per_unit, du))
+    assert same >= 0.999 * x.size, what
+    assert dx / cells_per_unit < 1e-2 and du < 1e-5, what
+
+
+def _full_size_against_oracle(t, o, steps, cells_per_unit):
+    """Step the tube and the oracle together and compare after every step."""
+    f = t.read_fields(rho=False)
+    assert rel(f["ez"], o.ez) < 1e-10
+    assert rel(f["er"], o.er, float(np.max(np.abs(o.ez)))) < 1e-10
+    for n in range(steps):
+        t.step()
+        o.step()
+        _state_against_oracle(t, o, cells_per_unit, "step %d" % n)
+    assert t.check() == 0
+
+
+def test_full_size_gr_tube_against_oracle_on_all_particles(gpu_lib):
     """The benchmark's tube (frame-dragging rho_GJ, 1e8 FP32 particles, Nz =
     65536, fixed-point current) in the launch configuration the benchmark
-    times: one step from a prefilled state is checked against the oracle on
-    every particle -- each push bit for bit, the whole current grid and the
-    field update exactly, the removal and the next injection counts."""
+    times, and the oracle, both from the same seeded synthetic state: three
+    steps compared on every particle, the whole grid and every count."""
     kw = workloads.gr_tube()
     t = B.Tube(B.default_params(**kw))
     d = t.derived
@@ -277,44 +317,15 @@ def test_full_size_gr_step_against_oracle_on_all_particles(gpu_lib):
     z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar, seed=0,
                                 eta_of_z=eta)
     t.add_particles(z, u)
-    del z, u
     t.solve_fields()
-    t.run(3)
-    f0 = t.read_fields(rho=False)
-    xi0, u0, _ = t.save_particles()
-    n_inj = t.status()["pending_injection"]
-    t.step()
-    f1 = t.read_fields(rho=False)
-    xi1, u1, _ = t.save_particles()
-    st = t.status()
-    nz = kw["Nz"]
-    assert st["last_injected"] == n_inj
-    xs_all = np.concatenate([xi0, np.zeros(n_inj, np.float32)])
-    us_all = np.concatenate([u0, np.zeros(n_inj, np.float32)])
-    del xi0, u0
-    acc = np.zeros(nz, np.int64)
-    x1o = np.empty_like(xs_all)
-    u1o = np.empty_like(us_all)
-    for s0 in range(0, xs_all.size, 10 ** 7):
-        xs, us = xs_all[s0:s0 + 10 ** 7], us_all[s0:s0 + 10 ** 7]
-        e = orc.gather(f0["ez"], xs, np.float32)
-        x1, u1c = orc.push(xs, us, e, d["dt"], d["dz"], np.float32)
-        x1o[s0:s0 + xs.size], u1o[s0:s0 + xs.size] = x1, u1c
-        acc += orc.deposit_fractions(nz, xs, x1, np.float32, "fixed")
-    alive = (x1o >= 0) & (x1o < np.float32(nz))
-    assert st["last_removed"] == x1o.size - int(np.count_nonzero(alive))
-    # every push, bit for bit, in ID order
-    assert np.array_equal(xi1, x1o[alive]) and np.array_equal(u1, u1o[alive])
-    # the whole current grid, exactly (fixed-point sums do not depend on order)
-    j = orc.current_from(acc, d["s"], d["dt"], "fixed")
-    assert np.array_equal(f1["j"], j)
-    ez, er, b = orc.field_update(f0["ez"], f0["er"], f0["b"], j, d["dt"], d["dz"])
-    assert np.array_equal(f1["ez"], ez) and np.array_equal(f1["er"], er)
-    assert np.array_equal(f1["b"], b)
-    w0 = orc.base_weight_fixed(xi1, np.float32)
-    n_next, _ = orc.injection_count(ez[0], w0, d["s"], d["dz"], d["rho0"])
-    assert st["pending_injection"] == n_next
-    assert t.check() == 0
+    zn = np.arange(kw["Nz"] + 1) * d["dz"]
+    rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"])
+    o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="f32", accumulate="fixed")
+    o.add_particles(z, u)
+    del z, u
+    o.solve_fields()
+    _full_size_against_oracle(t, o, 3, 1.0)
     t.close()
 
 
@@ -355,12 +366,11 @@ def test_fix32_ragged_tiles_with_forced_compaction(gpu_lib):
     t.close()
 
 
-def test_large_fix32_tube_step_against_oracle_on_all_particles(gpu_lib):
+def test_large_fix32_tube_against_oracle_on_all_particles(gpu_lib):
     """The large tube's configuration (B = 3e12 G, P = 0.1 s, Nz = 2^20,
-    fixed-point positions) with 2^27 particles: one step checked against the
-    oracle on every particle -- positions and momenta bit for bit, the whole
-    current grid and the field update exactly, removals and the next
-    injection count."""
+    fixed-point positions) with 2^27 particles, and the oracle, both from the
+    same seeded synthetic state: two steps compared on every particle, the
+    whole grid and every count."""
     n = 2 ** 27
     kw = workloads.large_tube(n_particles=n)
     t = B.Tube(B.default_params(**kw))
@@ -368,44 +378,94 @@ def test_large_fix32_tube_step_against_oracle_on_all_particles(gpu_lib):
     cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
     eta = lambda zz: 1.0 + zz * cu["R_over_Rstar"]
     gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(kw["incl_rad"])
+    zn = np.arange(kw["Nz"] + 1) * d["dz"]
+    rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"])
+    o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="fix32", accumulate="fixed")
     for z, u in synth.prefilled_beam_chunks(n, d["L"] - d["dz"], gfar, seed=5,
                                             chunk=1 << 25, eta_of_z=eta):
         t.add_particles(z, u)
+        o.add_particles(z, u)
     t.solve_fields()
-    t.run(2)
+    o.solve_fields()
+    _full_size_against_oracle(t, o, 2, float(2 ** orc.fix32_bits(kw["Nz"])))
+    t.close()
+
+
+def test_large_tube_full_size_step_against_streamed_oracle(gpu_lib):
+    """The large tube at its benchmark size (2^30 fixed-point particles, Nz =
+    2^20, the benchmark's seeded state and launch configuration): one step
+    against the oracle streamed over 2^26-particle chunks -- the oracle's own
+    initial fields from the summed cloud-in-cell charge, then every
+    particle's gather, push and deposit, the removals, the injected
+    electrons, the whole current grid, the field update and the next
+    injection count."""
+    n, chunk = 2 ** 30, 1 << 26
+    kw = workloads.large_tube(n_particles=n)
+    t = B.Tube(B.default_params(**kw))
+    d = t.derived
+    nz, dz, dt, s = kw["Nz"], d["dz"], d["dt"], d["s"]
+    fb = orc.fix32_bits(nz)
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    eta = lambda zz: 1.0 + zz * cu["R_over_Rstar"]
+    gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(kw["incl_rad"])
+    rho_gj = orc.rho_gj_profile(orc.RHO_GR, np.arange(nz + 1) * dz, cu["Lambda0"],
+                                kw["incl_rad"], cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+    o = orc.Tube(nz, d["L"], dt, rho_gj, s, precision="fix32", accumulate="fixed")
+    rho, w0, pieces = np.zeros(nz + 1), 0, []
+    for z, u in synth.prefilled_beam_chunks(n, d["L"] - dz, gfar, seed=0, chunk=chunk,
+                                            eta_of_z=eta):
+        t.add_particles(z, u)
+        oc = orc.Tube(nz, d["L"], dt, rho_gj, s, precision="fix32", accumulate="fixed")
+        oc.add_particles(z, u)
+        rho += oc.rho_nodes()
+        w0 += oc.w0
+        pieces.append((oc.xi.astype(np.int32), oc.u))
+        del z, u, oc
+    t.solve_fields()
+    o.solve_fields(rho)
     f0 = t.read_fields(rho=False)
-    X0, u0, _ = t.save_particles()
-    n_inj = t.status()["pending_injection"]
+    assert rel(f0["ez"], o.ez) < 1e-10
+    n_inj, _ = orc.injection_count(o.ez[0], w0, s, dz, rho_gj[0])
+    assert t.status()["pending_injection"] == n_inj
     t.step()
-    f1 = t.read_fields(rho=False)
-    X1, u1, _ = t.save_particles()
     st = t.status()
-    nz, fb = kw["Nz"], orc.fix32_bits(kw["Nz"])
-    assert st["last_injected"] == n_inj
-    xs_all = np.concatenate([X0.astype(np.int64), np.zeros(n_inj, np.int64)])
-    us_all = np.concatenate([u0, np.zeros(n_inj, np.float32)])
-    del X0, u0
+    f1 = t.read_fields(rho=False)
+    Xg, ug, _ = t.save_particles()                    # slot order = ID order
+    pieces.append((np.zeros(n_inj, np.int32), np.zeros(n_inj, np.float32)))
     acc = np.zeros(nz, np.int64)
-    x1o = np.empty_like(xs_all)
-    u1o = np.empty_like(us_all)
-    fin = np.empty(xs_all.size, bool)
-    step = 1 << 24
-    for s0 in range(0, xs_all.size, step):
-        xs, us = xs_all[s0:s0 + step], us_all[s0:s0 + step]
-        e = orc.gather_fix32(f0["ez"], xs, fb)
-        x1, u1c, ok = orc.push_fix32(xs, us, e, d["dt"], d["dz"], fb)
-        x1o[s0:s0 + xs.size], u1o[s0:s0 + xs.size], fin[s0:s0 + xs.size] = x1, u1c, ok
-        acc += orc.deposit_fix32(nz, xs[ok], x1[ok], fb)
-    alive = fin & (x1o >= 0) & (x1o < (nz << fb))
-    assert st["last_removed"] == x1o.size - int(np.count_nonzero(alive))
-    assert np.array_equal(X1.astype(np.int64), x1o[alive]) and np.array_equal(u1, u1o[alive])
-    j = orc.current_from(acc, d["s"], d["dt"], "fixed")
-    assert np.array_equal(f1["j"], j)
-    ez, er, b = orc.field_update(f0["ez"], f0["er"], f0["b"], j, d["dt"], d["dz"])
-    assert np.array_equal(f1["ez"], ez) and np.array_equal(f1["er"], er)
-    assert np.array_equal(f1["b"], b)
-    w0 = orc.base_weight_fix32(X1.astype(np.int64), fb)
-    n_next, _ = orc.injection_count(ez[0], w0, d["s"], d["dz"], d["rho0"])
+    off = removed = same = w1 = 0
+    dx = du = 0.0
+    for X, u in pieces:
+        X = X.astype(np.int64)
+        e = orc.gather_fix32(o.ez, X, fb)
+        X1, u1, ok = orc.push_fix32(X, u, e, dt, dz, fb)
+        acc += orc.deposit_fix32(nz, X[ok], X1[ok], fb)
+        alive = ok & (X1 >= 0) & (X1 < (nz << fb))
+        X1, u1 = X1[alive], u1[alive]
+        k = X1.size
+        removed += X.size - k
+        gx, gu = Xg[off:off + k].astype(np.int64), ug[off:off + k]
+        assert gx.size == k
+        same += int(np.count_nonzero((gx == X1) & (gu == u1)))
+        if k:
+            dx = max(dx, float(np.max(np.abs(gx - X1))) * 2.0 ** -fb)
+            du = max(du, float(np.max(np.abs(gu.astype(np.float64) - u1)
+                                      / np.sqrt(1.0 + u1.astype(np.float64) ** 2))))
+        w1 += orc.base_weight_fix32(X1, fb)
+        off += k
+    print("2^30 step: %d of %d particles bit for bit, max |dxi| %.3g cells, max |du|/gamma %.3g"
+          % (same, off, dx, du))
+    assert off == Xg.size == st["n_particles"]
+    assert st["last_injected"] == n_inj and st["last_removed"] == removed
+    assert same >= 0.999 * off and dx < 1e-2 and du < 1e-5
+    j = orc.current_from(acc, s, dt, "fixed")
+    ez, er, b = orc.field_update(o.ez, o.er, o.b, j, dt, dz)
+    scale = float(np.max(np.abs(ez)))
+    assert rel(f1["j"], j) < 1e-6
+    assert rel(f1["ez"], ez) < 1e-9 and rel(f1["er"], er, scale) < 1e-9
+    assert rel(f1["b"], b, scale) < 1e-9
+    n_next, _ = orc.injection_count(ez[0], w1, s, dz, rho_gj[0])
     assert st["pending_injection"] == n_next
     assert t.check() == 0
     t.close()
@@ -550,6 +610,51 @@ def _same_state(sa, sb):
             assert np.array_equal(x, y)
         for k in ("ez", "er", "b", "j"):
             assert np.array_equal(a[5][k], b[5][k]), k
+
+
+def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib):
+    """The 256-tube death-line batch at its benchmark size and launch
+    configuration (seeded states, autotuned particle-kernel shape; the
+    tuning steps are ordinary steps): after the tuning steps and one more,
+    five sampled tubes (flat and frame-dragging, the smallest and largest
+    grids) against the oracle run from the same seeded states."""
+    kws = workloads.death_line_batch()
+    batch = B.Batch([B.default_params(**kw) for kw in kws])
+    nzs = [kw["Nz"] for kw in kws]
+    sample = sorted({0, 1, int(np.argmin(nzs)), int(np.argmax(nzs)), len(kws) - 1})
+    states = {}
+    for i, kw in enumerate(kws):
+        t = batch.tubes[i]
+        d = t.derived
+        gr = kw["rho_gj_mode"] == B.SCLF_RHO_GR
+        gfar = (d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"]) if gr
+                else math.sqrt(2.0) * d["Lambda0"])
+        eta = (lambda zz, r=d["R_over_Rstar"]: 1.0 + zz * r) if gr else None
+        z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar, seed=i,
+                                    eta_of_z=eta)
+        t.add_particles(z, u)
+        t.solve_fields()
+        if i in sample:
+            states[i] = (z, u)
+    chosen, ms = batch.autotune(1)
+    batch.step()
+    nsteps = batch.tubes[0].status()["step"]
+    assert nsteps == len(B.Batch.VARIANTS) * 3 + 1
+    for i in sample:
+        kw, t = kws[i], batch.tubes[i]
+        d = t.derived
+        cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+        mode = orc.RHO_GR if kw["rho_gj_mode"] == B.SCLF_RHO_GR else orc.RHO_FLAT
+        rho = orc.rho_gj_profile(mode, np.arange(kw["Nz"] + 1) * d["dz"], cu["Lambda0"],
+                                 kw["incl_rad"], cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
+        o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="f32", accumulate="fixed")
+        o.add_particles(*states[i])
+        o.solve_fields()
+        o.run(nsteps)
+        _state_against_oracle(t, o, 1.0, "tube %d (Nz %d, shape %s)"
+                              % (i, kw["Nz"], B.Batch.VARIANTS[chosen]))
+    assert max(t.check() for t in batch.tubes) == 0
+    batch.close()
 
 
 def test_batch_members_survive_a_save_and_load_round_trip(gpu_lib):
