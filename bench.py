@@ -93,6 +93,11 @@ def combine_ranks(work, seconds, device="cpu"):
     return float(w.item()), float(t.item())
 
 
+def gr_workload_name(n, nz=65536):
+    """Name of the frame-dragging tube workload (both arms print the same)."""
+    return "gr_tube_P0.5s_B1e12G_Nz%d_%g_particles_fp32" % (nz, n)
+
+
 def barrier(ws):
     """Barrier over the ranks of a multi-GPU run (no-op on one GPU)."""
     if ws > 1:
@@ -276,7 +281,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "gr_tube_P0.5s_B1e12G_Nz65536_1e8_particles_fp32",
+        "config": {"workload": gr_workload_name(n),
                    "sample": "every %dth particle (%d), macro charge x%d" % (stride, z.size, stride),
                    "l2": "inputs larger than L2 on the GPU arm"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -846,7 +851,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "fix32+f32" if large else "f32",
         "data": "synthetic",
         "config": {"workload": ("large_tube_P0.1s_B3e12G_Nz%d_%d_particles_fix32" % (kw["Nz"], n))
-                   if large else "gr_tube_P0.5s_B1e12G_Nz65536_%g_particles_fp32" % n,
+                   if large else gr_workload_name(n, kw["Nz"]),
                    "rho_gj": "frame-dragging (Eq. 6-7), i = 0.5 rad",
                    "particles_per_gpu": n, "Nz": kw["Nz"], "Lambda0": d["Lambda0"],
                    "dt_R_over_c": d["dt"], "order": args.order,
