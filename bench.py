@@ -461,7 +461,9 @@ def run_batch(args):
         "plain_form": {"value": plain_value, "unit": UNIT, "steps": k_plain,
                        "how": "the same 256 tubes, each stepped alone (tube_run, graphs)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "batch_push_kernel",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": ("batch_push_const_kernel" if len(kws) <= 400
+                                else "batch_push_kernel"),
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],

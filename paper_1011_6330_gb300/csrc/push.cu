@@ -310,6 +310,47 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
     }
 }
 
+// The same with the tubes' constants in the parameter space; only the step
+// counters come from the descriptors.
+template <int kPPT, int kMinBlocks, bool kTwoRuns>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
+                        const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
+                        long long n_tiles) {
+    constexpr int kTile = kThreads * kPPT;
+    long long w0 = 0, removed = 0;
+    bool nonfinite = false;
+    int ti = blockIdx.x < n_tiles ? tile_tube[blockIdx.x] : 0;
+    for (long long g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+        const BatchConst& kc = k.t[ti];
+        const BatchTube& d = tubes[ti];
+        const long long gn = g + gridDim.x;
+        ti = gn < n_tiles ? tile_tube[gn] : 0;
+        const long long local = g - kc.tile0;
+        TileCtx<float, long long> c;
+        c.n_slots = d.n_slots;
+        c.n_tot = d.n_tot;
+        if (local == 0 && threadIdx.x == 0)
+            record_injection(kc.st, c.n_tot - c.n_slots, d.n_req, nullptr);
+        if (local * kTile >= c.n_tot) continue;          // the same for the whole CTA
+        c.xi = kc.xi;
+        c.u = kc.u;
+        c.xo = kc.xi;
+        c.uo = kc.u;
+        c.ids = kc.ids;
+        c.tab = reinterpret_cast<const float2*>(kc.ez2);
+        c.jacc = kc.jacc;
+        c.id0 = d.id0;
+        c.nzf = kc.nzf;
+        c.dt = kc.dt;
+        c.cfl = kc.cfl;
+        c.nz = kc.nz;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
+        push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
+        flush_tube_counters(kc.st, w0, removed, nonfinite);
+    }
+}
+
 __global__ void batch_refresh_kernel(BatchTube* tubes, int n_tubes) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tubes) return;
@@ -352,6 +393,15 @@ int batch_grid_of(int sms) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, batch_push_kernel<kPPT, kMinBlocks, kTwoRuns>, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * sms;
+}
+
+template <int kPPT, int kMinBlocks, bool kTwoRuns>
+int batch_const_grid_of(int sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_push_const_kernel<kPPT, kMinBlocks, kTwoRuns>, kThreads, 0);
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }
@@ -402,6 +452,34 @@ cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long
                               int grid, int variant, cudaStream_t s) {
 #define SCLF_BATCH_LAUNCH(P, M, T) \
     batch_push_kernel<P, M, T><<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles)
+    switch (variant) {
+        case 1: SCLF_BATCH_LAUNCH(8, 3, false); break;
+        case 2: SCLF_BATCH_LAUNCH(4, 4, false); break;
+        case 3: SCLF_BATCH_LAUNCH(8, 4, true); break;
+        case 4: SCLF_BATCH_LAUNCH(8, 3, true); break;
+        case 5: SCLF_BATCH_LAUNCH(16, 2, true); break;
+        default: SCLF_BATCH_LAUNCH(8, 4, false); break;
+    }
+#undef SCLF_BATCH_LAUNCH
+    return cudaGetLastError();
+}
+
+int batch_push_const_grid_size(int variant, int device_sms) {
+    switch (variant) {
+        case 1: return batch_const_grid_of<8, 3, false>(device_sms);
+        case 2: return batch_const_grid_of<4, 4, false>(device_sms);
+        case 3: return batch_const_grid_of<8, 4, true>(device_sms);
+        case 4: return batch_const_grid_of<8, 3, true>(device_sms);
+        case 5: return batch_const_grid_of<16, 2, true>(device_sms);
+        default: return batch_const_grid_of<8, 4, false>(device_sms);
+    }
+}
+
+cudaError_t launch_batch_push_const(const BatchConstTable& k, const BatchTube* tubes,
+                                    const int* tile_tube, long long n_tiles, int grid,
+                                    int variant, cudaStream_t s) {
+#define SCLF_BATCH_LAUNCH(P, M, T) \
+    batch_push_const_kernel<P, M, T><<<grid, kThreads, 0, s>>>(k, tubes, tile_tube, n_tiles)
     switch (variant) {
         case 1: SCLF_BATCH_LAUNCH(8, 3, false); break;
         case 2: SCLF_BATCH_LAUNCH(4, 4, false); break;

@@ -249,6 +249,31 @@ constexpr int kBatchMinBlocks[kBatchVariants] = {4, 3, 4, 4, 3, 2};
 constexpr int kBatchRuns[kBatchVariants] = {1, 1, 1, 2, 2, 2};
 cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
                               int grid, int variant, cudaStream_t s);
+// A tube's constants for the batched particle kernel, passed by value in the
+// kernel's parameter space (the constant bank, 32 KB at most): the compiler
+// reloads them instead of holding them in registers across a tile. Batches
+// of up to kBatchConstTubes tubes use it; larger ones read the descriptors.
+struct BatchConst {
+    DevState* st;
+    float* xi;
+    float* u;
+    long long* ids;
+    const float* ez2;
+    long long* jacc;
+    long long tile0;
+    int nz;
+    float nzf, dt, cfl;
+};
+constexpr int kBatchConstTubes = 400;
+struct BatchConstTable {
+    BatchConst t[kBatchConstTubes];
+};
+static_assert(sizeof(BatchConstTable) + 3 * sizeof(void*) <= 32764,
+              "kernel parameters are limited to 32764 bytes");
+cudaError_t launch_batch_push_const(const BatchConstTable& k, const BatchTube* tubes,
+                                    const int* tile_tube, long long n_tiles, int grid,
+                                    int variant, cudaStream_t s);
+int batch_push_const_grid_size(int variant, int device_sms);
 // Copies each tube's step counters (slots, clipped injection, first ID) into
 // its descriptor before the particle launch.
 cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s);

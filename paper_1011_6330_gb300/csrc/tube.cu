@@ -1005,6 +1005,10 @@ struct sclf_batch {
     long long n_tiles[3] = {0, 0, 0};
     int n_cells = 0;
     int push_grid[kBatchVariants] = {};
+    // the tubes' constants by value for the particle kernel (batches of up to
+    // kBatchConstTubes tubes), one table per tile class (tile0 differs)
+    std::vector<BatchConstTable> ctab;
+    int const_grid[kBatchVariants] = {};
     int variant = 0;                   // particle kernel shape (batch_autotune)
     int64_t host_step = 0;
     int steps_since_compact = 0;
@@ -1034,6 +1038,9 @@ cudaError_t batch_launch_push(sclf_batch* b, cudaStream_t s) {
     const int c = tile_class(b->variant);
     const cudaError_t e = launch_batch_refresh(b->d_desc[c], static_cast<int>(b->tubes.size()), s);
     if (e != cudaSuccess) return e;
+    if (!b->ctab.empty())
+        return launch_batch_push_const(b->ctab[c], b->d_desc[c], b->d_tile_tube[c], b->n_tiles[c],
+                                       b->const_grid[b->variant], b->variant, s);
     return launch_batch_push(b->d_desc[c], b->d_tile_tube[c], b->n_tiles[c],
                              b->push_grid[b->variant], b->variant, s);
 }
@@ -1194,6 +1201,22 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         if (cells >= (1LL << 31)) return fail(SCLF_EINVAL);
     }
     b->n_cells = static_cast<int>(cells);
+    if (n <= kBatchConstTubes) {
+        try {
+            b->ctab.resize(kTileClasses);
+        } catch (...) {
+            return fail(SCLF_ENOMEM);
+        }
+        for (int c = 0; c < kTileClasses; ++c) {
+            BatchConstTable& k = b->ctab[c];
+            std::memset(&k, 0, sizeof(k));
+            for (int32_t i = 0; i < n; ++i) {
+                const BatchTube& d = desc[i];
+                k.t[i] = BatchConst{d.st, d.xi, d.u, d.ids, d.ez2, d.jacc, tile0[c][i], d.nz, d.nzf,
+                                    d.dt, d.cfl};
+            }
+        }
+    }
     for (int c = 0; c < kTileClasses; ++c) {
         std::vector<BatchTube> dc(desc);
         for (int32_t i = 0; i < n; ++i) dc[i].tile0 = tile0[c][i];
@@ -1216,8 +1239,10 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
     const int sms = b->tubes[0]->sms;
     for (int v = 0; v < kBatchVariants; ++v) {
         b->push_grid[v] = batch_push_grid_size(v, sms);
+        b->const_grid[v] = batch_push_const_grid_size(v, sms);
         const long long nt = b->n_tiles[tile_class(v)];
         if (b->push_grid[v] > nt) b->push_grid[v] = static_cast<int>(nt);
+        if (b->const_grid[v] > nt) b->const_grid[v] = static_cast<int>(nt);
     }
     if (b->stream) {
         b->gstream = b->stream;

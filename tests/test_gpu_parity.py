@@ -657,6 +657,36 @@ def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib):
     batch.close()
 
 
+def test_large_batch_descriptor_kernel_equals_parameter_table_kernel(gpu_lib):
+    """Batches of more tubes than the particle kernel's parameter table holds
+    read every tube's constants from the device descriptors instead: a
+    401-tube batch advances its first five tubes bit for bit as a five-tube
+    batch does."""
+    small = _small_batch_params()
+    kws = [small[i % len(small)] for i in range(401)]
+    big = B.Batch([B.default_params(**kw) for kw in kws])
+    few = B.Batch([B.default_params(**kw) for kw in small])
+    for i, kw in enumerate(small):
+        _fill(big.tubes[i], kw, seed=30 + i)
+        _fill(few.tubes[i], kw, seed=30 + i)
+    for v in (0, 3):                              # one and two runs per thread
+        big.set_variant(v)
+        few.set_variant(v)
+        big.run(35)
+        few.run(35)
+    sb, sf = big.status(), few.status()
+    for i in range(len(small)):
+        assert sb[i] == sf[i], i
+        pa, pb = big.tubes[i].read_particles(), few.tubes[i].read_particles()
+        for x, y in zip(pa, pb):
+            assert np.array_equal(x, y), i
+        fa, fb = big.tubes[i].read_fields(rho=False), few.tubes[i].read_fields(rho=False)
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(fa[k], fb[k]), (i, k)
+    big.close()
+    few.close()
+
+
 def test_batch_members_survive_a_save_and_load_round_trip(gpu_lib):
     """Saving every tube of a batch to host memory and loading it back (the
     end-to-end path: tube_save_particles, tube_load_particles on batch
