@@ -46,11 +46,16 @@ extern "C" {
 #define SCLF_ENONFINITE -5   /* a particle produced NaN/Inf and was dropped   */
 #define SCLF_ETIMEOUT   -6   /* a bounded device-side wait gave up            */
 #define SCLF_ESTATE     -7   /* call not valid in the tube's current state    */
+#define SCLF_EBOUNDS    -8   /* an index failed its bounds check (set only by
+                                the bounds-checked build of the library)      */
 
 /* ---- sticky device status flags (tube_stats.flags) ---------------------- */
 #define SCLF_FLAG_CAPACITY  0x1u
 #define SCLF_FLAG_NONFINITE 0x2u
 #define SCLF_FLAG_TIMEOUT   0x4u
+#define SCLF_FLAG_BOUNDS    0x8u   /* bounds-checked build only: a particle
+                                      kernel met an index outside its array
+                                      and skipped the access                */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define SCLF_RHO_FLAT 0      /* Eq. 5 with the (R_* / r)^3 factor dropped       */

@@ -16,13 +16,16 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB_PATH = os.path.join(PKG, "libsclf_tube.so")
+# The bounds-checked build of the same library (tests load it in a separate
+# process through SCLF_TUBE_LIB).
+LIB_CHECKED_PATH = os.path.join(PKG, "libsclf_tube_checked.so")
 HEADER = os.path.join(ROOT, "include", "sclf_tube.h")
 
 SCLF_RHO_FLAT, SCLF_RHO_GR, SCLF_RHO_USER = 0, 1, 2
 SCLF_GR_COS, SCLF_GR_BOTH = 0, 1
 SCLF_FP32, SCLF_FP64, SCLF_FIX32 = 0, 1, 2
 SCLF_ACC_FIXED64, SCLF_ACC_FP64 = 0, 1
-FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
+FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOUNDS = 1, 2, 4, 8
 SCLF_OBJ_GAMMA, SCLF_OBJ_EZ, SCLF_OBJ_EZ_WEIGHTED = 0, 1, 2
 
 
@@ -139,11 +142,15 @@ class SclfError(RuntimeError):
         super().__init__("%s failed: %s (%d)" % (what, msg, code))
 
 
-def load(path=LIB_PATH):
-    """Load the in-tree library (built by ``paper_1011_6330_gb300.build``)."""
+def load(path=None):
+    """Load the in-tree library (built by ``paper_1011_6330_gb300.build``):
+    libsclf_tube.so, or the file SCLF_TUBE_LIB names (e.g. the
+    bounds-checked build)."""
     global _LIB
     if _LIB is not None:
         return _LIB
+    if path is None:
+        path = os.environ.get("SCLF_TUBE_LIB", LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError(
             "sclf_tube library not built (%s missing); run "

@@ -6,6 +6,9 @@ compiles csrc/*.cu and csrc/*.cpp with nvcc (in parallel, one -gencode) and
 links paper_1011_6330_gb300/libsclf_tube.so (static CUDA runtime). The
 kernels are compiled with --fmad=false so that every floating-point
 operation is rounded on its own, in the order the source writes it.
+build(checked=True) links libsclf_tube_checked.so from the same sources with
+-DSCLF_CHECKED: the particle kernels then test each data-dependent index
+before the access (a failed test sets SCLF_FLAG_BOUNDS and skips it).
 """
 
 from __future__ import annotations
@@ -22,6 +25,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsclf_tube.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libsclf_tube_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
@@ -43,8 +48,8 @@ def sources():
                   if f.endswith((".cu", ".cpp")))
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, build_dir):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc()] + ARCH + COMMON + list(extra) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -52,26 +57,30 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra_flags=()):
-    """Compile and link libsclf_tube.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra_flags=(), checked=False):
+    """Compile and link libsclf_tube.so (or, with checked=True, the
+    bounds-checked libsclf_tube_checked.so); returns its path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = list(extra_flags) + (["-DSCLF_CHECKED"] if checked else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, err in results:
             if err.strip():
                 sys.stderr.write(err)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv,
-                extra_flags=["-Xptxas", "-v"] if "-v" in sys.argv else []))
+                extra_flags=["-Xptxas", "-v"] if "-v" in sys.argv else [],
+                checked="--checked" in sys.argv))

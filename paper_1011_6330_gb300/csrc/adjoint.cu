@@ -101,7 +101,8 @@ __device__ __forceinline__ void adj_push_tile(const AdjPushArgs<Real>& a, long l
         const Real h = xx + Real(0.5);
         const Real mf = r_floor(h);
         const Real f = h - mf;
-        const Pair e = tab[static_cast<int>(mf)];
+        const int mi = static_cast<int>(mf);
+        const Pair e = checked_index(mi, nz + 1, a.flags) ? tab[mi] : Pair{};
         const Real ep = (Real(1) - f) * e.x + f * e.y;
         const Real u1 = us[k] - ep * dt;
         const Real g = r_sqrt(Real(1) + u1 * u1);
@@ -112,9 +113,11 @@ __device__ __forceinline__ void adj_push_tile(const AdjPushArgs<Real>& a, long l
         // unconditional (the index is clamped to a valid cell when unused)
         const int c1 = stay ? static_cast<int>(r_floor(x1)) : 0;
         const int c0 = static_cast<int>(r_floor(xx));
-        const Real lx1 = stay ? lxs[k] + ls[c1] : Real(0);
+        const Real ls1 = checked_index(c1, nz, a.flags) ? ls[c1] : Real(0);
+        const Real ls0 = checked_index(c0, nz, a.flags) ? ls[c0] : Real(0);
+        const Real lx1 = stay ? lxs[k] + ls1 : Real(0);
         const Real lu1 = stay ? lus[k] : Real(0);
-        Real lx0 = fin ? lx1 - ls[c0] : Real(0);
+        Real lx0 = fin ? lx1 - ls0 : Real(0);
         // (a3) x1 = x0 + (u1 / gamma) cfl, d(u1 / gamma)/du1 = gamma^-3
         const Real ig = r_div(Real(1), g);
         const Real lu0 = fin ? lu1 + lx1 * cfl * (ig * ig * ig) : Real(0);
@@ -200,7 +203,7 @@ __device__ __forceinline__ void adj_push_fix32_tile(const AdjPushFixArgs& a, lon
         const unsigned h = U + half;
         const unsigned m = h >> fb;
         const float f = __uint2float_rn(h & mask) * scale;
-        const float2 e = tab[m];
+        const float2 e = checked_index(m, nz + 1, a.flags) ? tab[m] : float2{};
         const float ep = (1.0f - f) * e.x + f * e.y;
         const float u1 = us[k] - ep * dt;
         const float g = __fsqrt_rn(1.0f + u1 * u1);
@@ -211,9 +214,11 @@ __device__ __forceinline__ void adj_push_fix32_tile(const AdjPushFixArgs& a, lon
         const bool stay = fin & (X1 >= 0) & (X1 < top);
         const int c1 = stay ? static_cast<int>(X1 >> fb) : 0;
         const int c0 = static_cast<int>(U >> fb);
-        const float lx1 = stay ? lxs[k] + ls[c1] : 0.0f;
+        const float ls1 = checked_index(c1, nz, a.flags) ? ls[c1] : 0.0f;
+        const float ls0 = checked_index(c0, nz, a.flags) ? ls[c0] : 0.0f;
+        const float lx1 = stay ? lxs[k] + ls1 : 0.0f;
         const float lu1 = stay ? lus[k] : 0.0f;
-        float lx0 = fin ? lx1 - ls[c0] : 0.0f;
+        float lx0 = fin ? lx1 - ls0 : 0.0f;
         const float ig = __fdiv_rn(1.0f, g);
         const float lu0 = fin ? lu1 + lx1 * cfl * (ig * ig * ig) : 0.0f;
         const float lep = -dt * lu0;

@@ -184,6 +184,7 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
             pa.ls_tab = reinterpret_cast<const float*>(A->ls_tab);
             pa.lez = A->lez;
             pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
+            pa.flags = &t->st->flags;
             pa.nz = A->nz;
             pa.fb = t->fb;
             pa.dt = static_cast<float>(t->d.dt);
@@ -201,6 +202,7 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
             pa.ls_tab = reinterpret_cast<const Real*>(A->ls_tab);
             pa.lez = A->lez;
             pa.log = A->seglog + static_cast<int64_t>(kLogStride) * k;
+            pa.flags = &t->st->flags;
             pa.nz = A->nz;
             pa.nzf = static_cast<Real>(A->nz);
             pa.dt = static_cast<Real>(t->d.dt);

@@ -41,6 +41,7 @@ struct TileCtx {
     long long* ids;
     const typename PairOf<Real>::T* tab;
     AccT* jacc;
+    unsigned int* flags;       // the tube's status word (bounds-checked builds)
     long long n_slots, n_tot, id0;
     Real nzf, dt, cfl;
     int nz;
@@ -107,7 +108,8 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
         const Real h = xx + Real(0.5);
         const Real mf = r_floor(h);
         const Real f = h - mf;
-        const Pair e = tab[static_cast<int>(mf)];
+        const int m = static_cast<int>(mf);
+        const Pair e = checked_index(m, nz + 1, c.flags) ? tab[m] : Pair{};
         const Real ep = (Real(1) - f) * e.x + f * e.y;
         // (a3) Eq. 1, q/m = -1, c = 1
         const Real u1 = us[k] - ep * dt;
@@ -139,7 +141,7 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
                         if (q1 != AccT(0)) acc_add(jacc + c1, q1);
                     }
                 }
-                if (qa != AccT(0)) acc_add(jacc + c0, qa);
+                if (qa != AccT(0) && checked_index(c0, nz, c.flags)) acc_add(jacc + c0, qa);
                 // (a5) removal at the ends; base-cell weight for the next injection
                 if (x1 >= Real(0) && x1 < nzf) {
                     xs[k] = x1;
@@ -163,9 +165,16 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
             vstore(c.uo + i0 + v, us + v);
         }
     }
-    warp_flush<AccT>(rkey >= Real(0) ? static_cast<int>(rkey) : -1, ra, jacc);
-    if constexpr (kTwoRuns)
-        warp_flush<AccT>(rkey2 >= Real(0) && rkey2 != rkey ? static_cast<int>(rkey2) : -1, rb, jacc);
+    const int key = rkey >= Real(0) ? static_cast<int>(rkey) : -1;
+    if constexpr (kChecked)
+        if (ra != AccT(0) && !checked_index(key, nz, c.flags)) ra = AccT(0);
+    warp_flush<AccT>(key, ra, jacc);
+    if constexpr (kTwoRuns) {
+        const int key2 = rkey2 >= Real(0) && rkey2 != rkey ? static_cast<int>(rkey2) : -1;
+        if constexpr (kChecked)
+            if (rb != AccT(0) && !checked_index(key2, nz, c.flags)) rb = AccT(0);
+        warp_flush<AccT>(key2, rb, jacc);
+    }
 }
 
 // Injection bookkeeping of a step: the requested count (the tube's own, or
@@ -209,6 +218,7 @@ push_kernel(const PushArgs<Real> a) {
     c.ids = a.ids;
     c.tab = reinterpret_cast<const typename PairOf<Real>::T*>(a.ez2);
     c.jacc = static_cast<AccT*>(a.jacc);
+    c.flags = &st->flags;
     c.n_slots = st->n_slots;
     c.n_tot = c.n_slots + n_inj;
     c.id0 = st->total_injected;
@@ -298,6 +308,7 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         c.ids = d.ids;
         c.tab = reinterpret_cast<const float2*>(d.ez2);
         c.jacc = d.jacc;
+        c.flags = &d.st->flags;
         c.id0 = d.id0;
         c.nzf = d.nzf;
         c.dt = d.dt;
@@ -340,6 +351,7 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
         c.ids = kc.ids;
         c.tab = reinterpret_cast<const float2*>(kc.ez2);
         c.jacc = kc.jacc;
+        c.flags = &kc.st->flags;
         c.id0 = d.id0;
         c.nzf = kc.nzf;
         c.dt = kc.dt;

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
             // (a2) h = X + 2^(fb-1): m = h >> fb, f = (h mod 2^fb) 2^-fb
             const unsigned h = U + half;
             const float f = __uint2float_rn(h & mask) * scale;
-            const float2 e = tab[h >> fb];
+            const unsigned m = h >> fb;
+            const float2 e = checked_index(m, nz + 1, &st->flags) ? tab[m] : float2{};
             const float ep = (1.0f - f) * e.x + f * e.y;
             // (a3) Eq. 1, then the displacement on the 2^-fb grid
             const float u1 = us[k] - ep * dt;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
                     const long long f0a = min(max(static_cast<long long>(XX) - b0, 0LL), one);
                     const long long f1a = min(max(X1 - b0, 0LL), one);
                     const long long qa = shl_signed(f1a - f0a, sh);
-                    if (qa) acc_add(jacc + c0, qa);
+                    if (qa && checked_index(c0, nz, &st->flags)) acc_add(jacc + c0, qa);
                     if (c1 != static_cast<long long>(c0) && c1 >= 0 && c1 < nz) {
                         const long long b1 = c1 << fb;
                         const long long f0b = min(max(static_cast<long long>(XX) - b1, 0LL), one);
@@ -150,8 +151,13 @@ __global__ void __launch_bounds__(kThreads) push_fix32_kernel(const PushFixArgs 
             }
         }
         const int key = rkey == 0xffffffffu ? -1 : static_cast<int>(rkey);
+        const int key2 = key >= 0 && key + 1 < nz ? key + 1 : -1;
+        if constexpr (kChecked) {
+            if (ra != 0 && !checked_index(key, nz, &st->flags)) ra = 0;
+            if (rb != 0 && !checked_index(key2, nz, &st->flags)) rb = 0;
+        }
         warp_flush<long long>(key, shl_signed(ra, sh), jacc);
-        warp_flush<long long>(key >= 0 && key + 1 < nz ? key + 1 : -1, shl_signed(rb, sh), jacc);
+        warp_flush<long long>(key2, shl_signed(rb, sh), jacc);
     }
 
     __shared__ long long s_w0[kThreads / 32], s_rm[kThreads / 32];

@@ -211,6 +211,7 @@ struct AdjPushArgs {
     const Real* ls_tab;        // (s/dt) lambda_J per cell
     double* lez;               // nz cells: the gather's share is added
     const long long* log;      // the step's kLogStride log entries
+    unsigned int* flags;       // the tube's status word (bounds-checked builds)
     int nz;
     Real nzf, dt, cfl;
 };
@@ -226,6 +227,7 @@ struct AdjPushFixArgs {
     const float* ls_tab;
     double* lez;
     const long long* log;
+    unsigned int* flags;       // the tube's status word (bounds-checked builds)
     int nz, fb;
     float dt, cfl, scale, two_fb;
 };

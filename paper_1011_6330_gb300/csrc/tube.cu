@@ -917,6 +917,7 @@ int tube_check(tube_t t) {
     tube_stats s;
     const int rc = tube_status(t, &s);
     if (rc) return rc;
+    if (s.flags & SCLF_FLAG_BOUNDS) return SCLF_EBOUNDS;
     if (s.flags & SCLF_FLAG_TIMEOUT) return SCLF_ETIMEOUT;
     if (s.flags & SCLF_FLAG_NONFINITE) return SCLF_ENONFINITE;
     if (s.flags & SCLF_FLAG_CAPACITY) return SCLF_ECAPACITY;
@@ -978,11 +979,18 @@ const char* tube_strerror(int code) {
         case SCLF_ENONFINITE: return "non-finite particle state";
         case SCLF_ETIMEOUT: return "device-side wait timed out";
         case SCLF_ESTATE: return "invalid state for this call";
+        case SCLF_EBOUNDS: return "index out of bounds (bounds-checked build)";
         default: return "unknown error";
     }
 }
 
-const char* tube_version(void) { return "sclf_tube 0.1.0 sm_103a"; }
+const char* tube_version(void) {
+#ifdef SCLF_CHECKED
+    return "sclf_tube 0.1.0 sm_103a bounds-checked";
+#else
+    return "sclf_tube 0.1.0 sm_103a";
+#endif
+}
 
 }  // extern "C"
 

@@ -31,9 +31,24 @@ def test_every_declared_function_is_exported(lib):
 
 def test_version_and_error_strings(lib):
     assert b"sm_103a" in lib.tube_version()
-    for code in range(0, -8, -1):
-        assert lib.tube_strerror(code)
+    assert b"bounds-checked" not in lib.tube_version()
+    for code in range(0, -9, -1):
+        assert lib.tube_strerror(code) and lib.tube_strerror(code) != b"unknown error"
     assert lib.tube_strerror(-99) == b"unknown error"
+
+
+def test_bounds_checked_build_exports_the_same_calls(lib):
+    """libsclf_tube_checked.so (-DSCLF_CHECKED) exports every declared call
+    and says what it is."""
+    import ctypes
+    if not os.path.exists(B.LIB_CHECKED_PATH):
+        from paper_1011_6330_gb300 import build
+        build.build(checked=True)
+    chk = ctypes.CDLL(B.LIB_CHECKED_PATH)
+    for n in B.header_functions():
+        assert hasattr(chk, n), n
+    chk.tube_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in chk.tube_version()
 
 
 def test_defaults_are_the_standard_pulsar(lib):

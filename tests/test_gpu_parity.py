@@ -810,6 +810,43 @@ def test_diagnostics_match_the_oracle(gpu_lib):
     t.close()
 
 
+def test_bounds_checked_build_flags_nothing_and_changes_nothing(gpu_lib, tmp_path):
+    """The bounds-checked build (every data-dependent index in the particle,
+    batch and adjoint kernels tested before the access) runs the edge-heavy
+    cases of tests/checked_worker.py -- particles on cell and tube
+    boundaries, at rest and at gamma ~ 1e7 in both directions, compaction,
+    re-sorts, both batch run shapes, the float32 and fixed-point adjoint --
+    without setting SCLF_FLAG_BOUNDS, and gives every result bit for bit as
+    the normal build does."""
+    import os
+    import subprocess
+    import sys
+    if not os.path.exists(B.LIB_CHECKED_PATH):
+        from paper_1011_6330_gb300 import build
+        build.build(checked=True)
+    worker = os.path.join(os.path.dirname(os.path.abspath(__file__)), "checked_worker.py")
+    res = {}
+    for name, lib in (("plain", B.LIB_PATH), ("checked", B.LIB_CHECKED_PATH)):
+        out = tmp_path / (name + ".npz")
+        r = subprocess.run([sys.executable, worker, str(out)], capture_output=True, text=True,
+                           env=dict(os.environ, SCLF_TUBE_LIB=lib), timeout=900)
+        assert r.returncode == 0, r.stderr[-3000:]
+        res[name] = np.load(out)
+    plain, checked = res["plain"], res["checked"]
+    assert "bounds-checked" in str(checked["version"])
+    assert "bounds-checked" not in str(plain["version"])
+    assert set(plain.files) == set(checked.files)
+    n_flags = 0
+    for k in plain.files:
+        if k == "version":
+            continue
+        if k.endswith("_flags"):
+            n_flags += 1
+            assert int(checked[k][0]) & B.FLAG_BOUNDS == 0, k
+        assert np.array_equal(plain[k], checked[k]), k
+    assert n_flags == 9
+
+
 def test_bounded_wait_gives_up_and_the_context_stays_usable(gpu_lib):
     """The compaction look-back's wait is bounded: with the first tile's state
     withheld (a flag nothing sets) the second tile gives up, the device reports
