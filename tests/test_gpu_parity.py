@@ -816,8 +816,10 @@ def test_bounds_checked_build_flags_nothing_and_changes_nothing(gpu_lib, tmp_pat
     cases of tests/checked_worker.py -- particles on cell and tube
     boundaries, at rest and at gamma ~ 1e7 in both directions, compaction,
     re-sorts, both batch run shapes, the float32 and fixed-point adjoint --
-    without setting SCLF_FLAG_BOUNDS, and gives every result bit for bit as
-    the normal build does."""
+    without setting SCLF_FLAG_BOUNDS, and gives every result the normal
+    build gives: bit for bit, except sums whose FP64 atomic additions may
+    come in another order in any two runs (the adjoint gradients, the
+    FP64-atomic current), which agree norm-wise."""
     import os
     import subprocess
     import sys
@@ -843,7 +845,14 @@ def test_bounds_checked_build_flags_nothing_and_changes_nothing(gpu_lib, tmp_pat
         if k.endswith("_flags"):
             n_flags += 1
             assert int(checked[k][0]) & B.FLAG_BOUNDS == 0, k
-        assert np.array_equal(plain[k], checked[k]), k
+        # sums taken by FP64 atomics (the adjoint's lambda_E, the FP64-atomic
+        # current) depend on the order of the additions, in any two runs
+        if k.startswith("adj") and ("_drho" in k or "_ds" in k):
+            assert rel(checked[k], plain[k]) < 1e-9, k
+        elif k.startswith("fp32acc_") and k.split("_")[1] in ("ez", "er", "b", "j", "x", "u"):
+            assert rel(checked[k].astype(np.float64), plain[k].astype(np.float64)) < 1e-5, k
+        else:
+            assert np.array_equal(plain[k], checked[k]), k
     assert n_flags == 9
 
 
