@@ -824,14 +824,17 @@ def main():
         h0 = time.perf_counter()
         lib.tube_load_particles(t.h, pin_x.numel(), C.c_void_p(pin_x.data_ptr()),
                                 C.c_void_p(pin_u.data_ptr()), None)
-        n_e2e = 0
+        tickets = []
         for _ in range(ksteps):
-            st = t.status()                              # per-step D2H of the counters
-            n_e2e += st["n_particles"] + st["pending_injection"]
+            tickets.append(t.status_async())             # per-step D2H of the counters
             t.step()
         cap = out_x.numel()
         rc = lib.tube_save_particles(t.h, cap, C.byref(nout), C.c_void_p(out_x.data_ptr()),
                                      C.c_void_p(out_u.data_ptr()), None)
+        n_e2e = 0
+        for k in tickets:                                # every step's counters on the host
+            st = t.status_collect(k)
+            n_e2e += st["n_particles"] + st["pending_injection"]
         torch.cuda.synchronize()
         el_e2e = time.perf_counter() - h0
         n_all, el_e2e = combine_ranks(n_e2e, el_e2e, device="cuda")
@@ -839,9 +842,10 @@ def main():
         e2e = {"value": n_all / el_e2e, "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / ksteps,
                "d2h_bytes_per_step": (state_bytes * min(cap, nout.value) / max(cap, 1)
-                                      + ksteps * 88) / ksteps,
-               "path": "tube_load_particles(pinned) + K x (tube_status, tube_step) + "
-                       "tube_save_particles(pinned)", "rc": int(rc)}
+                                      + ksteps * 144) / ksteps,   # 144-byte counter block
+               "path": "tube_load_particles(pinned) + K x (tube_status_async, tube_step) + "
+                       "tube_save_particles(pinned) + K x tube_status_collect",
+               "rc": int(rc)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -280,6 +280,16 @@ int tube_solve_fields(tube_t t);
  * are set; tube_check() turns flags into an error code. */
 int tube_status(tube_t t, tube_stats* out);
 
+/* Pipelined status: queue a copy of the counters as they stand after the
+ * work queued so far (the same fields tube_status gives) into a pinned ring
+ * the tube owns, without waiting; *ticket names it. tube_status_collect
+ * synchronises the tube's stream and writes that copy to out (caller-owned
+ * host memory). A ticket stays valid for the next 1023 tube_status_async
+ * calls on the tube; an older, future or unknown ticket returns SCLF_EINVAL.
+ * The ring (256 KB of pinned host memory) is allocated on the first call. */
+int tube_status_async(tube_t t, int64_t* ticket);
+int tube_status_collect(tube_t t, int64_t ticket, tube_stats* out);
+
 /* SCLF_OK, or the error code of the most severe sticky flag. Synchronises. */
 int tube_check(tube_t t);
 

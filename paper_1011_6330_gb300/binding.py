@@ -96,6 +96,8 @@ SIGNATURES = {
     "tube_load_particles": (_i32, [_vp, _i64, _vp, _vp, _pi64]),
     "tube_solve_fields": (_i32, [_vp]),
     "tube_status": (_i32, [_vp, C.POINTER(TubeStats)]),
+    "tube_status_async": (_i32, [_vp, C.POINTER(_i64)]),
+    "tube_status_collect": (_i32, [_vp, _i64, C.POINTER(TubeStats)]),
     "tube_check": (_i32, [_vp]),
     "tube_diagnostics": (_i32, [_vp, C.POINTER(TubeDiag)]),
     "tube_compact": (_i32, [_vp]),
@@ -341,6 +343,18 @@ class Tube:
     def status(self):
         s = TubeStats()
         _check(self.lib.tube_status(self.h, C.byref(s)), "tube_status")
+        return {n: getattr(s, n) for n, _ in TubeStats._fields_}
+
+    def status_async(self):
+        """Queue a copy of the counters (pipelined, no wait); returns a ticket
+        for status_collect."""
+        k = C.c_int64()
+        _check(self.lib.tube_status_async(self.h, C.byref(k)), "tube_status_async")
+        return k.value
+
+    def status_collect(self, ticket):
+        s = TubeStats()
+        _check(self.lib.tube_status_collect(self.h, int(ticket), C.byref(s)), "tube_status_collect")
         return {n: getattr(s, n) for n, _ in TubeStats._fields_}
 
     def check(self):

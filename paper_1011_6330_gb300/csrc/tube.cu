@@ -339,6 +339,24 @@ int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int
 
 }  // namespace
 
+namespace {
+
+// The public view of the device counters.
+void stats_from_state(const DevState& h, tube_stats* out) {
+    out->step = h.step;
+    out->n_particles = h.n_live;
+    out->n_slots = h.n_slots;
+    out->total_injected = h.total_injected;
+    out->last_injected = h.last_injected;
+    out->last_removed = h.last_removed;
+    out->pending_injection = h.n_inj;
+    out->surface_field = h.surface_field;
+    out->flags = h.flags;
+    out->reserved = 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 int tube_params_default(tube_params* p) {
@@ -510,6 +528,7 @@ int tube_destroy(tube_t t) {
     }
     if (t->owns_ws && t->ws) cudaFree(t->ws);
     if (t->sort_ws) cudaFree(t->sort_ws);
+    if (t->status_ring) cudaFreeHost(t->status_ring);
     delete t;
     return SCLF_OK;
 }
@@ -900,16 +919,33 @@ int tube_status(tube_t t, tube_stats* out) {
     DevState h;
     const int rc = read_state(t, &h);
     if (rc) return rc;
-    out->step = h.step;
-    out->n_particles = h.n_live;
-    out->n_slots = h.n_slots;
-    out->total_injected = h.total_injected;
-    out->last_injected = h.last_injected;
-    out->last_removed = h.last_removed;
-    out->pending_injection = h.n_inj;
-    out->surface_field = h.surface_field;
-    out->flags = h.flags;
-    out->reserved = 0;
+    stats_from_state(h, out);
+    return SCLF_OK;
+}
+
+int tube_status_async(tube_t t, int64_t* ticket) {
+    if (!t || !ticket) return SCLF_EINVAL;
+    if (!t->status_ring) {
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(DevState) * sclf_tube::kStatusRing, cudaHostAllocDefault) !=
+            cudaSuccess)
+            return SCLF_ENOMEM;
+        t->status_ring = static_cast<DevState*>(p);
+    }
+    const int64_t k = t->status_next;
+    CK(cudaMemcpyAsync(t->status_ring + k % sclf_tube::kStatusRing, t->st, sizeof(DevState),
+                       cudaMemcpyDeviceToHost, t->stream));
+    t->status_next = k + 1;
+    *ticket = k;
+    return SCLF_OK;
+}
+
+int tube_status_collect(tube_t t, int64_t ticket, tube_stats* out) {
+    if (!t || !out || !t->status_ring || ticket < 0 || ticket >= t->status_next ||
+        ticket < t->status_next - sclf_tube::kStatusRing)
+        return SCLF_EINVAL;
+    CK(cudaStreamSynchronize(t->stream));
+    stats_from_state(t->status_ring[ticket % sclf_tube::kStatusRing], out);
     return SCLF_OK;
 }
 

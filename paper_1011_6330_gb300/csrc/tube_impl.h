@@ -77,6 +77,11 @@ struct sclf_tube {
     int steps_since_sort = 0;
     bool owned = false;                // stepped by a batch or an adjoint driver,
                                        // not by tube_step / tube_run
+    // tube_status_async: copies of the device counters in a pinned ring
+    // (allocated on first use), slot = ticket mod kStatusRing
+    static constexpr int64_t kStatusRing = 1024;
+    sclf::DevState* status_ring = nullptr;
+    int64_t status_next = 0;
 };
 
 namespace sclf {

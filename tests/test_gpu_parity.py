@@ -236,6 +236,32 @@ def test_inject_call_save_load_and_invalid_input(gpu_lib):
     t.close()
 
 
+def test_pipelined_status_matches_the_blocking_read(gpu_lib):
+    """tube_status_async queues a copy of the counters without waiting;
+    tube_status_collect returns exactly what tube_status read at that point,
+    and rejects tickets not yet issued or already overwritten in the ring."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    t = B.Tube(B.default_params(**kw))
+    z, u = synth.prefilled_beam(5000, 7.9, 5.0, seed=3)
+    t.add_particles(z, u)
+    t.solve_fields()
+    tickets, direct = [], []
+    for _ in range(12):
+        tickets.append(t.status_async())
+        direct.append(t.status())
+        t.step()
+    for k, st in zip(tickets, direct):
+        assert t.status_collect(k) == st
+    for bad in (-1, tickets[-1] + 1):
+        with pytest.raises(B.SclfError):
+            t.status_collect(bad)
+    last = [t.status_async() for _ in range(1024)][-1]
+    with pytest.raises(B.SclfError):
+        t.status_collect(tickets[0])              # overwritten in the 1024-entry ring
+    assert t.status_collect(last) == t.status()
+    t.close()
+
+
 def test_save_with_holes_compacts_and_keeps_id_order(gpu_lib):
     """Saving a tube whose slots hold holes (particles that left) returns the
     live particles in ID order (a device-side compaction), the same as
