@@ -34,12 +34,14 @@ def _rank(rank, world, port, out):
                  accumulate="fixed")
     z, u = synth.random_particles(500, L, seed=bench.rank_seed(rank))
     t.add_particles(z, u)
+    bench.barrier(world)                                 # as around bench.py's timed region
     t0 = time.perf_counter()
     work = 0
     for _ in range(20):
         work += t.xi.size + t.injection_count()
         t.step()
     secs = time.perf_counter() - t0 + 0.01 * rank       # ranks differ in time
+    bench.barrier(world)
     total, slowest = bench.combine_ranks(work, secs)
     out[rank] = (work, secs, total, slowest, t.total_injected, float(t.ez.sum()))
     dist.destroy_process_group()
@@ -60,4 +62,6 @@ def test_two_ranks_run_independent_tubes_and_combine_totals():
 def test_single_process_combine_is_identity():
     import bench
     assert bench.combine_ranks(123.0, 4.5) == (123.0, 4.5)
+    bench.barrier(1)                                     # no process group needed on one GPU
+    assert bench.gr_workload_name(10 ** 8) == "gr_tube_P0.5s_B1e12G_Nz65536_1e+08_particles_fp32"
     assert len({bench.rank_seed(r) for r in range(8)}) == 8
