@@ -584,6 +584,60 @@ def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
         t.close()
 
 
+def _binned_profiles(z, u, ez, L, nb=32):
+    """Mean gamma per height bin, E_z averaged over each bin's cells, and the
+    particle count per bin."""
+    edges = np.linspace(0.0, L, nb + 1)
+    idx = np.clip(np.digitize(z, edges) - 1, 0, nb - 1)
+    cnt = np.bincount(idx, minlength=nb)
+    g = np.sqrt(1.0 + np.asarray(u, np.float64) ** 2)
+    gm = np.bincount(idx, weights=g, minlength=nb) / np.maximum(cnt, 1)
+    return gm, np.asarray(ez).reshape(nb, -1).mean(axis=1), cnt
+
+
+def test_long_run_profiles_against_the_fp64_oracle(gpu_lib):
+    """Config 1 (flat SCLF tube, empty start) for its full 2000 steps, with
+    FP64 and with FP32 particles, against the FP64 oracle: the binned gamma(z)
+    and E_z(z) profiles, the particle count per bin, and the first step where
+    the injection counts part (FP32 ones part near step 1160; the float32
+    oracle mirror shows the same: its binned gamma stays within 7e-6 and its
+    binned E_z within 1.5e-5 of FP64)."""
+    nsteps = 2000
+    kw64 = workloads.flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FIXED64)
+    L, nz = kw64["L_over_R"], kw64["Nz"]
+    d = B.derive(B.default_params(**kw64))
+    o = orc.Tube(nz, L, d["dt"], -np.ones(nz + 1), d["s"], precision="f64", accumulate="fixed")
+    inj_o = []
+    for _ in range(nsteps):
+        o.step()
+        inj_o.append(o.last_injected)
+    go, eo, co = _binned_profiles(o.z(), o.u, o.ez, L)
+    occ = co > 0
+    # (gamma bins, binned E_z, full E_z, per-bin count) bounds per precision
+    tol = {B.SCLF_FP64: (1e-5, 1e-4, 1e-3, 0), B.SCLF_FP32: (1e-4, 1e-3, 1e-2, 0.01)}
+    for prec in (B.SCLF_FP64, B.SCLF_FP32):
+        t = B.Tube(B.default_params(**workloads.flat_sclf_small(
+            precision=prec, accumulate=B.SCLF_ACC_FIXED64)))
+        inj = []
+        for _ in range(nsteps):
+            t.step()
+            inj.append(t.status()["last_injected"])
+        z, u, _ = t.read_particles()
+        f = t.read_fields(rho=False)
+        g, e, c = _binned_profiles(z, u, f["ez"], L)
+        part = np.nonzero(np.array(inj) != np.array(inj_o))[0]
+        eg = float(np.max(np.abs(g[occ] - go[occ]) / go[occ]))
+        ee = float(np.max(np.abs(e - eo)) / np.max(np.abs(eo)))
+        ef = rel(f["ez"], o.ez)
+        ec = float(np.max(np.abs(c - co))) / float(np.max(co))
+        print("precision %d: injections part at step %s; gamma bins %.2g, E_z bins %.2g, "
+              "E_z %.2g, counts %.2g" % (prec, part[0] if part.size else None, eg, ee, ef, ec))
+        tg, te, tf, tc = tol[prec]
+        assert eg <= tg and ee <= te and ef <= tf and ec <= tc
+        assert np.array_equal(c > 0, occ)
+        t.close()
+
+
 @pytest.mark.parametrize("variant,alpha,tables", [(B.SCLF_GR_BOTH, 0, False),
                                                   (B.SCLF_GR_COS, 1, True)])
 def test_eq6_variant_tube_matches_oracle(gpu_lib, variant, alpha, tables):
