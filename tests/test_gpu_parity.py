@@ -599,9 +599,10 @@ def test_long_run_profiles_against_the_fp64_oracle(gpu_lib):
     """Config 1 (flat SCLF tube, empty start) for its full 2000 steps, with
     FP64 and with FP32 particles, against the FP64 oracle: the binned gamma(z)
     and E_z(z) profiles, the particle count per bin, and the first step where
-    the injection counts part (FP32 ones part near step 1160; the float32
-    oracle mirror shows the same: its binned gamma stays within 7e-6 and its
-    binned E_z within 1.5e-5 of FP64)."""
+    the injection counts part. Observed: FP64 never parts, profiles within
+    ~1e-11 and E_z within 4e-10; FP32 parts at step 1161 with binned gamma
+    6.7e-6, binned E_z 1.4e-5 and E_z 1.8e-4 -- the float32 oracle mirror's
+    own figures, as it is bit-identical to the GPU run."""
     nsteps = 2000
     kw64 = workloads.flat_sclf_small(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FIXED64)
     L, nz = kw64["L_over_R"], kw64["Nz"]
@@ -614,7 +615,7 @@ def test_long_run_profiles_against_the_fp64_oracle(gpu_lib):
     go, eo, co = _binned_profiles(o.z(), o.u, o.ez, L)
     occ = co > 0
     # (gamma bins, binned E_z, full E_z, per-bin count) bounds per precision
-    tol = {B.SCLF_FP64: (1e-5, 1e-4, 1e-3, 0), B.SCLF_FP32: (1e-4, 1e-3, 1e-2, 0.01)}
+    tol = {B.SCLF_FP64: (1e-8, 1e-8, 1e-7, 0), B.SCLF_FP32: (1e-4, 1e-3, 1e-2, 0.01)}
     for prec in (B.SCLF_FP64, B.SCLF_FP32):
         t = B.Tube(B.default_params(**workloads.flat_sclf_small(
             precision=prec, accumulate=B.SCLF_ACC_FIXED64)))
