@@ -74,6 +74,15 @@ def test_gr_workload_units(lib):
     assert abs(d["rho0"] / z0 - 1) < 1e-13
     assert d["s"] == pytest.approx(-abs(z0) * d["L"] / 1e8, rel=1e-13)
     assert 0 < d["dt"] < d["dz"]
+    # the oracle's own dt rule and macro charge give the numbers the parity
+    # tests hand to both sides
+    L_o = 2.0 / cu["theta_p"]
+    assert d["dt"] == pytest.approx(orc.default_dt(L_o / 65536, cu["Lambda0"]), rel=1e-12)
+    assert d["s"] == pytest.approx(orc.macro_charge_for(z0, L_o, 10 ** 8), rel=1e-12)
+    kw1 = workloads.flat_sclf_small()
+    d1 = B.derive(B.default_params(**kw1))
+    assert d1["dt"] == pytest.approx(0.4 * 8.0 / 1024, rel=1e-15)
+    assert d1["s"] == pytest.approx(orc.macro_charge_for(-1.0, 8.0, 50000), rel=1e-12)
 
 
 def test_invalid_parameters_are_rejected(lib):
