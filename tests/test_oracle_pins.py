@@ -562,3 +562,178 @@ def test_float32_mode_long_run_profiles_stay_close_to_float64():
     ea, eb = a.ez.reshape(nb, -1).mean(axis=1), b.ez.reshape(nb, -1).mean(axis=1)
     assert np.max(np.abs(eb - ea)) / np.max(np.abs(ea)) < 1e-3
     assert np.max(np.abs(b.ez - a.ez)) / np.max(np.abs(a.ez)) < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4 with the particles' charge (Tube.solve_fields, rho_nodes) and the
+# sin i term of Eq. 5, each against numbers fixed outside the oracle
+# ---------------------------------------------------------------------------
+
+def _slab_tube(nz, L=8.0, a=2.0, b=5.0, per_cell=4, s=-1e-3):
+    """A tube with no rho_GJ and a uniform slab of charge on [a, b]:
+    per_cell particles at the mid-points of per_cell equal sub-intervals of
+    every cell inside the slab, so the cloud-in-cell density is s per_cell / dz
+    on the slab's interior nodes and half that on its two edge nodes."""
+    dz = L / nz
+    t = orc.Tube(nz, L, 0.4 * dz, np.zeros(nz + 1), s)
+    ja, jb = int(round(a / dz)), int(round(b / dz))
+    cells = np.arange(ja, jb)
+    sub = (np.arange(per_cell) + 0.5) / per_cell
+    z = ((cells[:, None] + sub[None, :]) * dz).ravel()
+    t.add_particles(z, np.zeros(z.size))
+    return t, s * per_cell / dz
+
+
+def _slab_closed_form(z, rho0, L, a, b):
+    """phi and phi' of phi'' - phi = -4 pi rho (R = 1) with rho = rho0 on
+    [a, b] and 0 elsewhere, phi(0) = 0, phi'(L) = 0, from the Green's function
+    -sinh(z_<) cosh(L - z_>) / cosh(L) of that operator and those boundary
+    conditions, integrated over the slab by hand."""
+    c = 4.0 * math.pi * rho0 / math.cosh(L)
+    z = np.asarray(z, np.float64)
+    lo, hi = z < a, z > b
+    mid = ~(lo | hi)
+    phi = np.empty_like(z)
+    dphi = np.empty_like(z)
+    phi[lo] = c * np.sinh(z[lo]) * (math.sinh(L - a) - math.sinh(L - b))
+    dphi[lo] = c * np.cosh(z[lo]) * (math.sinh(L - a) - math.sinh(L - b))
+    phi[hi] = c * np.cosh(L - z[hi]) * (math.cosh(b) - math.cosh(a))
+    dphi[hi] = -c * np.sinh(L - z[hi]) * (math.cosh(b) - math.cosh(a))
+    zm = z[mid]
+    phi[mid] = c * (np.cosh(L - zm) * (np.cosh(zm) - math.cosh(a))
+                    + np.sinh(zm) * (np.sinh(L - zm) - math.sinh(L - b)))
+    dphi[mid] = c * (np.sinh(L - zm) * math.cosh(a) - np.cosh(zm) * math.sinh(L - b))
+    return phi, dphi
+
+
+def _slab_errors(nz, L=8.0, a=2.0, b=5.0):
+    """Norm-wise errors of Tube.solve_fields' E_z (cell centres) and E_r
+    (nodes) against the closed-form slab solution."""
+    t, rho0 = _slab_tube(nz, L, a, b)
+    t.solve_fields()
+    zn = np.arange(nz + 1) * t.dz
+    zc = (np.arange(nz) + 0.5) * t.dz
+    phi_n, _ = _slab_closed_form(zn, rho0, L, a, b)
+    _, dphi_c = _slab_closed_form(zc, rho0, L, a, b)
+    ez_err = np.max(np.abs(t.ez - (-dphi_c))) / np.max(np.abs(dphi_c))
+    er_err = np.max(np.abs(t.er - phi_n)) / np.max(np.abs(phi_n))
+    return ez_err, er_err
+
+
+def test_solve_fields_matches_the_closed_form_slab_second_order():
+    """Eq. 4 with the particles' charge (Sec. 2 initialisation applied to a
+    prefilled tube): for a uniform slab of charge, E_z = -phi' and E_r = phi
+    follow the closed-form solution to second order in dz."""
+    errs = [_slab_errors(nz) for nz in (128, 256, 512)]
+    assert errs[-1][0] < 2e-5 and errs[-1][1] < 2e-5
+    for k in (0, 1):
+        assert 3.5 < errs[0][k] / errs[1][k] < 4.5 and 3.5 < errs[1][k] / errs[2][k] < 4.5
+
+
+def _total_charge_error(nz=256, L=8.0, n=5000, seed=3):
+    """|sum_j rho_j dz - n s| / (n |s|) for random particles: cloud-in-cell
+    weights of one particle sum to one over its two nodes."""
+    rng = np.random.default_rng(seed)
+    s = -2e-4
+    rho = orc.sclf_oracle.rho_nodes(rng.uniform(0.0, nz - 1e-9, n), s, L / nz, nz)
+    return abs(rho.sum() * (L / nz) - n * s) / (n * abs(s))
+
+
+def test_rho_nodes_carries_the_whole_charge():
+    assert _total_charge_error() < 1e-12
+
+
+def _gauss_after_solve(nz=512, L=8.0, n=20000, seed=5):
+    """max |G_j| / scale on the interior nodes after solve_fields on a random
+    prefilled frame-dragging-like tube, G_j the discrete Gauss residual
+    (Eq. 2 with d/dr -> 1/R)."""
+    rng = np.random.default_rng(seed)
+    dz = L / nz
+    zn = np.arange(nz + 1) * dz
+    rho_gj = -(1.0 - 0.3 / (1.0 + 0.1 * zn) ** 3)
+    t = orc.Tube(nz, L, 0.4 * dz, rho_gj, orc.macro_charge_for(rho_gj[0], L, n))
+    t.add_particles(rng.uniform(0.0, L - 1e-9, n), rng.normal(0.0, 3.0, n))
+    t.solve_fields()
+    scale = 4.0 * math.pi * np.max(np.abs(t.rho_nodes() - t.rho_gj))
+    return np.max(np.abs(t.gauss_residual())) / scale
+
+
+def test_solve_fields_satisfies_gauss_on_a_random_prefilled_tube():
+    assert _gauss_after_solve() < 1e-10
+
+
+# Sec. 3: theta_p = (Omega R_* / c)^(1/2). For P = 0.5 s (Omega = 4 pi / s),
+# R_* = 1e6 cm, c = 2.99792458e10 cm/s: theta_p = 0.0204736, and theta_* =
+# 0.67 theta_p = 0.0137173 (text after Eq. 5). The Eq. 5 bracket
+# cos i + (3/2) eta^(1/2) theta_* sin i, worked by hand at these values:
+THETA_P_HALF_SECOND = 0.0204736
+EQ5_BRACKET = [              # (i [rad], eta, bracket)
+    (math.pi / 2, 1.0, 0.0205760),    # 1.5 * 1 * 0.0137173
+    (math.pi / 2, 4.0, 0.0411520),    # 1.5 * 2 * 0.0137173
+    (math.pi / 2, 2.25, 0.0308640),   # 1.5 * 1.5 * 0.0137173
+    (0.3, 1.0, 0.9614171),            # 0.9553365 + 1.5 * 1 * 0.0137173 * 0.2955202
+    (0.3, 4.0, 0.9674977),            # 0.9553365 + 1.5 * 2 * 0.0137173 * 0.2955202
+]
+
+
+def _eq5_bracket_error(profile=None, units=None):
+    """Largest relative error of the flat-space Eq. 5 bracket,
+    rho / (-Lambda0^2 / 4 pi), against the hand-worked EQ5_BRACKET."""
+    profile = profile or orc.rho_gj_profile
+    units = units or orc.code_units
+    worst = 0.0
+    for incl, eta, want in EQ5_BRACKET:
+        cu = units(1e12, 0.5, 1e6, incl, 1.4 * orc.M_SUN)
+        z = (eta - 1.0) / cu["R_over_Rstar"]
+        rho = profile(orc.RHO_FLAT, np.array([z]), cu["Lambda0"], incl, cu["theta_star"],
+                      cu["R_over_Rstar"], cu["kappa"])
+        got = float(rho[0]) / (-cu["Lambda0"] ** 2 / (4.0 * math.pi))
+        worst = max(worst, abs(got / want - 1.0))
+    return worst
+
+
+def test_eq5_sin_i_term_against_hand_worked_values():
+    cu = orc.code_units(1e12, 0.5, 1e6, 0.5, 1.4 * orc.M_SUN)
+    assert abs(cu["theta_p"] / THETA_P_HALF_SECOND - 1.0) < 5e-6
+    assert _eq5_bracket_error() < 5e-6
+
+
+def _mutant(func, *edits):
+    """A copy of an oracle function with source fragments replaced (a planted
+    mistake; edits are (old, new) pairs), compiled in the oracle module's
+    namespace."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(func))
+    for old, new in edits:
+        assert src.count(old) == 1, (func.__name__, old)
+        src = src.replace(old, new)
+    ns = dict(func.__globals__)
+    exec(compile(src, "<mutant>", "exec"), ns)
+    return ns[func.__name__]
+
+
+def test_planted_mistakes_fail_the_solve_and_eq5_pins(monkeypatch):
+    """Each pin above catches the plausible mistake it is there for."""
+    mod = orc.sclf_oracle
+    # the sign of rho in solve_fields
+    bad_solve = _mutant(mod.Tube.solve_fields, ("self.rho_gj - rho", "self.rho_gj + rho"))
+    with monkeypatch.context() as m:
+        m.setattr(mod.Tube, "solve_fields", bad_solve)
+        assert _slab_errors(256)[0] > 1e-2
+        assert _gauss_after_solve() > 1e-3
+    # a missing 1/dz in the cloud-in-cell density
+    with monkeypatch.context() as m:
+        m.setattr(mod, "rho_nodes", _mutant(mod.rho_nodes, ("s * (1.0 - w) / dz", "s * (1.0 - w)"),
+                                            ("s * w / dz", "s * w")))
+        assert _total_charge_error() > 1e-2
+        assert _slab_errors(256)[0] > 1e-2
+    # theta_p in place of theta_* in Eq. 5, and eta^(-1/2) in place of eta^(1/2)
+    with monkeypatch.context() as m:
+        m.setattr(mod, "code_units", _mutant(mod.code_units, ("theta_star=0.67 * theta_p",
+                                                              "theta_star=theta_p")))
+        assert _eq5_bracket_error(units=mod.code_units) > 1e-3
+    bad_eta = _mutant(mod.rho_gj_profile,
+                      ("bracket = math.cos(incl) + 1.5 * np.sqrt(eta) * theta_star",
+                       "bracket = math.cos(incl) + 1.5 / np.sqrt(eta) * theta_star"))
+    assert _eq5_bracket_error(profile=bad_eta) > 1e-3
