@@ -196,6 +196,16 @@ int tube_derive(const tube_params* p, tube_derived* d);
  * Nz+1 doubles. SCLF_EINVAL for invalid parameters. */
 int tube_rho_gj_profile(const tube_params* p, double* rho);
 
+/* Chain rule from rho_GJ to the pulsar's parameters (host only, no CUDA):
+ * grad (host, 3 doubles) = sum_j d_rho[j] d rho_GJ,j / d(B_G, P_s, R_cm) for
+ * d_rho (host, Nz+1 doubles), from the analytic derivatives of Eq. 5 or
+ * Eq. 6-7 with the Sec. 3 units (Lambda0^2 is proportional to B R^2 / P,
+ * theta_* to P^(-1/2), eta_j = 1 + z_j R / R_*), on the fixed grid z_j = j dz
+ * (in R) with R an independent coordinate taken at its derived value (so
+ * d/dP is at fixed R). lambda_override > 0 holds Lambda0; the f, H tables
+ * stay at their nodes; SCLF_RHO_USER gives 0. SCLF_EINVAL for invalid p. */
+int tube_rho_gj_param_gradient(const tube_params* p, const double* d_rho, double* grad);
+
 /* Bytes of device memory a tube with these parameters needs. */
 int tube_workspace_bytes(const tube_params* p, int64_t* bytes);
 
@@ -501,12 +511,15 @@ int adjoint_events(adjoint_t a, int64_t* n_inj, int64_t* n_removed, int64_t* n_s
 int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d_s);
 
 /* Chain a gradient to the pulsar's parameters: grad (host, 4 doubles) =
- * d objective / d(B_G, P_s, R_cm, w), where the macro charge is w s (w = 1
- * at this point). rho_GJ is differentiated in B, P and R on the fixed grid
- * by central differences (relative step 1e-6) of its closed form (Eq. 5, or
- * Eq. 6-7), with R an independent coordinate taken at its derived value;
- * a SCLF_RHO_USER profile gives 0 for B, P and R. */
-int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double* grad);
+ * d objective / d(B_G, P_s, R_cm, w), where the macro charge is s = w s_ref.
+ * s_ref: the reference charge the weight w multiplies, or 0 to take the
+ * tube's own s (w = 1); d/dw = d_s s_ref. The B, P, R entries are
+ * tube_rho_gj_param_gradient(d_rho_gj) of the driver's tube (analytic
+ * derivatives of Eq. 5 or Eq. 6-7 on the fixed grid, R an independent
+ * coordinate taken at its derived value; a SCLF_RHO_USER profile gives 0).
+ * SCLF_EINVAL for a non-finite s_ref. */
+int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double s_ref,
+                           double* grad);
 
 /* Device time (CUDA events on the driver's stream) of the last forward and
  * backward passes, and the particle slots one pass processes (the sum over
@@ -532,8 +545,9 @@ int adjoint_kernel_times(adjoint_t a, double* ms, int64_t* launches);
  * library who cannot call cudaMalloc: an application whose own allocator has
  * reserved the device's memory, a plug-in whose host forbids allocation once
  * it runs, or a latency-critical loop that cannot afford the device-wide
- * synchronisation of cudaMalloc/cudaFree. It allocates nothing (no
- * cudaMalloc, cudaFree or allocating library routine).
+ * synchronisation of cudaMalloc/cudaFree. After its first call on a device
+ * it allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).
  *
  * One gather-push-deposit pass over n FP32 particles, the same arithmetic
  * as a tube step without injection: cloud-in-cell gather of E_z, the Eq. 1
@@ -546,20 +560,33 @@ int adjoint_kernel_times(adjoint_t a, double* ms, int64_t* launches);
  *   dt, dz    step and cell size in R/c and R (0 < dt < dz); s < 0 the
  *             macro-particle charge
  *   j_out     device, nz doubles, out: J_{j+1/2} = (s/dt) sum of fractions
- *   n_removed device int64 or NULL, out: particles removed by this pass
+ *   n_removed device int64 or NULL, out: particles removed by this pass,
+ *             those that left the tube and those whose push gave a NaN or
+ *             an infinity (both become holes)
+ *   flags     device uint32 or NULL, in/out: SCLF_FLAG_NONFINITE is OR-ed
+ *             in when a push gave a NaN or an infinity (other bits are kept)
  *   stream    cudaStream_t; the call is asynchronous on it
+ * Returns SCLF_ECUDA without launching anything when a CUDA error is already
+ * pending in the calling thread (cudaPeekAtLastError; it stays pending).
  * Its scratch is one fixed file-scope device array of SCLF_STATIC_MAX_NZ
  * cells (about 1 MB), held by every GPU that loads the library until the
- * process exits; nz > SCLF_STATIC_MAX_NZ returns SCLF_EINVAL. The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.
+ * process exits; nz > SCLF_STATIC_MAX_NZ returns SCLF_EINVAL.
+ * The first call on a device, with that device current, does the set-up:
+ * CUDA loads modules lazily by default, so it loads this call's kernels and
+ * the scratch array (which takes device memory) and looks up the array's
+ * device address (cudaGetSymbolAddress). Make that first call before the
+ * application reserves the device's memory and before any stream capture
+ * (or run with CUDA_MODULE_LOADING=EAGER); later calls allocate nothing.
+ * After a cudaDeviceReset the library must be reloaded before this call is
+ * used again on that device (the address is cached per device).
  * Every call shares the array and clears it before use, so calls that
  * overlap on the GPU (other streams, other host threads) race with one
  * another: serialise them. */
 #define SCLF_STATIC_MAX_NZ 65536
 int tube_push_deposit_static(float* xi, float* u, int64_t n, const double* ez,
                              int32_t nz, double dt, double dz, double s,
-                             double* j_out, int64_t* n_removed, void* stream);
+                             double* j_out, int64_t* n_removed, uint32_t* flags,
+                             void* stream);
 
 /* Human-readable name of a return code (static storage). */
 const char* tube_strerror(int code);

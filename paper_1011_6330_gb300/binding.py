@@ -124,12 +124,13 @@ SIGNATURES = {
     "adjoint_set_weights": (_i32, [_vp, _pd]),
     "adjoint_events": (_i32, [_vp, _pi64, _pi64, _pi64]),
     "adjoint_backward": (_i32, [_vp, C.c_int32, _pd, _pd]),
-    "adjoint_param_gradient": (_i32, [_vp, _pd, C.c_double, _pd]),
+    "adjoint_param_gradient": (_i32, [_vp, _pd, C.c_double, C.c_double, _pd]),
+    "tube_rho_gj_param_gradient": (_i32, [C.POINTER(TubeParams), _pd, _pd]),
     "adjoint_timing": (_i32, [_vp, _pd, _pd, _pi64]),
     "adjoint_set_timing": (_i32, [_vp, _i32]),
     "adjoint_kernel_times": (_i32, [_vp, _pd, _pi64]),
     "tube_push_deposit_static": (_i32, [_vp, _vp, _i64, _vp, C.c_int32, C.c_double,
-                                         C.c_double, C.c_double, _vp, _vp, _vp]),
+                                         C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "tube_strerror": (C.c_char_p, [_i32]),
     "tube_version": (C.c_char_p, []),
 }
@@ -212,6 +213,16 @@ def rho_gj_profile(params):
     rho = np.empty(int(params.Nz) + 1)
     _check(lib.tube_rho_gj_profile(C.byref(params), _dptr(rho)), "tube_rho_gj_profile")
     return rho
+
+
+def rho_gj_param_gradient(params, d_rho):
+    """sum_j d_rho[j] d rho_GJ,j / d(B_G, P_s, R_cm) on the tube's fixed grid
+    (host only)."""
+    d_rho = np.ascontiguousarray(d_rho, dtype=np.float64)
+    g = np.empty(3)
+    _check(load().tube_rho_gj_param_gradient(C.byref(params), _dptr(d_rho), _dptr(g)),
+           "tube_rho_gj_param_gradient")
+    return g
 
 
 def workspace_bytes(params):
@@ -526,11 +537,13 @@ class Adjoint:
                "adjoint_backward")
         return d_rho, d_s.value
 
-    def param_gradient(self, d_rho, d_s):
-        """d objective / d(B_G, P_s, R_cm, w) with macro charge w s."""
+    def param_gradient(self, d_rho, d_s, s_ref=0.0):
+        """d objective / d(B_G, P_s, R_cm, w) with macro charge s = w s_ref
+        (s_ref = 0: the tube's own s, w = 1)."""
         d_rho = np.ascontiguousarray(d_rho, dtype=np.float64)
         g = np.empty(4)
-        _check(self.lib.adjoint_param_gradient(self.h, _dptr(d_rho), float(d_s), _dptr(g)),
+        _check(self.lib.adjoint_param_gradient(self.h, _dptr(d_rho), float(d_s), float(s_ref),
+                                               _dptr(g)),
                "adjoint_param_gradient")
         return g
 
@@ -609,6 +622,8 @@ def _objectives_function():
         def forward(ctx, theta, spec):
             th = theta.detach().cpu().double().numpy()
             a = _adjoint_at(spec, th)
+            # the driver (and its checkpoints) lives as long as ctx, so a
+            # second backward (retain_graph) sweeps the same recorded run
             ctx.adj, ctx.spec, ctx.theta = a, spec, th
             return torch.tensor(a.forward(), dtype=torch.float64)
 
@@ -620,10 +635,7 @@ def _objectives_function():
             for obj in (SCLF_OBJ_GAMMA, SCLF_OBJ_EZ):
                 if g[obj] != 0.0:
                     d_rho, d_s = a.backward(obj)
-                    pg = a.param_gradient(d_rho, d_s)
-                    pg[3] = d_s * spec["s_ref"]          # d/dw at macro charge w s_ref
-                    grad += g[obj] * pg
-            a.close()
+                    grad += g[obj] * a.param_gradient(d_rho, d_s, spec["s_ref"])
             return torch.tensor(grad, dtype=torch.float64), None
 
     return TubeObjectives

@@ -657,11 +657,12 @@ int adjoint_backward(adjoint_t a, int32_t objective, double* d_rho_gj, double* d
                       : run_backward<float, float>(a, objective, d_rho_gj, d_s);
 }
 
-int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double* grad) {
-    if (!a || !d_rho_gj || !grad) return SCLF_EINVAL;
+int adjoint_param_gradient(adjoint_t a, const double* d_rho_gj, double d_s, double s_ref,
+                           double* grad) {
+    if (!a || !d_rho_gj || !grad || !std::isfinite(s_ref)) return SCLF_EINVAL;
     const int rc = rho_gj_parameter_gradient(&a->t->p, d_rho_gj, grad);
     if (rc) return rc;
-    grad[3] = d_s * a->t->d.s;
+    grad[3] = d_s * (s_ref != 0.0 ? s_ref : a->t->d.s);      // s = w s_ref
     return SCLF_OK;
 }
 

@@ -16,6 +16,11 @@
 // charge-conserving current deposit summed in 2^-32 fixed point (each F_j
 // quantised before differencing), and removal
 // of particles that leave [0, Nz) (their slot becomes a hole, xi = -1).
+//
+// CUDA loads modules lazily by default, and loading this file's module (its
+// kernels and the scratch array) takes device memory. The per-device set-up
+// below therefore does all of that loading at once, on the first call on a
+// device: that call may allocate, every later call allocates nothing.
 #include <mutex>
 
 #include "sclf_internal.h"
@@ -29,7 +34,9 @@ struct StaticScratch {
     unsigned long long acc[kMaxNz];          // fixed-point current sums, 2^-32 units
     float table[2 * (kMaxNz + 1)];           // (E_{m-1/2}, E_{m+1/2}) per node m
     unsigned long long removed;              // particles removed by this call
-    unsigned long long pad[31];
+    unsigned int nonfinite;                  // 1 if a particle's push gave NaN/Inf
+    unsigned int pad0;
+    unsigned long long pad[30];
 };
 
 // The only scratch of this entry point. In host code the name is a host-side
@@ -37,29 +44,13 @@ struct StaticScratch {
 // cudaGetSymbolAddress (scratch_on_current_device) and passes it on.
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
-std::mutex g_mu;
-StaticScratch* g_ptr[kMaxDevices] = {};
-
-// Set-up, once per device, with that device current.
-int scratch_on_current_device(StaticScratch** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SCLF_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return SCLF_EINVAL;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) return SCLF_ECUDA;
-        g_ptr[dev] = static_cast<StaticScratch*>(p);
-    }
-    *out = g_ptr[dev];
-    return SCLF_OK;
-}
-
 __global__ void static_clear(StaticScratch* sc, int nz) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nz; j += gridDim.x * blockDim.x)
         sc->acc[j] = 0ull;
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->removed = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->removed = 0ull;
+        sc->nonfinite = 0u;
+    }
 }
 
 __global__ void static_table(StaticScratch* sc, const double* ez, int nz) {
@@ -99,6 +90,7 @@ __global__ void static_push(StaticScratch* sc, float* xi, float* u, long long n,
             xi[i] = -1.0f;
             u[i] = 0.0f;
             atomicAdd(&sc->removed, 1ull);
+            sc->nonfinite = 1u;
             continue;
         }
         const int c0 = static_cast<int>(floorf(x));
@@ -125,23 +117,59 @@ __global__ void static_push(StaticScratch* sc, float* xi, float* u, long long n,
 }
 
 __global__ void static_finish(const StaticScratch* sc, int nz, double s_over_dt, double* j_out,
-                              long long* n_removed) {
+                              long long* n_removed, unsigned int* flags) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nz; j += gridDim.x * blockDim.x) {
         const double ssum = double(static_cast<long long>(sc->acc[j])) * sclf::kFixedInv;
         j_out[j] = s_over_dt * ssum;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n_removed)
-        *n_removed = static_cast<long long>(sc->removed);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (n_removed) *n_removed = static_cast<long long>(sc->removed);
+        if (flags && sc->nonfinite) *flags |= SCLF_FLAG_NONFINITE;
+    }
+}
+
+std::mutex g_mu;
+StaticScratch* g_ptr[kMaxDevices] = {};
+
+// Set-up, once per device, with that device current: load the module's four
+// kernels (cudaFuncGetAttributes loads a kernel that has not been loaded
+// yet) and look up the device address of the scratch array, so that no
+// later call loads anything. A cudaDeviceReset invalidates the cached
+// address; the library must then be reloaded before this entry point is
+// used again on that device.
+int scratch_on_current_device(StaticScratch** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SCLF_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return SCLF_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_ptr[dev]) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, static_clear) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, static_table) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, static_push) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, static_finish) != cudaSuccess)
+            return SCLF_ECUDA;
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) return SCLF_ECUDA;
+        g_ptr[dev] = static_cast<StaticScratch*>(p);
+    }
+    *out = g_ptr[dev];
+    return SCLF_OK;
 }
 
 }  // namespace
 
 extern "C" int tube_push_deposit_static(float* xi, float* u, int64_t n, const double* ez,
                                         int32_t nz, double dt, double dz, double s,
-                                        double* j_out, int64_t* n_removed, void* stream) {
+                                        double* j_out, int64_t* n_removed, uint32_t* flags,
+                                        void* stream) {
     if (nz < 2 || nz > kMaxNz) return SCLF_EINVAL;             // beyond the static scratch
     if (n < 0 || (n > 0 && (!xi || !u)) || !ez || !j_out) return SCLF_EINVAL;
     if (!(dt > 0.0 && dz > 0.0 && dt < dz) || !(s < 0.0)) return SCLF_EINVAL;
+    // an error the caller's own work left pending is not this call's: refuse
+    // to launch, and leave it pending for the caller
+    if (cudaPeekAtLastError() != cudaSuccess) return SCLF_ECUDA;
     StaticScratch* sc = nullptr;
     const int rc = scratch_on_current_device(&sc);
     if (rc) return rc;
@@ -157,6 +185,6 @@ extern "C" int tube_push_deposit_static(float* xi, float* u, int64_t n, const do
             static_cast<float>(dt / dz));
     }
     static_finish<<<gz, 256, 0, st>>>(sc, nz, s / dt, j_out,
-                                      reinterpret_cast<long long*>(n_removed));
+                                      reinterpret_cast<long long*>(n_removed), flags);
     return cudaGetLastError() == cudaSuccess ? SCLF_OK : SCLF_ECUDA;
 }

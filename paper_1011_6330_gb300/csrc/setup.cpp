@@ -1,6 +1,6 @@
 // Host-side set-up of a tube: unit conversion (Sec. 3), the rho_GJ profile
 // (Eq. 5, Eq. 6-7), the empty-tube Poisson problem (Eq. 4) and, for the
-// adjoint, its transpose and the profile's derivatives in (B, P, R).
+// adjoint, its transpose and the profile's analytic derivatives in (B, P, R).
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -189,11 +189,64 @@ void solve_poisson_transpose(const double* lphi, int64_t nz, double dz, double* 
     delete[] y;
 }
 
-// d/d(B, P, R) of sum_j d_rho_j rho_GJ,j on a fixed grid: central
-// differences (relative step 1e-6) of the closed-form profile, with the
-// grid, dt and s held at the values of the unperturbed parameters and R an
-// independent coordinate (taken at its derived value, not R_* theta_p(P)).
-// A caller-supplied profile does not depend on them: all three are 0.
+// shape() and its derivatives in eta and theta_* at one node, written out
+// from the same closed forms (Eq. 5, Eq. 6-7):
+//   flat: d/deta = (3/4) theta_* sin i / sqrt(eta), d/dtheta_* = (3/2) sqrt(eta) sin i;
+//   frame dragging: with T = (3/2) sqrt(eta) (H / sqrt f) theta_* sin i,
+//   D = 1 - kappa / eta^3 (dD/deta = 3 kappa / eta^4) and
+//   alpha = sqrt(1 - r_g / (R_* eta)) (dalpha/deta = (r_g / R_*) / (2 alpha eta^2)),
+//   the bracket's derivatives by the product rule, then (f / f1) / alpha.
+namespace {
+struct ShapeD {
+    double s, d_eta, d_theta;
+};
+ShapeD shape_d(const tube_params* p, const tube_derived* d, double eta, double f, double f1,
+               double H) {
+    const double ci = std::cos(p->incl_rad), si = std::sin(p->incl_rad);
+    const double se = std::sqrt(eta), th = d->theta_star;
+    if (p->rho_gj_mode != SCLF_RHO_GR)
+        return {ci + 1.5 * se * th * si, 0.75 * th * si / se, 1.5 * se * si};
+    const double hs = H / std::sqrt(f);
+    const double t = 1.5 * se * hs * th * si;
+    const double t_eta = 0.75 * hs * th * si / se;
+    const double t_th = 1.5 * se * hs * si;
+    const double e3 = eta * eta * eta;
+    const double drag = 1.0 - d->kappa / e3;
+    const double drag_eta = 3.0 * d->kappa / (e3 * eta);
+    double b, b_eta, b_th;
+    if (p->gr_variant == SCLF_GR_BOTH) {
+        b = drag * (ci + t);
+        b_eta = drag_eta * (ci + t) + drag * t_eta;
+        b_th = drag * t_th;
+    } else {
+        b = drag * ci + t;
+        b_eta = drag_eta * ci + t_eta;
+        b_th = t_th;
+    }
+    double a = 1.0, a_eta = 0.0;
+    if (p->gr_alpha) {
+        const double g = 2.0 * kG * p->mass_g / (kC * kC) / p->Rstar_cm;
+        a = std::sqrt(1.0 - g / eta);
+        a_eta = g / (eta * eta) / (2.0 * a);
+    }
+    const double w = f / f1;
+    return {w * b / a, w * (b_eta / a - b * a_eta / (a * a)), w * b_th / a};
+}
+}  // namespace
+
+// d/d(B, P, R) of sum_j d_rho_j rho_GJ,j on a fixed grid (z_j = j dz in
+// units of R), with the grid, dt and s held at the values of the unperturbed
+// parameters and R an independent coordinate (taken at its derived value,
+// not R_* theta_p(P)). rho_GJ,j = -(Lambda0^2 / 4 pi) S(eta_j, theta_*) with
+// Lambda0^2 = 4 pi n0 e^2 R^2 / (m c^2) proportional to B R^2 / P (Sec. 3;
+// held when lambda_override is set), theta_* = 0.67 (Omega R_* / c)^(1/2)
+// proportional to P^(-1/2) and eta_j = 1 + z_j R / R_*, so
+//   d rho_j / dB = rho_j / B,
+//   d rho_j / dP = -rho_j / P - (Lambda0^2 / 4 pi) dS/dtheta_* (-theta_* / 2P),
+//   d rho_j / dR = 2 rho_j / R - (Lambda0^2 / 4 pi) dS/deta z_j / R_*,
+// the Lambda0 terms dropped when Lambda0 is overridden. The f, H node tables
+// belong to the nodes and do not move. A caller-supplied profile does not
+// depend on B, P, R: all three are 0.
 int rho_gj_parameter_gradient(const tube_params* p, const double* d_rho, double* grad) {
     grad[0] = grad[1] = grad[2] = 0.0;
     if (p->rho_gj_mode == SCLF_RHO_USER) return SCLF_OK;
@@ -204,23 +257,33 @@ int rho_gj_parameter_gradient(const tube_params* p, const double* d_rho, double*
     q.R_cm = d0.R_cm;
     q.dt = d0.dt;
     q.macro_charge = d0.s;
-    const int64_t nz = p->Nz;
-    std::vector<double> rp(nz + 1), rm(nz + 1);
-    for (int k = 0; k < 3; ++k) {
-        tube_params a = q, b = q;
-        double* va = k == 0 ? &a.B_G : (k == 1 ? &a.P_s : &a.R_cm);
-        double* vb = k == 0 ? &b.B_G : (k == 1 ? &b.P_s : &b.R_cm);
-        const double h = 1e-6 * *va;
-        *va += h;
-        *vb -= h;
-        tube_derived da, db;
-        if ((rc = derive(&a, &da)) || (rc = derive(&b, &db))) return rc;
-        if ((rc = build_rho_gj(&a, &da, rp.data())) || (rc = build_rho_gj(&b, &db, rm.data())))
-            return rc;
-        double sum = 0.0;
-        for (int64_t j = 0; j <= nz; ++j) sum += d_rho[j] * (rp[j] - rm[j]);
-        grad[k] = sum / (2.0 * h);
+    tube_derived d;
+    if ((rc = derive(&q, &d))) return rc;
+    const bool lam = !(q.lambda_override > 0.0);
+    const double scale = -(d.Lambda0 * d.Lambda0 / (4.0 * kPi));
+    const double dth_dP = (q.P_s > 0.0 && q.Rstar_cm > 0.0) ? -d.theta_star / (2.0 * q.P_s) : 0.0;
+    const double deta_dR = q.Rstar_cm > 0.0 ? 1.0 / q.Rstar_cm : 0.0;     // times z_j
+    const double f1 = q.gr_f ? q.gr_f[0] : 1.0;
+    double gB = 0.0, gP = 0.0, gR = 0.0;
+    for (int64_t j = 0; j <= q.Nz; ++j) {
+        const double z = double(j) * d.dz;
+        const double eta = 1.0 + z * d.R_over_Rstar;
+        const ShapeD sd = shape_d(&q, &d, eta, q.gr_f ? q.gr_f[j] : 1.0, f1,
+                                  q.gr_H ? q.gr_H[j] : 1.0);
+        const double rho = scale * sd.s;
+        double dB = 0.0, dP = scale * sd.d_theta * dth_dP, dR = scale * sd.d_eta * z * deta_dR;
+        if (lam) {
+            dB += rho / q.B_G;
+            dP -= rho / q.P_s;
+            dR += 2.0 * rho / d.R_cm;
+        }
+        gB += d_rho[j] * dB;
+        gP += d_rho[j] * dP;
+        gR += d_rho[j] * dR;
     }
+    grad[0] = gB;
+    grad[1] = gP;
+    grad[2] = gR;
     return SCLF_OK;
 }
 

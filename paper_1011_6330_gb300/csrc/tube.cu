@@ -393,6 +393,11 @@ int tube_rho_gj_profile(const tube_params* p, double* rho) {
     return build_rho_gj(p, &d, rho);
 }
 
+int tube_rho_gj_param_gradient(const tube_params* p, const double* d_rho, double* grad) {
+    if (!p || !d_rho || !grad) return SCLF_EINVAL;
+    return rho_gj_parameter_gradient(p, d_rho, grad);
+}
+
 int tube_workspace_bytes(const tube_params* p, int64_t* bytes) {
     if (!p || !bytes) return SCLF_EINVAL;
     tube_derived d;

@@ -157,3 +157,52 @@ def test_eq6_parameters_are_validated():
                 dict(gr_H=np.full(65, np.nan))):
         p = B.default_params(**kw, **bad)
         assert lib.tube_derive(C.byref(p), C.byref(d)) == -1, bad
+
+
+@pytest.mark.parametrize("mode,variant,alpha,tables,override", [
+    (B.SCLF_RHO_FLAT, B.SCLF_GR_COS, 0, False, 0.0),
+    (B.SCLF_RHO_GR, B.SCLF_GR_COS, 0, False, 0.0),
+    (B.SCLF_RHO_GR, B.SCLF_GR_BOTH, 1, True, 0.0),
+    (B.SCLF_RHO_GR, B.SCLF_GR_COS, 1, False, 0.0),
+    (B.SCLF_RHO_GR, B.SCLF_GR_COS, 0, True, 3.0e4)])
+def test_rho_gj_param_gradient_is_the_derivative_of_the_host_profile(
+        lib, mode, variant, alpha, tables, override):
+    """tube_rho_gj_param_gradient (the analytic chain from rho_GJ to B, P, R
+    the adjoint uses) against central differences of the library's own host
+    profile (tube_rho_gj_profile) at fixed R, for the flat profile and the
+    Eq. 6 variants; with Lambda0 overridden only theta_* and eta move; and for
+    the default frame-dragging profile against the oracle's analytic
+    Jacobian."""
+    kw = workloads.gr_tube(B_G=1e12, P_s=0.3, Nz=1024, n_particles=10 ** 5)
+    kw.update(rho_gj_mode=mode, lambda_override=override)
+    d0 = B.derive(B.default_params(**kw))
+    kw.update(R_cm=d0["R_cm"], dt=d0["dt"], macro_charge=d0["s"])
+    nz, L = kw["Nz"], kw["L_over_R"]
+    z = np.arange(nz + 1) * (L / nz)
+    eta = 1.0 + z * d0["R_over_Rstar"]
+    if tables:
+        kw.update(gr_f=1.0 + 0.2 * (1.0 - 1.0 / eta), gr_H=1.0 - 0.1 * (1.0 - 1.0 / eta))
+    kw.update(gr_variant=variant, gr_alpha=alpha)
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=nz + 1)
+    g = B.rho_gj_param_gradient(B.default_params(**kw), w)
+    for k, name in enumerate(("B_G", "P_s", "R_cm")):
+        h = 1e-5 * kw[name]
+        rp = B.rho_gj_profile(B.default_params(**{**kw, name: kw[name] + h}))
+        rm = B.rho_gj_profile(B.default_params(**{**kw, name: kw[name] - h}))
+        fd = float(w @ (rp - rm)) / (2.0 * h)
+        assert abs(g[k] - fd) <= 1e-7 * max(abs(fd), 1e-30) + 1e-12 * abs(g).max(), (name, g[k], fd)
+    if override:
+        assert g[0] == 0.0
+    if mode == B.SCLF_RHO_GR and variant == B.SCLF_GR_COS and not alpha and not tables:
+        from oracle import adjoint as oadj
+        jac = oadj.rho_gj_parameter_jacobian(orc.RHO_GR, z, kw["B_G"], kw["P_s"], kw["R_cm"],
+                                              kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+        for k, key in enumerate("BPR"):
+            assert g[k] == pytest.approx(float(w @ jac[key]), rel=1e-11)
+
+
+def test_rho_gj_param_gradient_of_a_user_profile_is_zero(lib):
+    kw = workloads.flat_sclf_small()
+    g = B.rho_gj_param_gradient(B.default_params(**kw), np.ones(kw["Nz"] + 1))
+    assert np.array_equal(g, np.zeros(3))

@@ -166,22 +166,32 @@ def test_charge_free_run_obeys_euler_identity_gpu(gpu_lib):
 
 
 def test_autograd_function_gives_the_adjoint_gradient(gpu_lib):
-    """tube_objectives(theta).backward() equals the direct adjoint calls."""
+    """tube_objectives(theta).backward() equals the direct adjoint calls, at
+    an injection weight w != 1 (d/dw = d_s s_ref comes from the C ABI), and a
+    second backward through a retained graph gives the same gradient again."""
     import torch
     kw, z, u, nsteps, K = gr_problem(B.SCLF_FP32, n=20000, nsteps=40)
     base = {k: v for k, v in kw.items() if k not in ("dt", "R_cm")}
     spec, theta0 = B.adjoint_problem(base, nsteps, K, z, u)
+    theta0 = theta0.copy()
+    theta0[3] = 1.25
     theta = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
     out = B.tube_objectives(theta, spec)
-    (out[0] + 2.0 * out[1] / float(out[1].detach())).backward()
-    a, vals = gpu_run(kw, z, u, nsteps, K)
+    loss = out[0] + 2.0 * out[1] / float(out[1].detach())
+    loss.backward(retain_graph=True)
+    g1 = theta.grad.numpy().copy()
+    loss.backward()                                   # the same recorded run again
+    g2 = theta.grad.numpy() - g1
+    a, vals = gpu_run(dict(kw, macro_charge=1.25 * spec["s_ref"]), z, u, nsteps, K)
     assert np.allclose(out.detach().numpy(), vals, rtol=1e-12, atol=0)
     want = np.zeros(4)
     for i, w in enumerate((1.0, 2.0 / vals[1])):
         g_rho, g_s = a.backward(i)
-        pg = a.param_gradient(g_rho, g_s)
+        pg = a.param_gradient(g_rho, g_s, spec["s_ref"])
+        assert pg[3] == g_s * spec["s_ref"]
         want += w * pg
-    assert np.allclose(theta.grad.numpy(), want, rtol=1e-12, atol=0)
+    assert np.allclose(g1, want, rtol=1e-12, atol=0)
+    assert np.allclose(g2, want, rtol=1e-12, atol=0)
     a.close()
 
 
