@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--sort-interval", type=int, default=0,
                     help="gr1e8/large: re-sort the slots by cell (tube_sort) once before the "
                          "run and every this many steps (0: never)")
+    ap.add_argument("--push-stages", type=int, default=0,
+                    help="gr1e8/large: shared-memory stages of the particle kernel's bulk-copy "
+                         "ring (1: loads straight into registers; 0: the library's default)")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="adjoint workload: no event-record nodes (for ncu runs, where "
                          "each event node is very slow); no per-kernel times or roofline")
@@ -183,7 +186,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=None):
+def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=None,
+               push_stages=0):
     """Create the workload's tube and fill it with its seeded synthetic state.
     Returns (tube, params, derived, sample_z, sample_u, stride): every
     stride-th particle of the state, for the CPU baseline."""
@@ -193,6 +197,7 @@ def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=
     else:
         kw = workloads.gr_tube(n_particles=n, accumulate=acc, **({"Nz": nz} if nz else {}))
     kw["sort_interval"] = sort_interval
+    kw["push_stages"] = push_stages
     t = B.Tube(B.default_params(**kw))
     d = t.derived
     # frame-dragging ramp for the initial momenta: gamma_far = Lambda0^2 kappa cos i
@@ -748,7 +753,7 @@ def main():
     n = int(args.particles or (2 ** 30 if large else 1e8))
     t, kw, d, zs, us, stride = build_tube(B, workloads, args.workload, n, acc, args.order,
                                           seed=rank_seed(rank), sort_interval=args.sort_interval,
-                                          nz=args.nz)
+                                          nz=args.nz, push_stages=args.push_stages)
     t.solve_fields()
     sort_ms = None
     if args.sort_interval > 0:                       # a stable re-sort by cell up front
@@ -862,6 +867,7 @@ def main():
                    "particles_per_gpu": n, "Nz": kw["Nz"], "Lambda0": d["Lambda0"],
                    "dt_R_over_c": d["dt"], "order": args.order,
                    "current_accumulator": args.accumulate,
+                   "push_stages": args.push_stages or "default",
                    "sort_by_cell": ({"interval_steps": args.sort_interval,
                                      "first_sort_ms_wall": sort_ms}
                                     if args.sort_interval > 0 else None),

@@ -134,7 +134,16 @@ typedef struct tube_params {
     int32_t sort_interval; /* > 0: tube_run re-sorts the slots by position
                               (tube_sort) every sort_interval steps or more
                               (between graph chunks); 0: never           */
-    int32_t reserved0;
+    int32_t push_stages;   /* particle kernel of a single tube: 0 -> the
+                              library's default (1); 1: each thread loads its
+                              slots straight into registers; 2..4: the tiles
+                              a CTA processes next stream into that many
+                              shared-memory stages by bulk asynchronous
+                              copies (TMA) while it computes (slower on the
+                              benchmarked tubes, whose particle kernel is
+                              bound by instruction issue, not by load
+                              latency). Results do not depend on it (bit
+                              for bit); < 0 or > 4 is EINVAL              */
 } tube_params;
 
 /* Code-unit quantities derived from tube_params (all FP64). */
@@ -336,6 +345,19 @@ int tube_compact(tube_t t);
  * are unspecified afterwards and its TIMEOUT flag stays set: use a scratch
  * tube. Synchronises. */
 int tube_selftest_wait_timeout(tube_t t);
+
+/* Check of the particle kernels' float32 velocity (Sec. 2, Eq. 1: the push
+ * advances z by dt u / gamma with gamma = sqrt(1 + u^2)). The kernels
+ * compute v = u / sqrt(1 + u^2) by a Newton step on the hardware reciprocal
+ * square root and Markstein's FMA division instead of the general-range
+ * square root and division; this runs both on the float32 bit patterns
+ * [first, first + count) on the current device and counts the patterns
+ * whose results differ in any bit (NaN equals NaN): *n_mismatch, and the
+ * smallest such pattern in *first_mismatch (0xffffffff when none).
+ * first + count <= 2^32, else SCLF_EINVAL; NULL outputs are EINVAL.
+ * Allocates 16 bytes of device memory for the call. Synchronises. */
+int tube_selftest_velocity(uint32_t first, uint64_t count, uint64_t* n_mismatch,
+                           uint32_t* first_mismatch);
 
 /* Re-sort the particle slots by position, stably (particles in one of 256
  * bins per cell keep their slot order; fewer bins above 2^23 cells), and

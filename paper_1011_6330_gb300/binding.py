@@ -42,7 +42,7 @@ class TubeParams(C.Structure):
         ("compact_interval", C.c_int32), ("use_graphs", C.c_int32),
         ("gr_variant", C.c_int32), ("gr_alpha", C.c_int32),
         ("gr_f", C.POINTER(C.c_double)), ("gr_H", C.POINTER(C.c_double)),
-        ("sort_interval", C.c_int32), ("reserved0", C.c_int32),
+        ("sort_interval", C.c_int32), ("push_stages", C.c_int32),
     ]
 
 
@@ -103,6 +103,8 @@ SIGNATURES = {
     "tube_compact": (_i32, [_vp]),
     "tube_sort": (_i32, [_vp]),
     "tube_selftest_wait_timeout": (_i32, [_vp]),
+    "tube_selftest_velocity": (_i32, [C.c_uint32, C.c_uint64, C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint32)]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
     "batch_create": (_i32, [C.c_int32, C.POINTER(TubeParams), _vp, C.POINTER(_vp)]),

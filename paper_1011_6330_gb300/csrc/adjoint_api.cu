@@ -114,7 +114,7 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
             pa.ez2 = reinterpret_cast<const float*>(tab_of(A, k));
             pa.evlog = evlog;
             pa.replay = replay;
-            e = launch_push_fix32(pa, t->push_grid, s);
+            e = launch_push_fix32(pa, t->push_stages, t->push_grid, s);
         } else {
             PushArgs<Real> pa = push_args<Real>(t);
             pa.xi = reinterpret_cast<Real*>(A->sx[k]);
@@ -125,7 +125,7 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
             pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
             pa.evlog = evlog;
             pa.replay = replay;
-            e = launch_push<Real>(pa, t->p.accumulate, t->push_grid, s);
+            e = launch_push<Real>(pa, t->p.accumulate, t->push_stages, t->push_grid, s);
         }
         if (e == cudaSuccess) e = mark(A, timed, 2 * k + 1);
         if (e != cudaSuccess) break;

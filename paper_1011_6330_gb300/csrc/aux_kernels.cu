@@ -98,6 +98,37 @@ __global__ void rho_kernel(const Pos* xi, long long n, double* acc, int nz, doub
     }
 }
 
+// velocity_f32 against the general-range IEEE sequence on the float32 bit
+// patterns [first, first + count): out[0] counts the patterns whose results
+// differ (two NaNs count as equal), out[1] keeps the smallest such pattern.
+__global__ void velocity_check_kernel(unsigned first, unsigned long long count,
+                                      unsigned long long* out) {
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    unsigned long long bad = 0, lowest = ~0ULL;
+    for (unsigned long long i = blockIdx.x * static_cast<unsigned long long>(blockDim.x) +
+                                threadIdx.x;
+         i < count; i += stride) {
+        const unsigned bits = first + static_cast<unsigned>(i);
+        const float u = __uint_as_float(bits);
+        const float a = velocity_f32(u), b = velocity_f32_ieee(u);
+        const bool same = __float_as_uint(a) == __float_as_uint(b) || (isnan(a) && isnan(b));
+        if (!same) {
+            ++bad;
+            lowest = bits < lowest ? bits : lowest;
+        }
+    }
+    bad = warp_sum(bad);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, lowest, off);
+        lowest = o < lowest ? o : lowest;
+    }
+    if ((threadIdx.x & 31) == 0 && bad) {
+        atomicAdd(out, bad);
+        atomicMin(out + 1, lowest);
+    }
+}
+
 template <class Real>
 __global__ void ez_table_kernel(const double* ez, Real* ez2, int nz) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,6 +249,12 @@ cudaError_t launch_finish_append(DevState* st, const double* ez, long long n_add
 template <class Real>
 cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s) {
     ez_table_kernel<Real><<<(nz + 1 + 255) / 256, 256, 0, s>>>(ez, ez2, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_check(unsigned first, unsigned long long count,
+                                  unsigned long long* out, int grid, cudaStream_t s) {
+    velocity_check_kernel<<<grid, 256, 0, s>>>(first, count, out);
     return cudaGetLastError();
 }
 

@@ -233,15 +233,20 @@ struct AdjPushFixArgs {
 };
 
 // Launchers. All return cudaGetLastError() after the launch.
+// The single-tube particle kernels take `stages`: 1 loads each tile straight
+// into registers, 2..kMaxPushStages stream the next tiles through a ring of
+// that many shared-memory stages by bulk asynchronous copies (TMA).
+constexpr int kMaxPushStages = 4;
+constexpr int kDefaultPushStages = 1;
 template <class Real>
-cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int grid,
+cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int stages, int grid,
                         cudaStream_t s);
 template <class Real>
-int push_grid_size(int accumulate, int device_sms);
+int push_grid_size(int accumulate, int stages, int device_sms);
 template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
                          cudaStream_t s);
-cudaError_t launch_push_fix32(const PushFixArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_push_fix32(const PushFixArgs& a, int stages, int grid, cudaStream_t s);
 // Shapes of the batched particle kernel: particles per thread (the tile is
 // kThreads times that), CTAs per SM in its launch bounds and per-thread
 // current runs (1: the first particle's cell; 2: also the last one's).
@@ -284,7 +289,7 @@ cudaError_t launch_batch_status(const BatchTube* tubes, int n_tubes, tube_stats*
 int batch_push_grid_size(int variant, int device_sms);
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
                                int parity, cudaStream_t s);
-int push_fix32_grid_size(int device_sms);
+int push_fix32_grid_size(int stages, int device_sms);
 template <class Pos, class Mom>
 cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s);
 template <class Pos, class Mom>
@@ -315,6 +320,8 @@ cudaError_t launch_finish_append(DevState* st, const double* ez,
                                  cudaStream_t s);
 template <class Real>
 cudaError_t launch_ez_table(const double* ez, Real* ez2, int nz, cudaStream_t s);
+cudaError_t launch_velocity_check(unsigned first, unsigned long long count,
+                                  unsigned long long* out, int grid, cudaStream_t s);
 template <class Pos>
 cudaError_t launch_rho(const Pos* xi, long long n_slots, double* rho_acc,
                        int nz, double scale, cudaStream_t s);

@@ -109,9 +109,11 @@ double raw_mom(const sclf_tube* t, const void* raw, int64_t i) {
 }
 
 cudaError_t enqueue_push(sclf_tube* t, cudaStream_t s) {
-    if (fix32(t)) return launch_push_fix32(push_fix_args(t), t->push_grid, s);
-    return fp64(t) ? launch_push<double>(push_args<double>(t), t->p.accumulate, t->push_grid, s)
-                   : launch_push<float>(push_args<float>(t), t->p.accumulate, t->push_grid, s);
+    if (fix32(t)) return launch_push_fix32(push_fix_args(t), t->push_stages, t->push_grid, s);
+    return fp64(t) ? launch_push<double>(push_args<double>(t), t->p.accumulate, t->push_stages,
+                                         t->push_grid, s)
+                   : launch_push<float>(push_args<float>(t), t->p.accumulate, t->push_stages,
+                                        t->push_grid, s);
 }
 cudaError_t enqueue_field(sclf_tube* t, int parity, cudaStream_t s) {
     return fp64(t) ? launch_field<double>(field_args<double>(t, parity), t->p.accumulate, s)
@@ -491,9 +493,10 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     if (launch_finish_append(t->st, t->ez, 0, t->fc, t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
     if (cudaStreamSynchronize(t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
 
-    t->push_grid = fix32(t) ? push_fix32_grid_size(t->sms)
-                 : fp64(t) ? push_grid_size<double>(p->accumulate, t->sms)
-                           : push_grid_size<float>(p->accumulate, t->sms);
+    t->push_stages = p->push_stages > 0 ? p->push_stages : kDefaultPushStages;
+    t->push_grid = fix32(t) ? push_fix32_grid_size(t->push_stages, t->sms)
+                 : fp64(t) ? push_grid_size<double>(p->accumulate, t->push_stages, t->sms)
+                           : push_grid_size<float>(p->accumulate, t->push_stages, t->sms);
     t->compact_grid = fix32(t) ? compact_grid_size<int, float>(t->sms)
                     : fp64(t) ? compact_grid_size<double, double>(t->sms)
                               : compact_grid_size<float, float>(t->sms);
@@ -652,6 +655,31 @@ int tube_selftest_wait_timeout(tube_t t) {
     rc = read_state(t, &h);
     if (rc) return rc;
     return (h.flags & SCLF_FLAG_TIMEOUT) ? SCLF_ETIMEOUT : SCLF_OK;
+}
+
+int tube_selftest_velocity(uint32_t first, uint64_t count, uint64_t* n_mismatch,
+                           uint32_t* first_mismatch) {
+    if (!n_mismatch || !first_mismatch) return SCLF_EINVAL;
+    if (count > (uint64_t(1) << 32) - first) return SCLF_EINVAL;
+    *n_mismatch = 0;
+    *first_mismatch = 0xffffffffu;
+    if (count == 0) return SCLF_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SCLF_ECUDA;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return SCLF_ENOMEM;
+    const unsigned long long init[2] = {0ULL, ~0ULL};
+    unsigned long long h[2] = {0ULL, ~0ULL};
+    cudaError_t e = cudaMemcpy(d, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_velocity_check(first, count, d, sms * 8, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return SCLF_ECUDA;
+    *n_mismatch = h[0];
+    *first_mismatch = h[0] ? static_cast<uint32_t>(h[1]) : 0xffffffffu;
+    return SCLF_OK;
 }
 
 int tube_sort(tube_t t) {

@@ -49,6 +49,7 @@ struct sclf_tube {
     std::vector<double> gr_f, gr_H;     // copies of the caller's Eq. 6 tables (p points here)
     sclf::FieldConsts fc{};
     int push_grid = 0, compact_grid = 0;
+    int push_stages = 1;               // the particle kernel's TMA ring (1: none)
     int fb = 0;                        // fractional bits of SCLF_FIX32 positions
     int64_t host_step = 0;             // steps launched (== device step count)
     int steps_since_compact = 0;

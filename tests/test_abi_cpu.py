@@ -89,7 +89,8 @@ def test_invalid_parameters_are_rejected(lib):
     kw = workloads.flat_sclf_small()
     for bad in (dict(dt=kw["L_over_R"] / kw["Nz"]),       # c dt = dz
                 dict(Nz=1), dict(capacity=-1), dict(precision=7),
-                dict(accumulate=3), dict(rho_gj_mode=9), dict(L_over_R=0.0)):
+                dict(accumulate=3), dict(rho_gj_mode=9), dict(L_over_R=0.0),
+                dict(push_stages=-1), dict(push_stages=5)):
         p = B.default_params(**{**kw, **bad})
         with pytest.raises(B.SclfError) as e:
             B.derive(p)
@@ -206,3 +207,12 @@ def test_rho_gj_param_gradient_of_a_user_profile_is_zero(lib):
     kw = workloads.flat_sclf_small()
     g = B.rho_gj_param_gradient(B.default_params(**kw), np.ones(kw["Nz"] + 1))
     assert np.array_equal(g, np.zeros(3))
+
+
+def test_velocity_selftest_validates_its_range_without_a_device(lib):
+    import ctypes as C
+    n, first = C.c_uint64(7), C.c_uint32(7)
+    assert lib.tube_selftest_velocity(1, 1 << 32, C.byref(n), C.byref(first)) == -1
+    assert lib.tube_selftest_velocity(0, 1, None, C.byref(first)) == -1
+    assert lib.tube_selftest_velocity(5, 0, C.byref(n), C.byref(first)) == 0
+    assert n.value == 0 and first.value == 0xffffffff

@@ -8,6 +8,7 @@ the floating-point decisions -- which cell, inside or outside -- are taken
 in the same precision on both sides).
 """
 
+import ctypes as C
 import math
 
 import numpy as np
@@ -828,6 +829,39 @@ def test_batch_kernel_shapes_agree_bit_for_bit_and_autotune_keeps_one(gpu_lib):
         b.close()
 
 
+@pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FP64, B.SCLF_FIX32])
+def test_push_stages_change_no_result(gpu_lib, prec):
+    """The particle kernel with its slots loaded straight into registers
+    (push_stages 1) and streamed through a ring of 2, 3 or 4 shared-memory
+    stages by bulk asynchronous copies gives the same run bit for bit. The
+    tube holds enough tiles that every CTA refills its ring several times,
+    with a ragged tail and injection every step; no wait gives up. (The
+    fields start from the empty tube's: the Eq. 4 solve with the particles'
+    charge sums FP64 atomics, whose order is not fixed.)"""
+    kw = workloads.flat_sclf_small(precision=prec, accumulate=B.SCLF_ACC_FIXED64,
+                                   capacity=1 << 23)
+    z, u = synth.random_particles(6 * 10 ** 6 + 1234, kw["L_over_R"], seed=11, u_sigma=2.0)
+    ref = None
+    for stages in (1, 2, 3, 4):
+        t = B.Tube(B.default_params(**kw, push_stages=stages))
+        t.add_particles(z, u)
+        t.run(12)
+        st = t.status()
+        assert st["flags"] == 0, (stages, st["flags"])
+        got = (st, t.read_particles(), t.read_fields(rho=False))
+        t.close()
+        if ref is None:
+            ref = got
+            continue
+        for k in ("n_particles", "n_slots", "total_injected", "last_removed",
+                  "pending_injection"):
+            assert got[0][k] == ref[0][k], (stages, k)
+        for a, b in zip(got[1], ref[1]):
+            assert np.array_equal(a, b), stages
+        for k in ("ez", "er", "b", "j"):
+            assert np.array_equal(got[2][k], ref[2][k]), (stages, k)
+
+
 @pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
 def test_sort_by_cell_changes_no_result(gpu_lib, prec):
     """A shuffled beam stepped with a stable re-sort by cell every 10 steps
@@ -958,3 +992,15 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(gpu_lib):
         compare(t2, o, TOL[B.SCLF_FP32], "after the timeout, step %d" % n)
     assert t2.check() == 0
     t2.close()
+
+
+def test_velocity_routine_equals_ieee_sequence_on_every_float32(gpu_lib):
+    """The particle kernels' float32 velocity u / sqrt(1 + u^2) (Newton step
+    on the hardware reciprocal square root, Markstein's FMA division) equals
+    the correctly rounded sequence RN(u / RN(sqrt(RN(1 + RN(u u))))) bit for
+    bit on all 2^32 float32 inputs, so the float32 results stay those of the
+    float32 oracle."""
+    n = C.c_uint64()
+    first = C.c_uint32()
+    assert gpu_lib.tube_selftest_velocity(0, 1 << 32, C.byref(n), C.byref(first)) == 0
+    assert n.value == 0, (n.value, hex(first.value))
