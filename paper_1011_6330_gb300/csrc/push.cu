@@ -31,13 +31,24 @@ __device__ __forceinline__ typename AccType<kAcc>::T common_frac(double x0, doub
     return frac_acc_in_cell<kAcc>(x0, x1, jf);
 }
 
-// A run's total in the accumulator's units: a float32 run of exact x1 - x0
-// sums (multiples of 2^-20, below 16) is converted to 2^-32 units exactly.
+// Adds the warp's per-lane runs (cell key, sum) to the current. A float32
+// run of exact x1 - x0 terms (multiples of 2^-20, below 16) is first
+// converted to 2^-20 units exactly (below 2^24); the segmented sums of up to
+// 32 lanes then stay below 2^29 and are scanned in 32-bit integers, and
+// each segment's total goes to the 2^-32-unit accumulator shifted by 12.
 template <bool kFloatRun, class AccT, class RunT>
-__device__ __forceinline__ AccT run_total(RunT r) {
-    if constexpr (kFloatRun)
-        return static_cast<long long>(__float2int_rn(r * 1048576.0f)) * 4096;
-    else return r;
+__device__ __forceinline__ void flush_run(int key, RunT r, int nz, unsigned int* flags,
+                                          AccT* jacc) {
+    if constexpr (kFloatRun) {
+        int q = __float2int_rn(r * 1048576.0f);
+        if constexpr (kChecked)
+            if (q != 0 && !checked_index(key, nz, flags)) q = 0;
+        warp_flush_i32(key, q, jacc, 12);
+    } else {
+        if constexpr (kChecked)
+            if (r != AccT(0) && !checked_index(key, nz, flags)) r = AccT(0);
+        warp_flush<AccT>(key, r, jacc);
+    }
 }
 
 // What one tile of one tube needs.
@@ -92,6 +103,11 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
             }
         }
     }
+    if (k_tot < kPPT) {                          // padding past the last slot: a hole
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k)
+            if (k >= k_tot) xs[k] = Real(-1);
+    }
     // The common particle stays inside the cell of the thread's first
     // particle, away from the base cells and the top: its current
     // fraction joins a per-thread run without any branch. Everything
@@ -113,15 +129,14 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
     static_assert(!kFloatRun || kPPT <= 16, "float run: at most 16 terms");
     using RunT = typename std::conditional<kFloatRun, float, AccT>::type;
     constexpr Real kRunMin = kFloatRun ? Real(8) : Real(1);
-    const Real rkey = (k_tot > 0 && xs[0] >= kRunMin) ? r_floor(xs[0]) : Real(-2);
-    const Real rkey2 = kTwoRuns ? ((kPPT - 1 < k_tot && xs[kPPT - 1] >= kRunMin)
-                                       ? r_floor(xs[kPPT - 1]) : Real(-2))
+    const Real rkey = xs[0] >= kRunMin ? r_floor(xs[0]) : Real(-2);
+    const Real rkey2 = kTwoRuns ? (xs[kPPT - 1] >= kRunMin ? r_floor(xs[kPPT - 1]) : Real(-2))
                                 : rkey;
     RunT ra = RunT(0), rb = RunT(0);
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
         const Real x = xs[k];
-        const bool lv = (k < k_tot) & (x >= Real(0)) & (x < nzf);   // holes carry xi < 0
+        const bool lv = (x >= Real(0)) & (x < nzf);   // holes and padding carry xi < 0
         const Real xx = lv ? x : Real(0);
         // (a2) cloud-in-cell gather from the (E_{m-1/2}, E_{m+1/2}) table;
         // 0 <= xx < Nz keeps m in [0, Nz]
@@ -186,16 +201,10 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
         }
     }
     const int key = rkey >= Real(0) ? static_cast<int>(rkey) : -1;
-    AccT qr = run_total<kFloatRun, AccT>(ra);
-    if constexpr (kChecked)
-        if (qr != AccT(0) && !checked_index(key, nz, c.flags)) qr = AccT(0);
-    warp_flush<AccT>(key, qr, jacc);
+    flush_run<kFloatRun, AccT>(key, ra, nz, c.flags, jacc);
     if constexpr (kTwoRuns) {
         const int key2 = rkey2 >= Real(0) && rkey2 != rkey ? static_cast<int>(rkey2) : -1;
-        AccT qr2 = run_total<kFloatRun, AccT>(rb);
-        if constexpr (kChecked)
-            if (qr2 != AccT(0) && !checked_index(key2, nz, c.flags)) qr2 = AccT(0);
-        warp_flush<AccT>(key2, qr2, jacc);
+        flush_run<kFloatRun, AccT>(key2, rb, nz, c.flags, jacc);
     }
 }
 
@@ -245,7 +254,8 @@ __device__ __forceinline__ void record_injection(DevState* st, long long n_inj, 
 // while it computes, and each thread takes its slots from there.
 // 4 CTAs of 256 threads per SM (at most 64 registers): measured fastest on
 // the 1e8-particle tube (0.320 ms against 0.353 ms at 3 and 0.441 ms with
-// no bound, where the compiler takes 103 registers).
+// no bound, where the compiler takes 103 registers; 4 particles per thread
+// at 5 CTAs per SM took 0.323 ms against 0.314 ms for 8 at 4).
 constexpr int kPushMinBlocks = 4;
 template <class Real, int kAcc, int kStages>
 __global__ void __launch_bounds__(kThreads, kPushMinBlocks)

@@ -56,14 +56,18 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
             }
         }
     }
+    if (k_tot < kPPT) {                          // padding past the last slot: a hole
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k)
+            if (k >= k_tot) xs[k] = -1;
+    }
     // run key: the first slot's cell (0xffffffff for a hole: no run)
-    const unsigned rkey = (k_tot > 0 && xs[0] >= 0) ? (static_cast<unsigned>(xs[0]) >> fb)
-                                                    : 0xffffffffu;
+    const unsigned rkey = xs[0] >= 0 ? (static_cast<unsigned>(xs[0]) >> fb) : 0xffffffffu;
     int ra = 0, rb = 0;       // run sums on cells rkey and rkey + 1, in 2^-fb units
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
         const int X = xs[k];
-        const bool lv = (k < k_tot) & (X >= 0);
+        const bool lv = X >= 0;                  // holes and padding carry X < 0
         const unsigned U = lv ? static_cast<unsigned>(X) : 0u;
         // (a2) h = X + 2^(fb-1): m = h >> fb, f = (h mod 2^fb) 2^-fb
         const unsigned h = U + half;
@@ -140,8 +144,14 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
         if (ra != 0 && !checked_index(key, nz, c.flags)) ra = 0;
         if (rb != 0 && !checked_index(key2, nz, c.flags)) rb = 0;
     }
-    warp_flush<long long>(key, shl_signed(ra, sh), jacc);
-    warp_flush<long long>(key2, shl_signed(rb, sh), jacc);
+    // |ra|, |rb| <= 8 2^fb per lane: 32-lane segment sums fit 32 bits up to fb = 22
+    if (fb <= 22) {
+        warp_flush_i32(key, ra, jacc, sh);
+        warp_flush_i32(key2, rb, jacc, sh);
+    } else {
+        warp_flush<long long>(key, shl_signed(ra, sh), jacc);
+        warp_flush<long long>(key2, shl_signed(rb, sh), jacc);
+    }
 }
 
 // The particle kernel of SCLF_FIX32 tubes. kStages == 1: each tile's slots
