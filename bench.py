@@ -59,6 +59,9 @@ def parse():
                          "profiling case with the same particles per cell")
     ap.add_argument("--order", choices=["descending", "shuffled"], default="descending")
     ap.add_argument("--accumulate", choices=["fixed64", "fp64"], default="fixed64")
+    ap.add_argument("--precision", choices=["f32", "fix32"], default="f32",
+                    help="gr1e8: particle positions as float32 or as 32-bit fixed point "
+                         "(SCLF_FIX32; momenta float32 either way)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -187,7 +190,7 @@ class ClockSampler:
 
 
 def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=None,
-               push_stages=0):
+               push_stages=0, precision="f32"):
     """Create the workload's tube and fill it with its seeded synthetic state.
     Returns (tube, params, derived, sample_z, sample_u, stride): every
     stride-th particle of the state, for the CPU baseline."""
@@ -195,7 +198,9 @@ def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=
     if workload == "large":
         kw = workloads.large_tube(n_particles=n, **({"Nz": nz} if nz else {}))
     else:
-        kw = workloads.gr_tube(n_particles=n, accumulate=acc, **({"Nz": nz} if nz else {}))
+        kw = workloads.gr_tube(n_particles=n, accumulate=acc,
+                               precision=B.SCLF_FIX32 if precision == "fix32" else B.SCLF_FP32,
+                               **({"Nz": nz} if nz else {}))
     kw["sort_interval"] = sort_interval
     kw["push_stages"] = push_stages
     t = B.Tube(B.default_params(**kw))
@@ -753,7 +758,8 @@ def main():
     n = int(args.particles or (2 ** 30 if large else 1e8))
     t, kw, d, zs, us, stride = build_tube(B, workloads, args.workload, n, acc, args.order,
                                           seed=rank_seed(rank), sort_interval=args.sort_interval,
-                                          nz=args.nz, push_stages=args.push_stages)
+                                          nz=args.nz, push_stages=args.push_stages,
+                                          precision=args.precision)
     t.solve_fields()
     sort_ms = None
     if args.sort_interval > 0:                       # a stable re-sort by cell up front

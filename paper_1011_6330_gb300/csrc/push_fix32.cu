@@ -25,7 +25,7 @@ struct FixCtx {
     unsigned int* flags;
     long long n_slots, n_tot, id0;
     int nz, fb, sh;
-    unsigned half, mask, utop;
+    unsigned half, mask;
     long long one, top;
     float dt, cfl, scale, two_fb;
 };
@@ -37,7 +37,7 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
                                            long long& removed, bool& nonfinite) {
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
     const int nz = c.nz, fb = c.fb, sh = c.sh;
-    const unsigned half = c.half, mask = c.mask, utop = c.utop;
+    const unsigned half = c.half, mask = c.mask;
     const long long one = c.one, top = c.top;
     const float dt = c.dt, cfl = c.cfl, scale = c.scale, two_fb = c.two_fb;
     const float2* __restrict__ tab = c.tab;
@@ -61,9 +61,18 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
         for (int k = 0; k < kPPT; ++k)
             if (k >= k_tot) xs[k] = -1;
     }
-    // run key: the first slot's cell (0xffffffff for a hole: no run)
-    const unsigned rkey = xs[0] >= 0 ? (static_cast<unsigned>(xs[0]) >> fb) : 0xffffffffu;
-    int ra = 0, rb = 0;       // run sums on cells rkey and rkey + 1, in 2^-fb units
+    // Runs on the first slot's cell c_r and on c_r + 1, when c_r lies in
+    // [1, Nz - 2]; A = c_r 2^fb, else A = 0xc0000000, which puts U - A at or
+    // above 2^30 >= 2^fb for every position U < 2^31 (no particle is common).
+    // A common particle starts in c_r (U - A < 2^fb: live, cell >= 1) and
+    // ends in c_r or c_r + 1 (U1 - A < 2^(fb+1): inside the tube); in 2^-fb
+    // units its current is F_cr(X1) - F_cr(X) = min(U1 - A, 2^fb) - (U - A)
+    // on c_r and max(U1 - A - 2^fb, 0) on c_r + 1, so the runs keep the sum
+    // of the increments and the sum of the parts above c_r.
+    const bool has_run = xs[0] >= static_cast<int>(one) && xs[0] < top - one;
+    const unsigned A = has_run ? (static_cast<unsigned>(xs[0]) & ~mask) : 0xc0000000u;
+    const unsigned one_u = 1u << fb, two_u = 2u << fb;
+    int s_inc = 0, s_over = 0;
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
         const int X = xs[k];
@@ -78,25 +87,23 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
         // (a3) Eq. 1, then the displacement on the 2^-fb grid
         const float u1 = us[k] - ep * dt;
         const float d = velocity_f32(u1) * cfl;
-        const bool fin = isfinite(d);
-        const int inc = __float2int_rn(d * two_fb);  // |inc| < 2^fb
-        // X1 = X + inc in 32-bit two's complement: with X < 2^31 and
-        // |inc| < 2^fb, 0 <= X1 < Nz 2^fb exactly when U1 < Nz 2^fb
+        // |v| <= 1 and c dt < dz: a finite d has |d| <= 1 (NaN fails the test)
+        const bool fin = fabsf(d) <= 1.0f;
+        const int inc = __float2int_rn(d * two_fb);  // |inc| <= 2^fb
+        // X1 = X + inc in 32-bit arithmetic: X < Nz 2^fb <= 2^31 and
+        // |inc| <= 2^fb keep U + inc away from wrapping for cells >= 1
         const unsigned U1 = U + static_cast<unsigned>(inc);
-        const unsigned c0 = U >> fb, c1u = U1 >> fb;
-        // (a4) staying in the cell: F_c0(X1) - F_c0(X) = inc; moving up one
-        // cell: F_c0 goes to 2^fb (adds 2^fb - (X mod 2^fb)) and F_c1 from 0
-        // to X1 mod 2^fb
-        const bool stay = c1u == c0, up = c1u == c0 + 1u;
-        const bool common = lv & fin & (U1 < utop) & (stay | up) & (c1u != 0u) &
-                            (c0 == rkey);
-        const int q0 = stay ? inc : static_cast<int>((1u << fb) - (U & mask));
-        ra += common ? q0 : 0;
-        rb += (common & up) ? static_cast<int>(U1 & mask) : 0;
+        // (a4) the common particle's current joins the runs
+        const unsigned t1 = U1 - A;
+        const bool common = fin & (U - A < one_u) & (t1 < two_u);
+        const int over = max(static_cast<int>(t1 - one_u), 0);
+        s_inc += common ? inc : 0;
+        s_over += common ? over : 0;
         if (lv & !common) {
             const int XX = static_cast<int>(U);
             const long long X1 = static_cast<long long>(XX) + inc;
             const long long c1 = X1 >> fb;
+            const unsigned c0 = U >> fb;
             if (!fin) {
                 nonfinite = true;
                 ++removed;
@@ -138,8 +145,9 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
             vstore(c.uo + i0 + v, us + v);
         }
     }
-    const int key = rkey == 0xffffffffu ? -1 : static_cast<int>(rkey);
-    const int key2 = key >= 0 && key + 1 < nz ? key + 1 : -1;
+    const int key = has_run ? static_cast<int>(A >> fb) : -1;
+    const int key2 = has_run ? key + 1 : -1;
+    int ra = s_inc - s_over, rb = s_over;
     if constexpr (kChecked) {
         if (ra != 0 && !checked_index(key, nz, c.flags)) ra = 0;
         if (rb != 0 && !checked_index(key2, nz, c.flags)) rb = 0;
@@ -157,9 +165,11 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
 // The particle kernel of SCLF_FIX32 tubes. kStages == 1: each tile's slots
 // are loaded straight into registers; kStages >= 2: the next tiles stream
 // through a ring of shared-memory stages by bulk asynchronous copies (TMA).
-// At least 3 CTAs of 256 threads per SM: 1.449 ms per step of a 2^28-particle
-// large tube, against 1.455 ms at 4 and 1.613 ms with no bound.
-constexpr int kFix32MinBlocks = 3;
+// At least 4 CTAs of 256 threads per SM: 0.343 ms per step of the 1e8-particle
+// frame-dragging tube and 3.80 ms of the 2^30-particle large tube, against
+// 0.362 and 4.05 ms at 3 CTAs per SM and 1.613 ms (2^28 particles) with no
+// bound.
+constexpr int kFix32MinBlocks = 4;
 template <int kStages>
 __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(const PushFixArgs a) {
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
@@ -195,7 +205,6 @@ __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(c
     c.mask = (1u << a.fb) - 1u;
     c.one = 1LL << a.fb;
     c.top = static_cast<long long>(a.nz) << a.fb;    // first position past the tube
-    c.utop = static_cast<unsigned>(c.top);            // <= 2^31
     c.dt = a.dt;
     c.cfl = a.cfl;
     c.scale = a.scale;
