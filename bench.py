@@ -36,6 +36,7 @@ UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 16          # FP32 xi and u, read once and written once per step
 CSRC = os.path.join(ROOT, "paper_1011_6330_gb300", "csrc")
 KERNEL_SRC = {"gr1e8": ["push.cu", "device_common.cuh", "sclf_internal.h"],
+              "gr1e8_fix32": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"],
               "large": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"],
               "batch": ["push.cu", "device_common.cuh", "sclf_internal.h"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
@@ -59,9 +60,13 @@ def parse():
                          "profiling case with the same particles per cell")
     ap.add_argument("--order", choices=["descending", "shuffled"], default="descending")
     ap.add_argument("--accumulate", choices=["fixed64", "fp64"], default="fixed64")
-    ap.add_argument("--precision", choices=["f32", "fix32"], default="f32",
-                    help="gr1e8: particle positions as float32 or as 32-bit fixed point "
-                         "(SCLF_FIX32; momenta float32 either way)")
+    ap.add_argument("--precision", choices=["f32", "fix32"], default="fix32",
+                    help="gr1e8: particle positions as 32-bit fixed point (SCLF_FIX32, "
+                         "default) or as float32; momenta float32 either way")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="gr1e8: only the headline measurement (no precision comparison, "
+                         "no other-precision or FP64-accumulator figures, no batched or "
+                         "adjoint forms)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -99,9 +104,24 @@ def combine_ranks(work, seconds, device="cpu"):
     return float(w.item()), float(t.item())
 
 
-def gr_workload_name(n, nz=65536):
+def gr_workload_name(n, nz=65536, precision="fix32"):
     """Name of the frame-dragging tube workload (both arms print the same)."""
-    return "gr_tube_P0.5s_B1e12G_Nz%d_%g_particles_fp32" % (nz, n)
+    return "gr_tube_P0.5s_B1e12G_Nz%d_%g_particles_%s" % (
+        nz, n, "fix32" if precision == "fix32" else "fp32")
+
+
+def host_info():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
 def barrier(ws):
@@ -274,7 +294,8 @@ def run_reference(args):
     gfar = cu["Lambda0"] ** 2 * cu["kappa"] * math.cos(0.5)
     z, u = synth.prefilled_beam(n // stride, L - dz, gfar, seed=0, order=args.order,
                                 eta_of_z=lambda zz: 1.0 + zz * cu["R_over_Rstar"])
-    o = orc.Tube(nz, L, dt, rho, s * stride, precision="f32", accumulate="fixed")
+    prec = "fix32" if args.precision == "fix32" else "f32"
+    o = orc.Tube(nz, L, dt, rho, s * stride, precision=prec, accumulate="fixed")
     o.add_particles(z, u)
     o.solve_fields()
     for _ in range(args.warmup):
@@ -289,21 +310,21 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": gr_workload_name(n),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fix32+f32" if prec == "fix32" else "f32", "data": "synthetic",
+        "config": {"workload": gr_workload_name(n, nz, args.precision),
                    "sample": "every %dth particle (%d), macro charge x%d" % (stride, z.size, stride),
                    "l2": "inputs larger than L2 on the GPU arm"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d particles of the 1e8-particle state, Nz=%d, %d steps"
-                                   % (z.size, nz, args.steps)},
+                                   % (z.size, nz, args.steps), "host": host_info()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def run_batch(args):
+def run_batch(args, sub=False):
     """The death-line batch: 256 seeded pulsar tubes (flat and frame-dragging,
     Nz 1024..16384, 1e5..2e6 FP32 particles each) stepped by batched launches;
     reported next to the plain form (the same tubes stepped one at a time)."""
@@ -312,7 +333,7 @@ def run_batch(args):
     from paper_1011_6330_gb300 import synth, workloads
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
+    if ws > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kws = workloads.death_line_batch(seed=rank_seed(rank))
@@ -483,11 +504,13 @@ def run_batch(args):
         "clocks": clk,
         "status": {"check": int(max(t.check() for t in batch.tubes))},
     }
-    if rank == 0:
+    if rank == 0 and not sub:
         print(json.dumps(line))
     batch.close()
     for t in plain:
         t.close()
+    if sub:
+        return line
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -533,7 +556,7 @@ def adjoint_cpu_baseline(kw, d, z, u, seconds, stride=100):
                       % (n, z[::stride].size, z.size, stride, stride, nz, el)}
 
 
-def run_adjoint(args):
+def run_adjoint(args, sub=False):
     """Gradients of the mean terminal gamma with respect to (B, P, R, w) for a
     2000-step run of the B = 1e12 G, P = 0.3 s frame-dragging tube (Nz =
     16384, 1e6 FP32 electrons), checkpointed every 100 steps: one timed
@@ -544,7 +567,7 @@ def run_adjoint(args):
     from paper_1011_6330_gb300 import workloads
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
+    if ws > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kw = workloads.adjoint_tube()
@@ -728,12 +751,115 @@ def run_adjoint(args):
         "gpu_launches": int(n_eval * (sum(per_eval.values()) + 4 + nseg - 1)),
         "clocks": clk,
     }
-    if rank == 0:
+    if rank == 0 and not sub:
         print(json.dumps(line))
     a.close()
+    if sub:
+        return line
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+PREC_N, PREC_STEPS, PREC_BINS = 500000, 2000, 64
+
+
+def binned_profiles(z, u, ez, L, nb):
+    """Mean gamma per height bin, E_z averaged over each bin's cells, and the
+    particle count per bin."""
+    edges = np.linspace(0.0, L, nb + 1)
+    idx = np.clip(np.digitize(z, edges) - 1, 0, nb - 1)
+    cnt = np.bincount(idx, minlength=nb)
+    g = np.sqrt(1.0 + np.asarray(u, np.float64) ** 2)
+    gm = np.bincount(idx, weights=g, minlength=nb) / np.maximum(cnt, 1)
+    return gm, np.asarray(ez).reshape(nb, -1).mean(axis=1), cnt
+
+
+def precision_vs_fp64(B, workloads, seed):
+    """The headline tube's grid and time step with PREC_N particles of the
+    same kind of seeded prefilled beam, PREC_STEPS steps with FIX32, float32
+    and FP64 positions on the GPU; the 32-bit runs against the FP64 run
+    (which the GPU tests hold to the FP64 oracle within 1e-12): binned gamma
+    and E_z (PREC_BINS height bins), E_z cell by cell, particle count per bin."""
+    from paper_1011_6330_gb300 import synth
+    kw = workloads.gr_tube(n_particles=PREC_N, precision=B.SCLF_FP64,
+                           accumulate=B.SCLF_ACC_FIXED64)
+    d = B.derive(B.default_params(**kw))
+    L = d["L"]
+    gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
+    z, u = synth.prefilled_beam(PREC_N, L - d["dz"], gfar, seed=seed,
+                                eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
+    runs = {}
+    for name, prec in (("fp64", B.SCLF_FP64), ("fix32", B.SCLF_FIX32), ("f32", B.SCLF_FP32)):
+        t = B.Tube(B.default_params(**dict(kw, precision=prec)))
+        t.add_particles(z, u)
+        t.solve_fields()
+        t.run(PREC_STEPS)
+        zz, uu, _ = t.read_particles()
+        ez = t.read_fields(rho=False)["ez"]
+        runs[name] = (binned_profiles(zz, uu, ez, L, PREC_BINS), ez)
+        t.close()
+    (g0, e0, c0), ez0 = runs["fp64"]
+    occ = c0 > 0
+    out = {"reference": "FP64 particle positions and momenta on the GPU",
+           "particles": PREC_N, "steps": PREC_STEPS, "bins": PREC_BINS,
+           "how": "max |x - x_fp64| / max |x_fp64| per quantity (gamma bins: per bin, "
+                  "relative to the bin's FP64 mean)"}
+    for name in ("fix32", "f32"):
+        (g, e, c), ez = runs[name]
+        out[name] = {"gamma_bins": float(np.max(np.abs(g[occ] - g0[occ]) / g0[occ])),
+                     "ez_bins": float(np.max(np.abs(e - e0)) / np.max(np.abs(e0))),
+                     "ez_cells": float(np.max(np.abs(ez - ez0)) / np.max(np.abs(ez0))),
+                     "count_bins": float(np.max(np.abs(c - c0))) / float(np.max(c0))}
+    return out
+
+
+def secondary_tube(B, workloads, n, precision, acc, order, seed, steps, warmup):
+    """Push time and roofline of the headline tube with another particle
+    precision or current accumulator (same seeded state)."""
+    t, kw, d, _, _, _ = build_tube(B, workloads, "gr1e8", n, acc, order, seed,
+                                   precision=precision)
+    t.solve_fields()
+    t.run(warmup)
+    t.set_timing(True)
+    t.run(steps)
+    tm = t.timing()
+    t.close()
+    push_ms = tm["push_ms"] / max(tm["n_steps"], 1)
+    slots = tm["particle_slots"] / max(tm["n_steps"], 1)
+    peak, kind = measured_peaks()
+    achieved = BYTES_PER_PARTICLE * slots / (push_ms * 1e-3) / 1e9
+    return {"positions": precision, "current_accumulator": "fp64" if acc == B.SCLF_ACC_FP64
+            else "fixed64", "steps": steps, "push_ms_avg": push_ms,
+            "particle_steps_per_s_push": slots / (push_ms * 1e-3),
+            "roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": kind}}
+
+
+def form_summary(line, headline_value):
+    """The batched or adjoint form's figures next to its plain form."""
+    pf = line["plain_form"]
+    roof = line.get("roofline") or {}
+    out = {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+           "steps": line["steps"], "plain_value": pf["value"],
+           "vs_plain": line["value"] / pf["value"], "plain_how": pf["how"],
+           "vs_headline": line["value"] / headline_value,
+           "roofline": {k: roof.get(k) for k in ("kernel", "achieved", "peak", "frac",
+                                                  "push_ms_avg", "bytes_per_launch")},
+           "clocks": line["clocks"]}
+    if "adjoint" in line:
+        a = line["adjoint"]
+        out["forward_ms"], out["backward_ms"] = a["forward_ms"], a["backward_ms"]
+        out["fp32_vs_fp64_grad_rel_err"] = a["fp32_vs_fp64_grad_rel_err"]
+    return out
+
+
+def sub_args(args, **kw):
+    """A copy of the arguments for a form measured inside the default run."""
+    d = dict(vars(args))
+    d.update(no_e2e=True, no_cpu_baseline=True, no_kernel_timing=False)
+    d.update(kw)
+    return argparse.Namespace(**d)
 
 
 def main():
@@ -802,11 +928,13 @@ def main():
     achieved = BYTES_PER_PARTICLE * slots_per_launch / (push_avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
+    fix32 = large or args.precision == "fix32"
+    tkey = args.workload + ("_fix32" if fix32 and not large else "")
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        ent = tr.get(args.workload, {})
-        if ent.get("kernel_sha") == kernel_sha(args.workload) \
+        ent = tr.get(tkey, {})
+        if ent.get("kernel_sha") == kernel_sha(tkey) \
                 and ent.get("accumulate", "fixed64") == args.accumulate \
                 and ent.get("order", "descending") == args.order and ent.get("particles") == n:
             traffic = ent["bytes_per_launch"]
@@ -856,19 +984,26 @@ def main():
                                       + ksteps * 144) / ksteps,   # 144-byte counter block
                "path": "tube_load_particles(pinned) + K x (tube_status_async, tube_step) + "
                        "tube_save_particles(pinned) + K x tube_status_collect",
+               "amortised_over_steps": ksteps,
+               "note": "the whole particle state goes in and comes back once per K = %d "
+                       "steps; per-step copies are the 144-byte counter block" % ksteps,
                "rc": int(rc)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(zs, us, n, kw, d, args.cpu_seconds, stride)
+        cpu["host"] = host_info()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "fix32+f32" if large else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "fix32+f32" if fix32 else "f32",
         "data": "synthetic",
         "config": {"workload": ("large_tube_P0.1s_B3e12G_Nz%d_%d_particles_fix32" % (kw["Nz"], n))
-                   if large else gr_workload_name(n, kw["Nz"]),
+                   if large else gr_workload_name(n, kw["Nz"], args.precision),
+                   "positions": ("32-bit fixed point, 2^-%d cell (SCLF_FIX32)"
+                                 % (31 - int(math.ceil(math.log2(kw["Nz"]))))) if fix32
+                   else "float32",
                    "rho_gj": "frame-dragging (Eq. 6-7), i = 0.5 rad",
                    "particles_per_gpu": n, "Nz": kw["Nz"], "Lambda0": d["Lambda0"],
                    "dt_R_over_c": d["dt"], "order": args.order,
@@ -881,7 +1016,7 @@ def main():
                    "parallelism": "independent tube per GPU" if ws > 1 else "single tube"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "push_fix32_kernel" if large else
+                     "kernel": "push_fix32_kernel" if fix32 else
                      ("push_kernel<float, fixed64>" if acc == B.SCLF_ACC_FIXED64
                       else "push_kernel<float, fp64>"),
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
@@ -897,9 +1032,21 @@ def main():
                    "injected_per_step": (st1["total_injected"] - st0["total_injected"]) / args.steps,
                    "flags": st1["flags"]},
     }
+    t.close()
+    # the same workload in its other forms, measured after the headline (N = 1)
+    if not args.no_extras and ws == 1 and not large:
+        other = "f32" if fix32 else "fix32"
+        line["precision_vs_fp64"] = precision_vs_fp64(B, workloads, rank_seed(rank))
+        line["other_positions"] = secondary_tube(B, workloads, n, other, B.SCLF_ACC_FIXED64,
+                                                 args.order, rank_seed(rank), 100, 5)
+        line["fp64_accumulator"] = secondary_tube(B, workloads, n, "f32", B.SCLF_ACC_FP64,
+                                                  args.order, rank_seed(rank), 50, 5)
+        line["batched"] = form_summary(run_batch(sub_args(args, steps=64, warmup=5), sub=True),
+                                       value)
+        line["adjoint"] = form_summary(run_adjoint(sub_args(args, steps=2000, warmup=4),
+                                                   sub=True), value)
     if rank == 0:
         print(json.dumps(line))
-    t.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

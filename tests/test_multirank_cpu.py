@@ -63,5 +63,7 @@ def test_single_process_combine_is_identity():
     import bench
     assert bench.combine_ranks(123.0, 4.5) == (123.0, 4.5)
     bench.barrier(1)                                     # no process group needed on one GPU
-    assert bench.gr_workload_name(10 ** 8) == "gr_tube_P0.5s_B1e12G_Nz65536_1e+08_particles_fp32"
+    assert bench.gr_workload_name(10 ** 8) == "gr_tube_P0.5s_B1e12G_Nz65536_1e+08_particles_fix32"
+    assert bench.gr_workload_name(10 ** 8, 65536, "f32") == \
+        "gr_tube_P0.5s_B1e12G_Nz65536_1e+08_particles_fp32"
     assert len({bench.rank_seed(r) for r in range(8)}) == 8
