@@ -380,6 +380,83 @@ int tube_set_timing(tube_t t, int enable);
 /* Accumulated timings since timing was enabled. Synchronises. */
 int tube_get_timing(tube_t t, tube_timing* out);
 
+/* ---- one tube split into z-domains ------------------------------------------
+ * A tube's cells cut into contiguous ranges ("sub-domains"), each with its own
+ * particle slots, stream and copy of the grids, as a multi-GPU run would hold
+ * them; here all sub-domains share one GPU. The split follows Sec. 2: Eq. 3
+ * couples a cell only to its neighbours (B_phi of the adjacent cells, E_r at
+ * the cell's two nodes), the cloud-in-cell gather reads the cell and its
+ * neighbour, and a particle moves less than one cell per step (c dt < dz),
+ * so each step a sub-domain exchanges with each neighbour: the current its
+ * particles deposited in the neighbour's first cell, the neighbour's new
+ * B_phi and E_z of that cell (E_r at the shared node is computed on both
+ * sides from the same values), and the particles that crossed. Every step
+ * runs: particle kernels (one per sub-domain, concurrently) -> current
+ * exchange -> field kernels -> particle hand-off and field halos. The
+ * current is the exact fixed-point sum, so a decomposed run gives the same
+ * fields bit for bit as the same tube stepped whole, and the same particles
+ * (compared by ID; their slot order differs). Requires SCLF_ACC_FIXED64;
+ * every sub-domain has at least 2 cells. Only the base sub-domain injects. */
+typedef struct sclf_dtube* dtube_t;   /* opaque, library-owned */
+
+/* Create a tube of parameters *p split at the cell boundaries cuts[0..n]
+ * (host array: cuts[0] = 0 < cuts[1] < ... < cuts[n] = Nz, every range at
+ * least 2 cells), or into n near-equal ranges when cuts is NULL; 1 <= n <= 64.
+ * Each sub-domain holds the tube's full capacity of slots and its own copy
+ * of the grids (only its cells and their neighbours are kept current), plus
+ * two outboxes of max(65536, capacity/8) particles for the particles that
+ * leave it; an outbox overflow sets SCLF_FLAG_CAPACITY. The fields start as
+ * the empty tube's (Eq. 4 without particles). Synchronises. EINVAL for bad
+ * cuts, accumulate != SCLF_ACC_FIXED64 or invalid params. */
+int dtube_create(const tube_params* p, int32_t n, const int64_t* cuts, dtube_t* out);
+
+/* Free every sub-domain and the exchange buffers. */
+int dtube_destroy(dtube_t dt);
+
+/* Number of sub-domains, and sub-domain i's tube and owned cells [lo, hi).
+ * The tube is for reading (tube_read_particles, tube_save_particles,
+ * tube_status, tube_read_fields: only cells lo-1..hi of its grids are
+ * current); stepping it alone returns SCLF_ESTATE. */
+int dtube_domains(dtube_t dt, int32_t* n);
+int dtube_domain(dtube_t dt, int32_t i, tube_t* tube, int64_t* lo, int64_t* hi);
+
+/* The tube's initial particles (host heights z in [0, L) in units of R, and
+ * u = gamma beta; ID k for particle k), each given to the sub-domain of its
+ * cell. Only on a tube that has no particles and has not stepped (ESTATE
+ * otherwise). Synchronises. */
+int dtube_load_particles(dtube_t dt, int64_t n, const double* z, const double* u);
+
+/* Set every sub-domain's fields from host arrays: E_z at the Nz cells, E_r
+ * at the Nz+1 nodes, B_phi at the Nz cells (NULL: zero); the next injection
+ * count follows from them (Sec. 2). Synchronises. */
+int dtube_set_fields(dtube_t dt, const double* Ez, const double* Er, const double* Bphi);
+
+/* Eq. 4 with the charge of every sub-domain's particles (as
+ * tube_solve_fields; the density is summed over the sub-domains in FP64, so
+ * its last bits can differ from a whole tube's). Synchronises. */
+int dtube_solve_fields(dtube_t dt);
+
+/* One step (Figure A) of every sub-domain with its exchanges. Async. */
+int dtube_step(dtube_t dt);
+int dtube_run(dtube_t dt, int64_t nsteps);
+
+/* The whole tube's counters: live particles, slots, removals and flags
+ * summed (flags OR-ed) over the sub-domains, injection counters of the base
+ * sub-domain. Synchronises. */
+int dtube_status(dtube_t dt, tube_stats* out);
+
+/* The whole tube's fields (caller-owned host arrays, NULL skips): each cell
+ * (and node) from the sub-domain that owns it; the last node from the top
+ * sub-domain. Synchronises. */
+int dtube_read_fields(dtube_t dt, double* Ez, double* Er, double* Bphi, double* J);
+
+/* Data exchanged between sub-domains since creation: *steps, *field_bytes
+ * (current, B_phi and E_z halo values), *particles (particles handed to a
+ * neighbour) and *particle_bytes (their positions, momenta and IDs).
+ * Synchronises. */
+int dtube_exchange_stats(dtube_t dt, int64_t* steps, int64_t* field_bytes, int64_t* particles,
+                         int64_t* particle_bytes);
+
 /* ---- batches of independent tubes -------------------------------------------
  * Many tubes (each its own pulsar: B, P, R, Nz, rho_GJ profile, particles)
  * advanced together: every step is one particle launch over all tubes'

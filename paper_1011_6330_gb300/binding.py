@@ -107,6 +107,18 @@ SIGNATURES = {
                                        C.POINTER(C.c_uint32)]),
     "tube_set_timing": (_i32, [_vp, _i32]),
     "tube_get_timing": (_i32, [_vp, C.POINTER(TubeTiming)]),
+    "dtube_create": (_i32, [C.POINTER(TubeParams), C.c_int32, _pi64, C.POINTER(_vp)]),
+    "dtube_destroy": (_i32, [_vp]),
+    "dtube_domains": (_i32, [_vp, C.POINTER(C.c_int32)]),
+    "dtube_domain": (_i32, [_vp, C.c_int32, C.POINTER(_vp), _pi64, _pi64]),
+    "dtube_load_particles": (_i32, [_vp, _i64, _pd, _pd]),
+    "dtube_set_fields": (_i32, [_vp, _pd, _pd, _pd]),
+    "dtube_solve_fields": (_i32, [_vp]),
+    "dtube_step": (_i32, [_vp]),
+    "dtube_run": (_i32, [_vp, _i64]),
+    "dtube_status": (_i32, [_vp, C.POINTER(TubeStats)]),
+    "dtube_read_fields": (_i32, [_vp, _pd, _pd, _pd, _pd]),
+    "dtube_exchange_stats": (_i32, [_vp, _pi64, _pi64, _pi64, _pi64]),
     "batch_create": (_i32, [C.c_int32, C.POINTER(TubeParams), _vp, C.POINTER(_vp)]),
     "batch_destroy": (_i32, [_vp]),
     "batch_size": (_i32, [_vp, C.POINTER(C.c_int32)]),
@@ -406,6 +418,95 @@ class _TubeView(Tube):
         self.h = None
 
 
+class DTube:
+    """One tube split into z-ranges of cells (sub-domains), each with its
+    own slots, stream and grid copy, stepped with the per-step exchanges a
+    multi-GPU run makes (include/sclf_tube.h, dtube_*). n sub-domains of
+    near-equal size, or the cell boundaries `cuts` (n + 1 values)."""
+
+    def __init__(self, params, n=2, cuts=None):
+        self.lib = load()
+        self.params = params
+        self.h = _vp()
+        c = None
+        if cuts is not None:
+            cuts = np.ascontiguousarray(cuts, dtype=np.int64)
+            n = cuts.size - 1
+            c = cuts.ctypes.data_as(_pi64)
+        _check(self.lib.dtube_create(C.byref(params), int(n), c, C.byref(self.h)),
+               "dtube_create")
+        self.nz = int(params.Nz)
+        self.n = int(n)
+
+    def close(self):
+        if self.h:
+            _check(self.lib.dtube_destroy(self.h), "dtube_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def domain(self, i):
+        """(tube, lo, hi): sub-domain i's tube (for reading) and its cells."""
+        t, lo, hi = _vp(), C.c_int64(), C.c_int64()
+        _check(self.lib.dtube_domain(self.h, int(i), C.byref(t), C.byref(lo), C.byref(hi)),
+               "dtube_domain")
+        return _TubeView(self.lib, t, self.params), lo.value, hi.value
+
+    def load_particles(self, z, u):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(self.lib.dtube_load_particles(self.h, z.size, _dptr(z), _dptr(u)),
+               "dtube_load_particles")
+
+    def set_fields(self, ez, er, b=None):
+        ez = np.ascontiguousarray(ez, dtype=np.float64)
+        er = np.ascontiguousarray(er, dtype=np.float64)
+        b = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        _check(self.lib.dtube_set_fields(self.h, _dptr(ez), _dptr(er), _dptr(b)),
+               "dtube_set_fields")
+
+    def solve_fields(self):
+        _check(self.lib.dtube_solve_fields(self.h), "dtube_solve_fields")
+
+    def step(self):
+        _check(self.lib.dtube_step(self.h), "dtube_step")
+
+    def run(self, nsteps):
+        _check(self.lib.dtube_run(self.h, int(nsteps)), "dtube_run")
+
+    def status(self):
+        s = TubeStats()
+        _check(self.lib.dtube_status(self.h, C.byref(s)), "dtube_status")
+        return {n: getattr(s, n) for n, _ in TubeStats._fields_}
+
+    def read_fields(self):
+        nz = self.nz
+        f = {"ez": np.empty(nz), "er": np.empty(nz + 1), "b": np.empty(nz), "j": np.empty(nz)}
+        _check(self.lib.dtube_read_fields(self.h, _dptr(f["ez"]), _dptr(f["er"]),
+                                          _dptr(f["b"]), _dptr(f["j"])), "dtube_read_fields")
+        return f
+
+    def read_particles(self):
+        """All sub-domains' live particles (z, u, ids), in ID order."""
+        parts = [self.domain(i)[0].read_particles() for i in range(self.n)]
+        z = np.concatenate([p[0] for p in parts])
+        u = np.concatenate([p[1] for p in parts])
+        ids = np.concatenate([p[2] for p in parts])
+        o = np.argsort(ids, kind="stable")
+        return z[o], u[o], ids[o]
+
+    def exchange_stats(self):
+        v = [C.c_int64() for _ in range(4)]
+        _check(self.lib.dtube_exchange_stats(self.h, *[C.byref(x) for x in v]),
+               "dtube_exchange_stats")
+        return dict(zip(("steps", "field_bytes", "particles", "particle_bytes"),
+                        (x.value for x in v)))
+
+
 class Batch:
     """Independent tubes stepped together by batched launches."""
 
@@ -660,4 +761,4 @@ def header_functions(path=HEADER):
     import re
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:tube|batch|adjoint)_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:tube|dtube|batch|adjoint)_[a-z_]+)\s*\(", text)))

@@ -55,7 +55,7 @@ __device__ __forceinline__ void field_store(const FieldArgs<Real>& a, int j,
     const double bjp = (j + 1 < nz) ? in.bp : bj;
     const double erj1 = in.er1 - a.c.cdt * (bjp - bj);
     a.er_out[j] = erj;
-    if (j == nz - 1) a.er_out[nz] = erj1;
+    if (j == a.hi - 1) a.er_out[a.hi] = erj1;     // the last node (a sub-domain's: shared)
     a.b_out[j] = bj - a.c.cdt * (erj1 - erj) - a.c.dt * ez1;
 
     // gather table of the next step: entry m = (E_{m-1/2}, E_{m+1/2}), ends clamped
@@ -65,8 +65,9 @@ __device__ __forceinline__ void field_store(const FieldArgs<Real>& a, int j,
     if (j == 0) a.ez2[0] = e;
     if (j == nz - 1) a.ez2[2 * nz + 1] = e;
 
-    if (j == 0) {
-        // commit of the step's counters and the next injection count
+    if (j == a.lo) {
+        // commit of the step's counters and the next injection count (only the
+        // sub-domain at the base injects)
         DevState* st = a.st;
         const long long inj = st->inj_done;
         const long long rem = static_cast<long long>(st->acc_removed);
@@ -77,9 +78,9 @@ __device__ __forceinline__ void field_store(const FieldArgs<Real>& a, int j,
         st->last_removed = rem;
         if (a.evlog) a.evlog[kLogStride * st->step + kLogRemoved] = rem;
         st->w0 = static_cast<long long>(st->acc_w0);
-        long long n;
-        double es;
-        injection_count(ez1, st->w0, a.c, &n, &es);
+        long long n = 0;
+        double es = 0.0;
+        if (j == 0) injection_count(ez1, st->w0, a.c, &n, &es);
         st->n_inj = n;
         st->surface_field = es;
         st->acc_w0 = 0;
@@ -99,8 +100,8 @@ __device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
 
 template <class Real, int kAcc>
 __global__ void __launch_bounds__(256) field_kernel(const FieldArgs<Real> a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.c.nz) return;
+    const int j = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.hi) return;
     field_cell<Real, kAcc>(a, j);
 }
 
@@ -123,6 +124,8 @@ __device__ __forceinline__ FieldArgs<float> batch_field_args(const BatchTube& d,
     a.ez2 = d.ez2;
     a.evlog = nullptr;
     a.c = d.fc;
+    a.lo = 0;
+    a.hi = d.nz;
     return a;
 }
 
@@ -163,7 +166,7 @@ batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ 
 
 template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate, cudaStream_t s) {
-    const int grid = (a.c.nz + 255) / 256;
+    const int grid = (a.hi - a.lo + 255) / 256;
     if (accumulate == kAccFixed) field_kernel<Real, kAccFixed><<<grid, 256, 0, s>>>(a);
     else field_kernel<Real, kAccF64><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();

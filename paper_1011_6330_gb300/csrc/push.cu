@@ -65,7 +65,24 @@ struct TileCtx {
     long long n_slots, n_tot, id0;
     Real nzf, dt, cfl;
     int nz;
+    Real lof, hif;             // owned cells [lof, hif) (a sub-domain; 0, nzf: whole tube)
+    Outbox out_down, out_up;   // used only when a particle leaves [lof, hif) inside the tube
 };
+
+// A particle that leaves the sub-domain for a neighbour's cells: appended to
+// that side's outbox (an overflow sets SCLF_FLAG_CAPACITY and loses it).
+template <class P, class M>
+__device__ __forceinline__ void emigrate(const Outbox& ob, P x, M u, long long id,
+                                         unsigned int* flags) {
+    const unsigned long long k = ob.n ? atomicAdd(ob.n, 1ULL) : ~0ULL;
+    if (k < static_cast<unsigned long long>(ob.cap)) {
+        static_cast<P*>(ob.x)[k] = x;
+        static_cast<M*>(ob.u)[k] = u;
+        if (ob.ids) ob.ids[k] = id;
+    } else {
+        atomicOr(flags, SCLF_FLAG_CAPACITY);
+    }
+}
 
 // One tile of kThreads * kPPT slots: thread t owns slots [i0, i0 + kPPT)
 // (kPPT defaults to the precision's layout; the batched kernel varies it).
@@ -178,10 +195,15 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
                 }
                 if (qa != AccT(0) && checked_index(c0, nz, c.flags)) acc_add(jacc + c0, qa);
                 // (a5) removal at the ends; base-cell weight for the next injection
-                if (x1 >= Real(0) && x1 < nzf) {
+                if (x1 >= c.lof && x1 < c.hif) {
                     xs[k] = x1;
                     us[k] = u1;
                     if (x1 < Real(1)) w0_acc += to_fixed(Real(1) - x1);
+                } else if (x1 >= Real(0) && x1 < nzf) {   // to a neighbouring sub-domain
+                    emigrate<Real, Real>(x1 < c.lof ? c.out_down : c.out_up, x1, u1,
+                                         c.ids ? c.ids[i0 + k] : -1LL, c.flags);
+                    xs[k] = Real(-1);
+                    us[k] = Real(0);
                 } else {
                     ++removed;
                     xs[k] = Real(-1);
@@ -282,6 +304,10 @@ push_kernel(const PushArgs<Real> a) {
     c.dt = a.dt;
     c.cfl = a.cfl;
     c.nz = a.nz;
+    c.lof = static_cast<Real>(a.lo);
+    c.hif = static_cast<Real>(a.hi);
+    c.out_down = a.out_down;
+    c.out_up = a.out_up;
     const long long ntiles = (c.n_tot + kTile - 1) / kTile;
 
     long long w0_acc = 0;
@@ -382,6 +408,9 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         c.dt = d.dt;
         c.cfl = d.cfl;
         c.nz = d.nz;
+        c.lof = 0.0f;
+        c.hif = d.nzf;
+        c.out_down = c.out_up = Outbox{};
         // the next tile's descriptor line into L1 while this tile computes
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
         push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
@@ -425,6 +454,9 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
         c.dt = kc.dt;
         c.cfl = kc.cfl;
         c.nz = kc.nz;
+        c.lof = 0.0f;
+        c.hif = kc.nzf;
+        c.out_down = c.out_up = Outbox{};
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
         push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
         flush_tube_counters(kc.st, w0, removed, nonfinite);

@@ -28,7 +28,22 @@ struct FixCtx {
     unsigned half, mask;
     long long one, top;
     float dt, cfl, scale, two_fb;
+    long long lo_x, hi_x;      // owned positions [lo 2^fb, hi 2^fb) (0, top: whole tube)
+    Outbox out_down, out_up;
 };
+
+// A particle that leaves the sub-domain for a neighbour's cells (see push.cu).
+__device__ __forceinline__ void emigrate_fix(const Outbox& ob, int X, float u, long long id,
+                                             unsigned int* flags) {
+    const unsigned long long k = ob.n ? atomicAdd(ob.n, 1ULL) : ~0ULL;
+    if (k < static_cast<unsigned long long>(ob.cap)) {
+        static_cast<int*>(ob.x)[k] = X;
+        static_cast<float*>(ob.u)[k] = u;
+        if (ob.ids) ob.ids[k] = id;
+    } else {
+        atomicOr(flags, SCLF_FLAG_CAPACITY);
+    }
+}
 
 // One tile of kThreads * kPPT slots whose thread's slots are in xs, us.
 __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
@@ -62,14 +77,15 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
             if (k >= k_tot) xs[k] = -1;
     }
     // Runs on the first slot's cell c_r and on c_r + 1, when c_r lies in
-    // [1, Nz - 2]; A = c_r 2^fb, else A = 0xc0000000, which puts U - A at or
+    // [1, hi - 2] (hi = Nz for a whole tube, else the sub-domain's end, so a
+    // common particle never leaves it); A = c_r 2^fb, else A = 0xc0000000, which puts U - A at or
     // above 2^30 >= 2^fb for every position U < 2^31 (no particle is common).
     // A common particle starts in c_r (U - A < 2^fb: live, cell >= 1) and
     // ends in c_r or c_r + 1 (U1 - A < 2^(fb+1): inside the tube); in 2^-fb
     // units its current is F_cr(X1) - F_cr(X) = min(U1 - A, 2^fb) - (U - A)
     // on c_r and max(U1 - A - 2^fb, 0) on c_r + 1, so the runs keep the sum
     // of the increments and the sum of the parts above c_r.
-    const bool has_run = xs[0] >= static_cast<int>(one) && xs[0] < top - one;
+    const bool has_run = xs[0] >= static_cast<int>(one) && xs[0] < c.hi_x - one;
     const unsigned A = has_run ? (static_cast<unsigned>(xs[0]) & ~mask) : 0xc0000000u;
     const unsigned one_u = 1u << fb, two_u = 2u << fb;
     int s_inc = 0, s_over = 0;
@@ -123,10 +139,15 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
                     if (qb) acc_add(jacc + static_cast<int>(c1), qb);
                 }
                 // (a5) removal at the ends; base-cell weight for the next injection
-                if (X1 >= 0 && X1 < top) {
+                if (X1 >= c.lo_x && X1 < c.hi_x) {
                     xs[k] = static_cast<int>(X1);
                     us[k] = u1;
                     if (c1 == 0) w0_acc += shl_signed(one - X1, sh);
+                } else if (X1 >= 0 && X1 < top) {         // to a neighbouring sub-domain
+                    emigrate_fix(X1 < c.lo_x ? c.out_down : c.out_up, static_cast<int>(X1), u1,
+                                 c.ids ? c.ids[i0 + k] : -1LL, c.flags);
+                    xs[k] = -1;
+                    us[k] = 0.0f;
                 } else {
                     ++removed;
                     xs[k] = -1;
@@ -209,6 +230,10 @@ __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(c
     c.cfl = a.cfl;
     c.scale = a.scale;
     c.two_fb = a.two_fb;
+    c.lo_x = static_cast<long long>(a.lo) << a.fb;
+    c.hi_x = static_cast<long long>(a.hi) << a.fb;
+    c.out_down = a.out_down;
+    c.out_up = a.out_up;
     const long long ntiles = (c.n_tot + kTile - 1) / kTile;
 
     long long w0_acc = 0;

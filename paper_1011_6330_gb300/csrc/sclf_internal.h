@@ -70,6 +70,19 @@ struct DevState {
     long long pad1[2];
 };
 
+// Particles that leave a sub-domain's cell range for a neighbour's (z-domain
+// decomposition of one tube): the particle kernel appends them here (one
+// outbox per direction); the decomposed tube's exchange moves them into the
+// neighbour's slots after the step. x holds positions in the tube's particle
+// format (Real, or int32 for SCLF_FIX32).
+struct Outbox {
+    void* x;
+    void* u;
+    long long* ids;            // null when the tube keeps no IDs
+    unsigned long long* n;     // count (atomically incremented); null: no outbox
+    long long cap;
+};
+
 // Per-step event log of a recorded run: kLogStride entries per step, indexed
 // by the step counter DevState::step.
 constexpr int kLogStride = 4;
@@ -102,6 +115,10 @@ struct PushArgs {
     Real nzf;                  // (Real)nz
     Real dt;                   // (Real)dt
     Real cfl;                  // (Real)(dt/dz)
+    // owned cells [lo, hi) of a sub-domain (0, nz for a whole tube): a particle
+    // that ends inside the tube but outside them goes to out_down / out_up
+    int lo, hi;
+    Outbox out_down, out_up;
 };
 
 template <class Real>
@@ -117,6 +134,7 @@ struct FieldArgs {
     Real* ez2;                 // gather table for the next step
     long long* evlog;          // may be null: records the step's removals
     FieldConsts c;
+    int lo, hi;                // cells updated: [lo, hi) (0, nz for a whole tube)
 };
 
 // Particle kernel of the SCLF_FIX32 mode: positions X = xi 2^fb (int32,
@@ -139,6 +157,8 @@ struct PushFixArgs {
     float cfl;                 // (float)(dt/dz)
     float scale;               // 2^-fb
     float two_fb;              // 2^fb
+    int lo, hi;                // owned cells (see PushArgs)
+    Outbox out_down, out_up;
 };
 
 template <class Pos, class Mom>

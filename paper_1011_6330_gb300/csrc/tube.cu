@@ -95,6 +95,10 @@ cudaError_t do_rho(sclf_tube* t, long long slots) {
                                          std::ldexp(1.0, -t->fb), t->stream);
     return launch_rho<float>(static_cast<const float*>(t->xi), slots, t->rho_acc, nz, 1.0, t->stream);
 }
+}  // namespace
+
+namespace sclf {
+
 // Position of raw slot i in cell units; negative for a hole.
 double raw_cells(const sclf_tube* t, const void* raw, int64_t i) {
     if (fp64(t)) return static_cast<const double*>(raw)[i];
@@ -131,6 +135,10 @@ cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s, int force) {
                    : launch_compact<float, float>(compact_args<float, float>(t, force), t->compact_grid, s);
 }
 
+
+}  // namespace sclf
+
+namespace {
 
 int drain_timing(sclf_tube* t);
 
@@ -312,6 +320,10 @@ void to_native(const double* z, const double* u, int64_t n, double dz, std::vect
     }
 }
 
+}  // namespace
+
+namespace sclf {
+
 // Append n raw particles (already in the tube's precision) after the slots.
 int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int64_t* id) {
     DevState h;
@@ -339,7 +351,54 @@ int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int
     return SCLF_OK;
 }
 
-}  // namespace
+// Checks physical heights z in [0, L) and finite u, and converts them to the
+// tube's raw particle format (cell units; FIX32: round-half-even(z/dz 2^fb)).
+int native_particles(const sclf_tube* t, int64_t n, const double* z, const double* u,
+                     std::vector<char>& xs, std::vector<char>& us) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!(z[i] >= 0.0 && z[i] < t->d.L) || !std::isfinite(u[i])) return SCLF_EINVAL;
+    if (fp64(t)) {
+        to_native<double>(z, u, n, t->d.dz, xs, us);
+    } else if (fix32(t)) {
+        to_native<float>(z, u, n, t->d.dz, xs, us);
+        int* X = reinterpret_cast<int*>(xs.data());
+        const double top = std::ldexp(double(t->p.Nz), t->fb);
+        for (int64_t i = 0; i < n; ++i) {
+            const double v = std::nearbyint(std::ldexp(z[i] / t->d.dz, t->fb));
+            if (!(v < top)) return SCLF_EINVAL;
+            X[i] = static_cast<int>(v);
+        }
+    } else {
+        to_native<float>(z, u, n, t->d.dz, xs, us);
+    }
+    // a position that rounds up to the top node is outside the tube
+    for (int64_t i = 0; i < n; ++i)
+        if (!(raw_cells(t, xs.data(), i) < double(t->p.Nz))) return SCLF_EINVAL;
+    return SCLF_OK;
+}
+
+// Host fields (E_z at the Nz cells, E_r at the Nz+1 nodes, B_phi at the cells)
+// into the tube's current copies, with the gather table, W_0 and the next
+// injection count brought up to date.
+int set_fields_host(sclf_tube* t, const double* ez, const double* er, const double* b) {
+    const int64_t nz = t->p.Nz;
+    const int par = static_cast<int>(t->host_step & 1);
+    CK(cudaMemcpyAsync(t->ez, ez, nz * 8, cudaMemcpyHostToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->er[par], er, (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream));
+    if (b) CK(cudaMemcpyAsync(t->b[par], b, nz * 8, cudaMemcpyHostToDevice, t->stream));
+    else CK(cudaMemsetAsync(t->b[par], 0, nz * 8, t->stream));
+    CK(do_ez_table(t));
+    DevState h;
+    const int rc = read_state(t, &h);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(&t->st->w0, 0, sizeof(long long), t->stream));
+    CK(do_base_weight(t, 0, h.n_slots));
+    CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    return SCLF_OK;
+}
+
+}  // namespace sclf
 
 namespace {
 
@@ -426,6 +485,8 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     t->p.gr_H = t->gr_H.empty() ? nullptr : t->gr_H.data();
     t->lay = plan(p);
     t->fb = p->precision == SCLF_FIX32 ? fix32_bits(p->Nz) : 0;
+    t->dom_lo = 0;                                   // the whole tube
+    t->dom_hi = static_cast<int>(p->Nz);
     t->stream = static_cast<cudaStream_t>(stream);
     t->compact_every = p->compact_interval > 0 ? p->compact_interval : 64;
     t->chunk_steps = t->compact_every + (t->compact_every & 1);
@@ -564,27 +625,9 @@ int tube_inject(tube_t t, int64_t* n_injected) {
 
 int tube_add_particles(tube_t t, int64_t n, const double* z, const double* u) {
     if (!t || n < 0 || (n > 0 && (!z || !u))) return SCLF_EINVAL;
-    for (int64_t i = 0; i < n; ++i)
-        if (!(z[i] >= 0.0 && z[i] < t->d.L) || !std::isfinite(u[i])) return SCLF_EINVAL;
     std::vector<char> xs, us;
-    if (fp64(t)) {
-        to_native<double>(z, u, n, t->d.dz, xs, us);
-    } else if (fix32(t)) {
-        // X = round-half-even(z / dz 2^fb)
-        to_native<float>(z, u, n, t->d.dz, xs, us);
-        int* X = reinterpret_cast<int*>(xs.data());
-        const double top = std::ldexp(double(t->p.Nz), t->fb);
-        for (int64_t i = 0; i < n; ++i) {
-            const double v = std::nearbyint(std::ldexp(z[i] / t->d.dz, t->fb));
-            if (!(v < top)) return SCLF_EINVAL;
-            X[i] = static_cast<int>(v);
-        }
-    } else {
-        to_native<float>(z, u, n, t->d.dz, xs, us);
-    }
-    // a position that rounds up to the top node is outside the tube
-    for (int64_t i = 0; i < n; ++i)
-        if (!(raw_cells(t, xs.data(), i) < double(t->p.Nz))) return SCLF_EINVAL;
+    const int rc = native_particles(t, n, z, u, xs, us);
+    if (rc) return rc;
     return append_raw(t, n, xs.data(), us.data(), nullptr);
 }
 
@@ -881,19 +924,7 @@ int tube_solve_fields(tube_t t) {
     for (int64_t j = 0; j <= nz; ++j) src[j] = t->rho_gj[j] - rho[j];
     solve_poisson(src.data(), nz, t->d.dz, phi.data());
     for (int64_t j = 0; j < nz; ++j) ez0[j] = -(phi[j + 1] - phi[j]) / t->d.dz;
-    const int par = static_cast<int>(t->host_step & 1);
-    CK(cudaMemcpyAsync(t->ez, ez0.data(), nz * 8, cudaMemcpyHostToDevice, t->stream));
-    CK(cudaMemcpyAsync(t->er[par], phi.data(), (nz + 1) * 8, cudaMemcpyHostToDevice, t->stream));
-    CK(cudaMemsetAsync(t->b[par], 0, nz * 8, t->stream));
-    CK(do_ez_table(t));
-    DevState h;
-    rc = read_state(t, &h);
-    if (rc) return rc;
-    CK(cudaMemsetAsync(&t->st->w0, 0, sizeof(long long), t->stream));
-    CK(do_base_weight(t, 0, h.n_slots));
-    CK(launch_finish_append(t->st, t->ez, 0, t->fc, t->stream));
-    CK(cudaStreamSynchronize(t->stream));
-    return SCLF_OK;
+    return set_fields_host(t, ez0.data(), phi.data(), nullptr);   // E_r = phi / R, B = 0
 }
 
 int tube_diagnostics(tube_t t, tube_diag* out) {

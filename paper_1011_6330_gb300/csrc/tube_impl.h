@@ -83,6 +83,10 @@ struct sclf_tube {
     static constexpr int64_t kStatusRing = 1024;
     sclf::DevState* status_ring = nullptr;
     int64_t status_next = 0;
+    // sub-domain of a decomposed tube: owned cells [dom_lo, dom_hi) and the
+    // outboxes of particles leaving them (a whole tube: 0, Nz, none)
+    int dom_lo = 0, dom_hi = 0;
+    sclf::Outbox out_down{}, out_up{};
 };
 
 namespace sclf {
@@ -124,6 +128,10 @@ inline PushArgs<Real> push_args(sclf_tube* t) {
     a.nzf = static_cast<Real>(t->p.Nz);
     a.dt = static_cast<Real>(t->d.dt);
     a.cfl = static_cast<Real>(t->d.dt / t->d.dz);
+    a.lo = t->dom_lo;
+    a.hi = t->dom_hi;
+    a.out_down = t->out_down;
+    a.out_up = t->out_up;
     return a;
 }
 
@@ -141,6 +149,8 @@ inline FieldArgs<Real> field_args(sclf_tube* t, int parity) {
     a.ez2 = static_cast<Real*>(t->ez2);
     a.evlog = nullptr;
     a.c = t->fc;
+    a.lo = t->dom_lo;
+    a.hi = t->dom_hi;
     return a;
 }
 
@@ -163,6 +173,10 @@ inline PushFixArgs push_fix_args(sclf_tube* t) {
     a.cfl = static_cast<float>(t->d.dt / t->d.dz);
     a.scale = std::ldexp(1.0f, -t->fb);
     a.two_fb = std::ldexp(1.0f, t->fb);
+    a.lo = t->dom_lo;
+    a.hi = t->dom_hi;
+    a.out_down = t->out_down;
+    a.out_up = t->out_up;
     return a;
 }
 
@@ -171,6 +185,16 @@ inline cudaError_t do_ez_table(sclf_tube* t) {
     return fp64(t) ? launch_ez_table<double>(t->ez, static_cast<double*>(t->ez2), nz, t->stream)
                    : launch_ez_table<float>(t->ez, static_cast<float*>(t->ez2), nz, t->stream);
 }
+
+// Shared with the decomposed-tube driver (defined in tube.cu).
+cudaError_t enqueue_push(sclf_tube* t, cudaStream_t s);
+cudaError_t enqueue_field(sclf_tube* t, int parity, cudaStream_t s);
+cudaError_t enqueue_compact(sclf_tube* t, cudaStream_t s, int force);
+double raw_cells(const sclf_tube* t, const void* raw, int64_t i);
+int append_raw(sclf_tube* t, int64_t n, const void* xi, const void* u, const int64_t* id);
+int native_particles(const sclf_tube* t, int64_t n, const double* z, const double* u,
+                     std::vector<char>& xs, std::vector<char>& us);
+int set_fields_host(sclf_tube* t, const double* ez, const double* er, const double* b);
 
 inline int read_state(sclf_tube* t, DevState* h) {
     CK(cudaMemcpyAsync(h, t->st, sizeof(DevState), cudaMemcpyDeviceToHost, t->stream));

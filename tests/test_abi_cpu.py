@@ -216,3 +216,23 @@ def test_velocity_selftest_validates_its_range_without_a_device(lib):
     assert lib.tube_selftest_velocity(0, 1, None, C.byref(first)) == -1
     assert lib.tube_selftest_velocity(5, 0, C.byref(n), C.byref(first)) == 0
     assert n.value == 0 and first.value == 0xffffffff
+
+
+def test_decomposed_tube_validates_before_touching_the_device(lib):
+    """dtube_create rejects bad sub-domain counts, cuts that do not cover
+    [0, Nz) in ranges of at least 2 cells, and the FP64-atomic current, with
+    SCLF_EINVAL before any CUDA call."""
+    import ctypes as C
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    p = B.default_params(**kw)
+    out = C.c_void_p()
+    for n in (0, 65):
+        assert lib.dtube_create(C.byref(p), n, None, C.byref(out)) == -1
+    for cuts in ([1, 512, 1024], [0, 512, 1000], [0, 1, 1024], [0, 600, 500, 1024],
+                 [0, 1023, 1024]):
+        c = np.array(cuts, dtype=np.int64)
+        assert lib.dtube_create(C.byref(p), len(cuts) - 1, c.ctypes.data_as(B._pi64),
+                                C.byref(out)) == -1, cuts
+    p64 = B.default_params(**dict(kw, accumulate=B.SCLF_ACC_FP64))
+    assert lib.dtube_create(C.byref(p64), 2, None, C.byref(out)) == -1
+    assert not out.value

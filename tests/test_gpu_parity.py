@@ -950,6 +950,82 @@ def test_sort_by_cell_changes_no_result(gpu_lib, prec):
     b.close()
 
 
+def _same_run(whole, dt, what):
+    """Fields bit for bit, particles bit for bit by ID, and the counters."""
+    sw, sd = whole.status(), dt.status()
+    for k in ("step", "n_particles", "total_injected", "last_injected", "pending_injection",
+              "flags"):
+        assert sw[k] == sd[k], (what, k, sw[k], sd[k])
+    fw = whole.read_fields(rho=False)
+    fd = dt.read_fields()
+    for k in ("ez", "er", "b", "j"):
+        assert np.array_equal(fw[k], fd[k]), (what, k)
+    zw, uw, iw = whole.read_particles()
+    o = np.argsort(iw, kind="stable")
+    zd, ud, idd = dt.read_particles()
+    assert np.array_equal(iw[o], idd), what
+    assert np.array_equal(zw[o], zd) and np.array_equal(uw[o], ud), what
+
+
+@pytest.mark.parametrize("prec,cuts", [(B.SCLF_FP64, [0, 100, 333, 1024]),
+                                       (B.SCLF_FP32, [0, 100, 333, 700, 1024]),
+                                       (B.SCLF_FIX32, [0, 2, 512, 1022, 1024])])
+def test_decomposed_flat_tube_equals_the_whole_tube(gpu_lib, prec, cuts):
+    """Config 1 (flat tube, empty start, injection) split into 3 or 4 z-ranges
+    (sub-domains with their own slots, streams and grid copies, exchanging
+    the boundary current, B_phi and E_z halos and the crossing particles each
+    step) gives the same fields bit for bit, the same particles by ID and the
+    same counters as the whole tube, checked every 150 steps up to 600 while
+    the electron front passes the cuts (FIX32 also with 2-cell sub-domains at
+    both ends)."""
+    kw = workloads.flat_sclf_small(precision=prec, accumulate=B.SCLF_ACC_FIXED64)
+    whole = B.Tube(B.default_params(**kw))
+    dt = B.DTube(B.default_params(**kw), cuts=cuts)
+    for n in range(4):
+        whole.run(150)
+        dt.run(150)
+        _same_run(whole, dt, "step %d" % (150 * (n + 1)))
+    ex = dt.exchange_stats()
+    ts = 8 if prec == B.SCLF_FP64 else 4
+    assert ex["steps"] == 600
+    assert ex["field_bytes"] == 600 * (len(cuts) - 2) * (16 + 16 + 2 * ts)
+    assert ex["particles"] > 0
+    assert ex["particle_bytes"] == ex["particles"] * (2 * ts + 8)
+    whole.close()
+    dt.close()
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FIX32, B.SCLF_FP32])
+def test_decomposed_frame_dragging_tube_equals_the_whole_tube(gpu_lib, prec):
+    """The 1e8-particle tube's grid (Nz = 65536) prefilled with 5e5 particles,
+    fields from Eq. 4 with their charge, split into 4 uneven sub-domains:
+    300 steps give the same fields, particles and counters as the whole tube
+    (at ~8 particles per cell moving 0.0093 cell per step, about one particle
+    crosses a cut every 14 steps: ~60 hand-overs in all)."""
+    n = 500000
+    kw = workloads.gr_tube(n_particles=n, precision=prec, accumulate=B.SCLF_ACC_FIXED64,
+                           track_ids=1)
+    whole = B.Tube(B.default_params(**kw))
+    d = whole.derived
+    gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
+    z, u = synth.prefilled_beam(n, d["L"] - d["dz"], gfar, seed=4,
+                                eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
+    whole.add_particles(z, u)
+    whole.solve_fields()
+    f0 = whole.read_fields(rho=False)
+    dt = B.DTube(B.default_params(**kw), cuts=[0, 9000, 30001, 47000, 65536])
+    dt.load_particles(z, u)
+    dt.set_fields(f0["ez"], f0["er"], f0["b"])
+    _same_run(whole, dt, "start")
+    for k in range(3):
+        whole.run(100)
+        dt.run(100)
+        _same_run(whole, dt, "step %d" % (100 * (k + 1)))
+    assert dt.exchange_stats()["particles"] > 30
+    whole.close()
+    dt.close()
+
+
 def test_diagnostics_match_the_oracle(gpu_lib):
     """tube_diagnostics (gamma max and mean, kinetic and field energy, Gauss
     residual) against the same quantities from the oracle's state after 150
