@@ -38,7 +38,8 @@ CSRC = os.path.join(ROOT, "paper_1011_6330_gb300", "csrc")
 KERNEL_SRC = {"gr1e8": ["push.cu", "device_common.cuh", "sclf_internal.h"],
               "gr1e8_fix32": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"],
               "large": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"],
-              "batch": ["push.cu", "device_common.cuh", "sclf_internal.h"]}
+              "batch": ["push.cu", "device_common.cuh", "sclf_internal.h"],
+              "batch_fix32": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
 
 
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "fix32"], default="fix32",
                     help="gr1e8: particle positions as 32-bit fixed point (SCLF_FIX32, "
                          "default) or as float32; momenta float32 either way")
+    ap.add_argument("--batch-precision", choices=["fix32", "f32"], default="fix32",
+                    help="batch workload: positions of the death-line tubes")
     ap.add_argument("--no-extras", action="store_true",
                     help="gr1e8: only the headline measurement (no precision comparison, "
                          "no other-precision or FP64-accumulator figures, no batched or "
@@ -336,7 +339,9 @@ def run_batch(args, sub=False):
     if ws > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    kws = workloads.death_line_batch(seed=rank_seed(rank))
+    bprec = B.SCLF_FP32 if getattr(args, "batch_precision", "fix32") == "f32" else B.SCLF_FIX32
+    fix = bprec == B.SCLF_FIX32
+    kws = workloads.death_line_batch(seed=rank_seed(rank), precision=bprec)
     params = [B.default_params(**kw) for kw in kws]
     batch = B.Batch(params)
     plain = [B.Tube(p) for p in params]
@@ -387,8 +392,9 @@ def run_batch(args, sub=False):
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as f:
-            ent = json.load(f).get("batch", {})
-        if ent.get("kernel_sha") == kernel_sha("batch") and ent.get("tubes") == len(kws) \
+            ent = json.load(f).get("batch_fix32" if fix else "batch", {})
+        if ent.get("kernel_sha") == kernel_sha("batch_fix32" if fix else "batch") \
+                and ent.get("tubes") == len(kws) \
                 and ws == 1:
             traffic = ent["bytes_per_launch"]
     # end to end through the C ABI: every tube's particles from pinned host
@@ -462,7 +468,7 @@ def run_batch(args, sub=False):
         z, u = states[0]
         d = plain[1].derived
         o = orc.Tube(kw["Nz"], d["L"], d["dt"], np.full(kw["Nz"] + 1, d["rho0"]), d["s"],
-                     precision="f32", accumulate="fixed")
+                     precision="fix32" if fix else "f32", accumulate="fixed")
         o.add_particles(z, u)
         o.solve_fields()
         o.step()
@@ -479,21 +485,28 @@ def run_batch(args, sub=False):
     line = {
         "metric": METRIC, "value": work / el_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "death_line_batch_256_tubes", "tubes": len(kws),
+        "scaling": "weak", "vs_baseline": None, "dtype": "fix32+f32" if fix else "f32",
+        "data": "synthetic",
+        "config": {"workload": "death_line_batch_256_tubes" + ("_fix32" if fix else "_fp32"),
+                   "tubes": len(kws),
                    "particles_total": int(n1), "cells_total": int(sum(kw["Nz"] for kw in kws)),
                    "l2": "inputs larger than L2 (%.0f MB of particle state)" % (8e-6 * n1),
-                   "kernel_shape": {"chosen": {"particles_per_thread": B.Batch.VARIANTS[chosen][0],
-                                               "ctas_per_sm": B.Batch.VARIANTS[chosen][1],
-                                               "runs_per_thread": B.Batch.VARIANTS[chosen][2]},
-                                    "autotune_push_ms": {"%dx%dx%d" % v: float(m) for v, m in
-                                                         zip(B.Batch.VARIANTS, tune_ms)}},
+                   "kernel_shape": ({"chosen": {"particles_per_thread": 8, "ctas_per_sm": 4,
+                                                "runs_per_thread": "run cell and the next"},
+                                     "autotune_push_ms": {"8x4 (FIX32)": float(tune_ms[0])}}
+                                    if fix else
+                                    {"chosen": {"particles_per_thread": B.Batch.VARIANTS[chosen][0],
+                                                "ctas_per_sm": B.Batch.VARIANTS[chosen][1],
+                                                "runs_per_thread": B.Batch.VARIANTS[chosen][2]},
+                                     "autotune_push_ms": {"%dx%dx%d" % v: float(m) for v, m in
+                                                          zip(B.Batch.VARIANTS, tune_ms)}}),
                    "parallelism": "independent batch per GPU" if ws > 1 else "one batch"},
         "plain_form": {"value": plain_value, "unit": UNIT, "steps": k_plain,
                        "how": "the same 256 tubes, each stepped alone (tube_run, graphs)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": ("batch_push_const_kernel" if len(kws) <= 400
+                     "kernel": ("batch_push_fix32_kernel" if fix else
+                                "batch_push_const_kernel" if len(kws) <= 400
                                 else "batch_push_kernel"),
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
@@ -814,6 +827,45 @@ def precision_vs_fp64(B, workloads, seed):
     return out
 
 
+def batch_precision_vs_fp64(B, workloads, seed, n_sample=8, steps=2000):
+    """E_z of sampled death-line tubes (spread over Nz and P) after `steps`
+    steps with FIX32 and float32 positions against FP64 positions, each tube
+    stepped alone from its seeded prefilled state (a batched tube computes
+    the same bits as that tube alone)."""
+    from paper_1011_6330_gb300 import synth
+    kws = workloads.death_line_batch(seed=seed, precision=B.SCLF_FP64)
+    order = sorted(range(len(kws)), key=lambda i: (kws[i]["Nz"], kws[i]["P_s"]))
+    pick = [order[k] for k in np.linspace(0, len(order) - 1, n_sample).astype(int)]
+    errs = {"fix32": [], "f32": []}
+    for i in pick:
+        kw = dict(kws[i], track_ids=0)
+        ez = {}
+        for name, prec in (("fp64", B.SCLF_FP64), ("fix32", B.SCLF_FIX32), ("f32", B.SCLF_FP32)):
+            t = B.Tube(B.default_params(**dict(kw, precision=prec)))
+            d = t.derived
+            gr = kw["rho_gj_mode"] == B.SCLF_RHO_GR
+            gfar = (d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"]) if gr
+                    else math.sqrt(2.0) * d["Lambda0"])
+            eta = (lambda zz, r=d["R_over_Rstar"]: 1.0 + zz * r) if gr else None
+            z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar,
+                                        seed=seed + i, eta_of_z=eta)
+            t.add_particles(z, u)
+            t.solve_fields()
+            t.run(steps)
+            ez[name] = t.read_fields(rho=False)["ez"]
+            t.close()
+        for name in errs:
+            errs[name].append(float(np.max(np.abs(ez[name] - ez["fp64"])) /
+                                    np.max(np.abs(ez["fp64"]))))
+    return {"reference": "the same tubes with FP64 positions and momenta on the GPU",
+            "tubes": [{"index": i, "Nz": kws[i]["Nz"], "P_s": kws[i]["P_s"],
+                       "B_G": kws[i]["B_G"]} for i in pick],
+            "steps": steps, "how": "max_j |E_z - E_z,fp64| / max |E_z,fp64| per tube",
+            "fix32_ez": errs["fix32"], "f32_ez": errs["f32"],
+            "fix32_ez_median": float(np.median(errs["fix32"])),
+            "f32_ez_median": float(np.median(errs["f32"]))}
+
+
 def secondary_tube(B, workloads, n, precision, acc, order, seed, steps, warmup):
     """Push time and roofline of the headline tube with another particle
     precision or current accumulator (same seeded state)."""
@@ -840,7 +892,8 @@ def form_summary(line, headline_value):
     """The batched or adjoint form's figures next to its plain form."""
     pf = line["plain_form"]
     roof = line.get("roofline") or {}
-    out = {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+    out = {"workload": line["config"]["workload"], "dtype": line["dtype"],
+           "value": line["value"], "unit": line["unit"],
            "steps": line["steps"], "plain_value": pf["value"],
            "vs_plain": line["value"] / pf["value"], "plain_how": pf["how"],
            "vs_headline": line["value"] / headline_value,
@@ -1043,6 +1096,8 @@ def main():
                                                   args.order, rank_seed(rank), 50, 5)
         line["batched"] = form_summary(run_batch(sub_args(args, steps=64, warmup=5), sub=True),
                                        value)
+        line["batched"]["precision_vs_fp64"] = batch_precision_vs_fp64(B, workloads,
+                                                                       rank_seed(rank))
         line["adjoint"] = form_summary(run_adjoint(sub_args(args, steps=2000, warmup=4),
                                                    sub=True), value)
     if rank == 0:

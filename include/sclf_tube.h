@@ -463,8 +463,9 @@ int dtube_exchange_stats(dtube_t dt, int64_t* steps, int64_t* field_bytes, int64
  * tiles and one field launch over all tubes' cells (plus the per-tube
  * compaction checks), so tubes of uneven Nz and particle count share the
  * GPU. Each tube computes exactly what it would compute alone (Sec. 2 step
- * for every tube). Batched tubes must use SCLF_FP32 particles and
- * SCLF_ACC_FIXED64. */
+ * for every tube). Batched tubes must use SCLF_ACC_FIXED64 and all the
+ * same particle format: SCLF_FP32, or SCLF_FIX32 (32-bit fixed-point
+ * positions; each tube's fractional bits follow from its own Nz). */
 typedef struct sclf_batch* batch_t;   /* opaque, library-owned */
 
 /* Create n tubes from params[0..n-1] (host array) on one stream; the
@@ -513,7 +514,7 @@ int batch_get_timing(batch_t b, tube_timing* out);
 #define SCLF_BATCH_VARIANTS 6
 
 /* Use shape `variant` from the next step on (SCLF_EINVAL outside
- * [0, SCLF_BATCH_VARIANTS)). */
+ * [0, SCLF_BATCH_VARIANTS); an SCLF_FIX32 batch has one shape, 0). */
 int batch_set_variant(batch_t b, int32_t variant);
 
 /* Autotuner: run 2 + steps ordinary steps of the batch with each shape,
@@ -521,7 +522,8 @@ int batch_set_variant(batch_t b, int32_t variant);
  * (host, SCLF_BATCH_VARIANTS doubles, may be NULL) receives each shape's
  * mean particle-kernel time per step, chosen (may be NULL) the shape kept.
  * The batch advances by SCLF_BATCH_VARIANTS * (steps + 2) steps; timing is
- * left off and its totals cleared. Synchronises. */
+ * left off and its totals cleared. An SCLF_FIX32 batch times its one shape
+ * (steps + 2 steps; ms[1..] = -1). Synchronises. */
 int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen);
 
 /* ---- discrete adjoint of a run: gradients ------------------------------------

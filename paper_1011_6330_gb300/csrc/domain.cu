@@ -321,13 +321,16 @@ int dtube_create(const tube_params* p, int32_t n, const int64_t* cuts, dtube_t* 
     D->part_bytes = 2 * rs + (ids ? 8 : 0);
     const int64_t box = (D->ob_cap * D->part_bytes + 255) / 256 * 256;
     const int64_t cnt_bytes = (int64_t(2 * n + 1) * 8 + 255) / 256 * 256;
-    const int64_t desc_bytes = int64_t(n) * sizeof(DomDev);
-    if (cudaMalloc(&D->mem, 2 * n * box + cnt_bytes + desc_bytes) != cudaSuccess) {
+    const int64_t desc_bytes = (int64_t(n) * sizeof(DomDev) + 255) / 256 * 256;
+    const int64_t pair_bytes = int64_t(n) * 2 * sizeof(Outbox);
+    if (cudaMalloc(&D->mem, 2 * n * box + cnt_bytes + desc_bytes + pair_bytes) != cudaSuccess) {
         D->mem = nullptr;
         return dt_fail(D, SCLF_ENOMEM);
     }
     D->counters = reinterpret_cast<unsigned long long*>(D->mem + 2 * n * box);
     D->dev = reinterpret_cast<DomDev*>(D->mem + 2 * n * box + cnt_bytes);
+    Outbox* pairs = reinterpret_cast<Outbox*>(D->mem + 2 * n * box + cnt_bytes + desc_bytes);
+    std::vector<Outbox> hpairs(2 * n);
     if (cudaMemset(D->counters, 0, cnt_bytes) != cudaSuccess) return dt_fail(D, SCLF_ECUDA);
     std::vector<DomDev> h(n);
     for (int k = 0; k < n; ++k) {
@@ -357,8 +360,13 @@ int dtube_create(const tube_params* p, int32_t n, const int64_t* cuts, dtube_t* 
         dd.hi = c[k + 1];
         dd.down = t->out_down;
         dd.up = t->out_up;
+        hpairs[2 * k] = t->out_down;
+        hpairs[2 * k + 1] = t->out_up;
+        t->out_dev = pairs + 2 * k;                  // the particle kernels read them there
     }
-    if (cudaMemcpy(D->dev, h.data(), desc_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(D->dev, h.data(), int64_t(n) * sizeof(DomDev), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(pairs, hpairs.data(), pair_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return dt_fail(D, SCLF_ECUDA);
     // per boundary and step: J of two cells, B_phi of two cells, two E_z table entries
     const int64_t ts = p->precision == SCLF_FP64 ? 8 : 4;

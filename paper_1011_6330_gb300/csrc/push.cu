@@ -66,14 +66,19 @@ struct TileCtx {
     Real nzf, dt, cfl;
     int nz;
     Real lof, hif;             // owned cells [lof, hif) (a sub-domain; 0, nzf: whole tube)
-    Outbox out_down, out_up;   // used only when a particle leaves [lof, hif) inside the tube
+    const Outbox* out;         // [down, up] (device), read only when a particle leaves [lof, hif)
 };
 
 // A particle that leaves the sub-domain for a neighbour's cells: appended to
 // that side's outbox (an overflow sets SCLF_FLAG_CAPACITY and loses it).
 template <class P, class M>
-__device__ __forceinline__ void emigrate(const Outbox& ob, P x, M u, long long id,
+__device__ __forceinline__ void emigrate(const Outbox* out, int side, P x, M u, long long id,
                                          unsigned int* flags) {
+    if (!out) {                                      // a whole tube has no neighbour
+        atomicOr(flags, SCLF_FLAG_CAPACITY);
+        return;
+    }
+    const Outbox& ob = out[side];
     const unsigned long long k = ob.n ? atomicAdd(ob.n, 1ULL) : ~0ULL;
     if (k < static_cast<unsigned long long>(ob.cap)) {
         static_cast<P*>(ob.x)[k] = x;
@@ -200,7 +205,7 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
                     us[k] = u1;
                     if (x1 < Real(1)) w0_acc += to_fixed(Real(1) - x1);
                 } else if (x1 >= Real(0) && x1 < nzf) {   // to a neighbouring sub-domain
-                    emigrate<Real, Real>(x1 < c.lof ? c.out_down : c.out_up, x1, u1,
+                    emigrate<Real, Real>(c.out, x1 < c.lof ? 0 : 1, x1, u1,
                                          c.ids ? c.ids[i0 + k] : -1LL, c.flags);
                     xs[k] = Real(-1);
                     us[k] = Real(0);
@@ -259,16 +264,6 @@ __device__ __forceinline__ long long clipped_injection(const DevState* st, long 
     room = room > 0 ? room : 0;
     return n_req < room ? n_req : room;
 }
-__device__ __forceinline__ void record_injection(DevState* st, long long n_inj, long long n_req,
-                                                 long long* evlog) {
-    st->inj_done = n_inj;
-    st->slots_processed += static_cast<unsigned long long>(st->n_slots + n_inj);
-    if (n_inj < n_req) atomicOr(&st->flags, SCLF_FLAG_CAPACITY);
-    if (evlog) {
-        evlog[kLogStride * st->step + kLogSlots] = st->n_slots;
-        evlog[kLogStride * st->step + kLogInjected] = n_inj;
-    }
-}
 
 // The particle kernel. kStages == 1: each tile's slots are loaded straight
 // into registers. kStages >= 2: the tiles a CTA will process next stream into
@@ -306,8 +301,7 @@ push_kernel(const PushArgs<Real> a) {
     c.nz = a.nz;
     c.lof = static_cast<Real>(a.lo);
     c.hif = static_cast<Real>(a.hi);
-    c.out_down = a.out_down;
-    c.out_up = a.out_up;
+    c.out = a.out;
     const long long ntiles = (c.n_tot + kTile - 1) / kTile;
 
     long long w0_acc = 0;
@@ -357,21 +351,6 @@ push_kernel(const PushArgs<Real> a) {
 // current) in one launch: persistent CTAs walk the batch's tile space, every
 // tile belongs to one tube and is pushed with that tube's constants.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void flush_tube_counters(DevState* st, long long& w0, long long& rm,
-                                                    bool& nf) {
-    const unsigned any = __ballot_sync(kFull, (w0 != 0) | (rm != 0) | nf);
-    if (any) {
-        const long long w = warp_sum(w0), r = warp_sum(rm);
-        if ((threadIdx.x & 31) == 0) {
-            if (w) atomicAdd(&st->acc_w0, static_cast<unsigned long long>(w));
-            if (r) atomicAdd(&st->acc_removed, static_cast<unsigned long long>(r));
-        }
-        if (nf) atomicOr(&st->flags, SCLF_FLAG_NONFINITE);
-    }
-    w0 = 0;
-    rm = 0;
-    nf = false;
-}
 
 template <int kPPT, int kMinBlocks, bool kTwoRuns>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
@@ -410,7 +389,7 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         c.nz = d.nz;
         c.lof = 0.0f;
         c.hif = d.nzf;
-        c.out_down = c.out_up = Outbox{};
+        c.out = nullptr;
         // the next tile's descriptor line into L1 while this tile computes
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
         push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
@@ -456,7 +435,7 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
         c.nz = kc.nz;
         c.lof = 0.0f;
         c.hif = kc.nzf;
-        c.out_down = c.out_up = Outbox{};
+        c.out = nullptr;
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
         push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
         flush_tube_counters(kc.st, w0, removed, nonfinite);

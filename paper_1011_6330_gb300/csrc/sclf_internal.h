@@ -116,9 +116,10 @@ struct PushArgs {
     Real dt;                   // (Real)dt
     Real cfl;                  // (Real)(dt/dz)
     // owned cells [lo, hi) of a sub-domain (0, nz for a whole tube): a particle
-    // that ends inside the tube but outside them goes to out_down / out_up
+    // that ends inside the tube but outside them goes to out[0] (below) or
+    // out[1] (above), a device array of two outboxes (null for a whole tube)
     int lo, hi;
-    Outbox out_down, out_up;
+    const Outbox* out;
 };
 
 template <class Real>
@@ -158,7 +159,7 @@ struct PushFixArgs {
     float scale;               // 2^-fb
     float two_fb;              // 2^fb
     int lo, hi;                // owned cells (see PushArgs)
-    Outbox out_down, out_up;
+    const Outbox* out;
 };
 
 template <class Pos, class Mom>
@@ -196,6 +197,7 @@ struct alignas(128) BatchTube {
     // the rest
     long long capacity;
     int cell0;                 // first cell of this tube in the batch's cell space
+    int fb;                    // SCLF_FIX32 batches: fractional bits of the positions (xi holds int32)
     double* ez;
     double* er[2];
     double* b[2];
@@ -310,6 +312,10 @@ int batch_push_grid_size(int variant, int device_sms);
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
                                int parity, cudaStream_t s);
 int push_fix32_grid_size(int stages, int device_sms);
+// The SCLF_FIX32 batch's particle kernel (one shape: 8 slots per thread).
+cudaError_t launch_batch_push_fix32(const BatchTube* tubes, const int* tile_tube,
+                                    long long n_tiles, int grid, cudaStream_t s);
+int batch_push_fix32_grid_size(int device_sms);
 template <class Pos, class Mom>
 cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s);
 template <class Pos, class Mom>

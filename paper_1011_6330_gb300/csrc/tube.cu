@@ -1118,6 +1118,8 @@ struct sclf_batch {
     std::vector<BatchConstTable> ctab;
     int const_grid[kBatchVariants] = {};
     int variant = 0;                   // particle kernel shape (batch_autotune)
+    bool fix32 = false;                // SCLF_FIX32 tubes: one particle-kernel shape
+    int fix_grid = 0;
     int64_t host_step = 0;
     int steps_since_compact = 0;
     int compact_every = 64;
@@ -1143,6 +1145,11 @@ int tile_class(int variant) {
 }
 
 cudaError_t batch_launch_push(sclf_batch* b, cudaStream_t s) {
+    if (b->fix32) {
+        const cudaError_t e = launch_batch_refresh(b->d_desc[0], static_cast<int>(b->tubes.size()), s);
+        if (e != cudaSuccess) return e;
+        return launch_batch_push_fix32(b->d_desc[0], b->d_tile_tube[0], b->n_tiles[0], b->fix_grid, s);
+    }
     const int c = tile_class(b->variant);
     const cudaError_t e = launch_batch_refresh(b->d_desc[c], static_cast<int>(b->tubes.size()), s);
     if (e != cudaSuccess) return e;
@@ -1257,11 +1264,14 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
     if (!out || n <= 0 || !params) return SCLF_EINVAL;
     *out = nullptr;
     for (int32_t i = 0; i < n; ++i)
-        if (params[i].precision != SCLF_FP32 || params[i].accumulate != SCLF_ACC_FIXED64)
+        if ((params[i].precision != SCLF_FP32 && params[i].precision != SCLF_FIX32) ||
+            params[i].precision != params[0].precision ||
+            params[i].accumulate != SCLF_ACC_FIXED64)
             return SCLF_EINVAL;
     sclf_batch* b = new (std::nothrow) sclf_batch();
     if (!b) return SCLF_ENOMEM;
     b->stream = static_cast<cudaStream_t>(stream);
+    b->fix32 = params[0].precision == SCLF_FIX32;
     auto fail = [&](int code) { batch_destroy(b); return code; };
     std::vector<BatchTube> desc(n);
     std::vector<int> tile_tube[kTileClasses], cell_tube;
@@ -1298,6 +1308,7 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         d.b[1] = t->b[1];
         d.jlast = t->jlast;
         d.fc = t->fc;
+        d.fb = t->fb;
         for (int c = 0; c < kTileClasses; ++c) {   // cap_pad is a multiple of every tile size
             const long long nt = t->lay.cap_pad / (kThreads * static_cast<long long>(kClassPPT[c]));
             tile0[c].push_back(tiles[c]);
@@ -1309,7 +1320,7 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         if (cells >= (1LL << 31)) return fail(SCLF_EINVAL);
     }
     b->n_cells = static_cast<int>(cells);
-    if (n <= kBatchConstTubes) {
+    if (n <= kBatchConstTubes && !b->fix32) {
         try {
             b->ctab.resize(kTileClasses);
         } catch (...) {
@@ -1352,6 +1363,8 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
         if (b->push_grid[v] > nt) b->push_grid[v] = static_cast<int>(nt);
         if (b->const_grid[v] > nt) b->const_grid[v] = static_cast<int>(nt);
     }
+    b->fix_grid = batch_push_fix32_grid_size(sms);
+    if (b->fix_grid > b->n_tiles[0]) b->fix_grid = static_cast<int>(b->n_tiles[0]);
     if (b->stream) {
         b->gstream = b->stream;
     } else {
@@ -1472,6 +1485,7 @@ int batch_set_timing(batch_t b, int enable) {
 
 int batch_set_variant(batch_t b, int32_t variant) {
     if (!b || variant < 0 || variant >= kBatchVariants) return SCLF_EINVAL;
+    if (b->fix32 && variant != 0) return SCLF_EINVAL;        // one shape
     if (variant != b->variant && b->chunk) {
         CK(cudaStreamSynchronize(b->stream));
         cudaGraphExecDestroy(b->chunk);          // captured with the previous shape
@@ -1486,7 +1500,9 @@ int batch_autotune(batch_t b, int32_t steps, double* ms, int32_t* chosen) {
     if (!b || steps <= 0) return SCLF_EINVAL;
     double best = 0.0;
     int best_v = -1;
-    for (int v = 0; v < kBatchVariants; ++v) {
+    if (ms && b->fix32)
+        for (int v = 1; v < kBatchVariants; ++v) ms[v] = -1.0;   // shapes not built for FIX32
+    for (int v = 0; v < (b->fix32 ? 1 : kBatchVariants); ++v) {
         int rc = batch_set_variant(b, v);
         if (rc) return rc;
         for (int k = 0; k < 2; ++k)              // first launches of this kernel

@@ -87,6 +87,7 @@ struct sclf_tube {
     // outboxes of particles leaving them (a whole tube: 0, Nz, none)
     int dom_lo = 0, dom_hi = 0;
     sclf::Outbox out_down{}, out_up{};
+    const sclf::Outbox* out_dev = nullptr;   // the two above, in device memory
 };
 
 namespace sclf {
@@ -130,8 +131,7 @@ inline PushArgs<Real> push_args(sclf_tube* t) {
     a.cfl = static_cast<Real>(t->d.dt / t->d.dz);
     a.lo = t->dom_lo;
     a.hi = t->dom_hi;
-    a.out_down = t->out_down;
-    a.out_up = t->out_up;
+    a.out = t->out_dev;
     return a;
 }
 
@@ -175,8 +175,7 @@ inline PushFixArgs push_fix_args(sclf_tube* t) {
     a.two_fb = std::ldexp(1.0f, t->fb);
     a.lo = t->dom_lo;
     a.hi = t->dom_hi;
-    a.out_down = t->out_down;
-    a.out_up = t->out_up;
+    a.out = t->out_dev;
     return a;
 }
 

@@ -502,7 +502,7 @@ def test_large_tube_full_size_step_against_streamed_oracle(gpu_lib):
 # Batches of independent tubes
 # ---------------------------------------------------------------------------
 
-def _small_batch_params():
+def _small_batch_params(precision=B.SCLF_FP32):
     """Five uneven tubes: flat and frame-dragging, Nz from 64 to 4096."""
     specs = [(1e12, 0.5, 0.5, 64, 3000), (3e11, 1.3, 0.0, 200, 9000),
              (2e12, 0.2, 0.5, 1024, 20000), (5e12, 2.0, 0.0, 333, 1000),
@@ -510,7 +510,7 @@ def _small_batch_params():
     out = []
     for i, (Bg, P, incl, nz, n) in enumerate(specs):
         kw = workloads.gr_tube(B_G=Bg, P_s=P, incl=incl, Nz=nz, n_particles=n,
-                               capacity=n + 4096, track_ids=1)
+                               capacity=n + 4096, track_ids=1, precision=precision)
         kw["rho_gj_mode"] = B.SCLF_RHO_GR if incl > 0 else B.SCLF_RHO_FLAT
         kw["compact_interval"] = 7
         out.append(kw)
@@ -525,8 +525,13 @@ def _fill(t, kw, seed):
     t.solve_fields()
 
 
-def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
-    kws = _small_batch_params()
+@pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
+def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib, prec):
+    """A batch of five uneven tubes equals the same tubes stepped alone bit
+    for bit, and two of them match the same-precision oracle step by step;
+    with FIX32 positions (fractional bits 19 to 25 from the tubes' Nz) the
+    batch has one kernel shape."""
+    kws = _small_batch_params(prec)
     batch = B.Batch([B.default_params(**kw) for kw in kws])
     alone = [B.Tube(B.default_params(**kw)) for kw in kws]
     for i, kw in enumerate(kws):
@@ -535,11 +540,19 @@ def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
     with pytest.raises(B.SclfError) as e:
         batch.tubes[0].step()
     assert e.value.code == -7                   # a batch member is stepped by its batch
+    if prec == B.SCLF_FIX32:
+        with pytest.raises(B.SclfError):
+            batch.set_variant(1)
+        chosen, ms = batch.autotune(2)
+        assert chosen == 0 and ms[0] > 0 and all(m == -1.0 for m in ms[1:])
+    else:
+        batch.autotune(2)
+    n_tune = 4 if prec == B.SCLF_FIX32 else 4 * 6
     batch.run(40)
     batch.step()
     batch.run(25)
     for t in alone:
-        t.run(66)
+        t.run(66 + n_tune)
     gathered = batch.status()                   # one gather for the whole batch
     assert len(gathered) == len(kws)
     for i in range(len(kws)):
@@ -565,8 +578,8 @@ def test_batched_tubes_equal_tubes_stepped_alone_and_the_oracle(gpu_lib):
         rho = orc.rho_gj_profile(mode, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
                                  cu["R_over_Rstar"], cu["kappa"])
         d = t.derived
-        o = orc.Tube(kw["Nz"], kw["L_over_R"], d["dt"], rho, d["s"], precision="f32",
-                     accumulate="fixed")
+        o = orc.Tube(kw["Nz"], kw["L_over_R"], d["dt"], rho, d["s"],
+                     precision="fix32" if prec == B.SCLF_FIX32 else "f32", accumulate="fixed")
         z, u = synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], 3.0 * d["Lambda0"],
                                     seed=seed)
         t.add_particles(z, u)
@@ -747,13 +760,15 @@ def _same_state(sa, sb):
             assert np.array_equal(a[5][k], b[5][k]), k
 
 
-def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib):
+@pytest.mark.parametrize("prec", [B.SCLF_FIX32, B.SCLF_FP32])
+def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib, prec):
     """The 256-tube death-line batch at its benchmark size and launch
     configuration (seeded states, autotuned particle-kernel shape; the
     tuning steps are ordinary steps): after the tuning steps and one more,
     five sampled tubes (flat and frame-dragging, the smallest and largest
-    grids) against the oracle run from the same seeded states."""
-    kws = workloads.death_line_batch()
+    grids) against the oracle run from the same seeded states, with FIX32
+    (the benchmark's) and float32 positions."""
+    kws = workloads.death_line_batch(precision=prec)
     batch = B.Batch([B.default_params(**kw) for kw in kws])
     nzs = [kw["Nz"] for kw in kws]
     sample = sorted({0, 1, int(np.argmin(nzs)), int(np.argmax(nzs)), len(kws) - 1})
@@ -774,7 +789,8 @@ def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib):
     chosen, ms = batch.autotune(1)
     batch.step()
     nsteps = batch.tubes[0].status()["step"]
-    assert nsteps == len(B.Batch.VARIANTS) * 3 + 1
+    shapes = 1 if prec == B.SCLF_FIX32 else len(B.Batch.VARIANTS)
+    assert nsteps == shapes * 3 + 1
     for i in sample:
         kw, t = kws[i], batch.tubes[i]
         d = t.derived
@@ -782,12 +798,14 @@ def test_full_size_batch_against_oracle_on_sampled_tubes(gpu_lib):
         mode = orc.RHO_GR if kw["rho_gj_mode"] == B.SCLF_RHO_GR else orc.RHO_FLAT
         rho = orc.rho_gj_profile(mode, np.arange(kw["Nz"] + 1) * d["dz"], cu["Lambda0"],
                                  kw["incl_rad"], cu["theta_star"], cu["R_over_Rstar"], cu["kappa"])
-        o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="f32", accumulate="fixed")
+        fix = prec == B.SCLF_FIX32
+        o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="fix32" if fix else "f32",
+                     accumulate="fixed")
         o.add_particles(*states[i])
         o.solve_fields()
         o.run(nsteps)
-        _state_against_oracle(t, o, 1.0, "tube %d (Nz %d, shape %s)"
-                              % (i, kw["Nz"], B.Batch.VARIANTS[chosen]))
+        _state_against_oracle(t, o, 2.0 ** orc.fix32_bits(kw["Nz"]) if fix else 1.0,
+                              "tube %d (Nz %d, shape %s)" % (i, kw["Nz"], B.Batch.VARIANTS[chosen]))
     assert max(t.check() for t in batch.tubes) == 0
     batch.close()
 
