@@ -641,6 +641,24 @@ def run_adjoint(args, sub=False):
     s1 = t.status()["n_particles"]
     plain_value = 0.5 * (s0 + s1) * ADJ_STEPS / (1e-3 * p0.elapsed_time(p1))
     t.close()
+    # the same gradient with the segment length left to the library: the whole
+    # run is one segment when its snapshots fit, so the backward pass
+    # replays nothing (one warm-up evaluation, then one timed without event nodes)
+    a.close()
+    a1 = B.Adjoint(B.default_params(**kw), ADJ_STEPS, 0)
+    a1.tube.add_particles(z, u)
+    a1.forward()
+    a1.backward(B.SCLF_OBJ_GAMMA)
+    a1.forward()
+    f1_ms = a1.timing()["forward_ms"]
+    g1 = a1.param_gradient(*a1.backward(B.SCLF_OBJ_GAMMA))
+    b1_ms = a1.timing()["backward_ms"]
+    p1 = a1.timing()["particle_steps"]
+    one_segment = {"checkpoint_every": a1.checkpoint_every, "forward_ms": f1_ms,
+                   "backward_ms": b1_ms, "value": p1 / (1e-3 * (f1_ms + b1_ms)),
+                   "grad_gamma_rel_diff": [float(abs(x - y) / abs(y))
+                                           for x, y in zip(g1, grad_gamma)]}
+    a1.close()
     # FP32 against FP64: the same run with FP64 particles
     a64 = B.Adjoint(B.default_params(**dict(kw, precision=B.SCLF_FP64)), ADJ_STEPS, ADJ_EVERY)
     a64.tube.add_particles(z, u)
@@ -757,6 +775,10 @@ def run_adjoint(args, sub=False):
                        "how": "the same tube and particles stepped by tube_run (graphs), "
                               "CUDA events around the run",
                        "adjoint_over_plain": (work / el_s) / plain_value},
+        "one_segment": dict(one_segment, adjoint_over_plain=one_segment["value"] / plain_value,
+                            how="checkpoint_every = 0: the library keeps the whole run as "
+                                "one segment (its snapshots fit), no recompute; untimed "
+                                "graphs"),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         # per evaluation: the graph kernels (forward, recompute without the
         # last segment, reverse), the gather table, objectives (2) and seed
@@ -766,7 +788,6 @@ def run_adjoint(args, sub=False):
     }
     if rank == 0 and not sub:
         print(json.dumps(line))
-    a.close()
     if sub:
         return line
     if ws > 1:
@@ -903,6 +924,8 @@ def form_summary(line, headline_value):
     if "adjoint" in line:
         a = line["adjoint"]
         out["forward_ms"], out["backward_ms"] = a["forward_ms"], a["backward_ms"]
+        out["checkpoint_every"] = ADJ_EVERY
+        out["one_segment"] = line["one_segment"]
         out["fp32_vs_fp64_grad_rel_err"] = a["fp32_vs_fp64_grad_rel_err"]
     return out
 

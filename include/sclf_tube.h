@@ -561,9 +561,13 @@ typedef struct sclf_adjoint* adjoint_t;   /* opaque, library-owned */
                               one cell's sensitivity); its value is the dot
                               product of w with tube_read_fields' E_z     */
 
-/* Create a driver for runs of nsteps steps (> 0, a multiple of
+/* Create a driver for runs of nsteps steps (> 0, even, a multiple of
  * checkpoint_every, which is even and > 0) of a tube with parameters p
- * (track_ids is ignored). Device memory: about checkpoint_every +
+ * (track_ids is ignored). checkpoint_every = 0 lets the library choose the
+ * longest segment whose arrays fit in 80 % of the free device memory: a
+ * single segment (K = nsteps), whose backward pass needs no recompute, when
+ * the whole run's snapshots fit (adjoint_checkpoint_every reports the
+ * choice; ENOMEM when not even K = 2 fits). Device memory: about checkpoint_every +
  * nsteps / checkpoint_every + 5 copies of the particle arrays
  * (2 * capacity * 4 or 8 bytes each) and checkpoint_every grid copies.
  * SCLF_EINVAL for SCLF_ACC_FP64 (a recompute must reproduce the run bit for
@@ -572,6 +576,10 @@ typedef struct sclf_adjoint* adjoint_t;   /* opaque, library-owned */
  * own when NULL). Synchronises. */
 int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_every,
                    void* stream, adjoint_t* out);
+
+/* The segment length K the driver uses (the caller's checkpoint_every, or
+ * the library's choice for checkpoint_every = 0). */
+int adjoint_checkpoint_every(adjoint_t a, int32_t* k);
 
 /* Destroy the driver and its tube. */
 int adjoint_destroy(adjoint_t a);

@@ -132,6 +132,7 @@ SIGNATURES = {
     "batch_autotune": (_i32, [_vp, C.c_int32, _pd, C.POINTER(C.c_int32)]),
     "adjoint_create": (_i32, [C.POINTER(TubeParams), _i64, C.c_int32, _vp, C.POINTER(_vp)]),
     "adjoint_destroy": (_i32, [_vp]),
+    "adjoint_checkpoint_every": (_i32, [_vp, C.POINTER(C.c_int32)]),
     "adjoint_tube": (_i32, [_vp, C.POINTER(_vp)]),
     "adjoint_set_injections": (_i32, [_vp, _pi64]),
     "adjoint_forward": (_i32, [_vp, _pd]),
@@ -599,6 +600,9 @@ class Adjoint:
                                        C.c_void_p(stream.cuda_stream), C.byref(h)),
                "adjoint_create")
         self.h = h
+        k = C.c_int32()
+        _check(self.lib.adjoint_checkpoint_every(self.h, C.byref(k)), "adjoint_checkpoint_every")
+        self.checkpoint_every = k.value           # the library's choice for checkpoint_every=0
         th = C.c_void_p()
         _check(self.lib.adjoint_tube(self.h, C.byref(th)), "adjoint_tube")
         self.tube = _TubeView(self.lib, th, params)

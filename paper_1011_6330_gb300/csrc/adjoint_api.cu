@@ -467,6 +467,20 @@ int run_backward(sclf_adjoint* A, int objective, double* d_rho, double* d_s) {
     return SCLF_OK;
 }
 
+// Device bytes of a driver with segments of K steps (the allocation of
+// adjoint_create, array by array).
+int64_t adjoint_bytes(int64_t K, int64_t nsteps, int64_t nz, int64_t cap_pad, int64_t rs) {
+    const int64_t bytes = cap_pad * rs, nseg = nsteps / K;
+    return align256(2 * (K + 1) * bytes) + 2 * align256((nseg + 1) * bytes) +
+           align256((nseg + 1) * (3 * nz + 1) * 8) +
+           align256((nseg + 1) * static_cast<int64_t>(sizeof(DevState))) +
+           align256((K + 1) * align256(2 * (nz + 1) * rs)) + align256(K * nz * 8) +
+           2 * align256(kLogStride * nsteps * 8) + align256(kLogStride * K * 8) +
+           2 * align256(bytes) + align256(nz * 8) + align256(2 * (nz + 1) * 8) +
+           align256(2 * nz * 8) + align256(nz * 8) + align256(nz * rs) +
+           align256(2 * kObjBlocks * 8) + align256(2 * 8) + align256(nz * 8);
+}
+
 void free_adjoint(sclf_adjoint* A) {
     if (!A) return;
     if (A->t) cudaStreamSynchronize(A->t->gstream);
@@ -496,8 +510,8 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
     if (p->precision != SCLF_FP32 && p->precision != SCLF_FP64 && p->precision != SCLF_FIX32)
         return SCLF_EINVAL;
     if (p->accumulate != SCLF_ACC_FIXED64) return SCLF_EINVAL;
-    if (checkpoint_every <= 0 || (checkpoint_every & 1) || nsteps <= 0 ||
-        nsteps % checkpoint_every != 0)
+    if (checkpoint_every < 0 || (checkpoint_every & 1) || nsteps <= 0 || (nsteps & 1) ||
+        (checkpoint_every > 0 && nsteps % checkpoint_every != 0))
         return SCLF_EINVAL;
     tube_params q = *p;
     q.track_ids = 0;
@@ -508,13 +522,27 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
     sclf_tube* t = A->t;
     t->owned = true;
     A->nsteps = nsteps;
-    A->K = checkpoint_every;
-    A->nseg = nsteps / checkpoint_every;
     A->rs = p->precision == SCLF_FP64 ? 8 : 4;
     A->cap_pad = t->lay.cap_pad;
     A->nz = static_cast<int>(p->Nz);
+    if (checkpoint_every == 0) {
+        // the longest segment whose arrays fit in 80 % of the free device
+        // memory: one segment (no recompute) when the whole run's snapshots fit
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { free_adjoint(A); return SCLF_ECUDA; }
+        const double budget = 0.8 * static_cast<double>(free_b);
+        int64_t best = 0;
+        for (int64_t k = 2; k <= nsteps; k += 2)
+            if (nsteps % k == 0 &&
+                static_cast<double>(adjoint_bytes(k, nsteps, A->nz, A->cap_pad, A->rs)) <= budget)
+                best = k;
+        if (best == 0 || best > INT32_MAX) { free_adjoint(A); return SCLF_ENOMEM; }
+        checkpoint_every = static_cast<int32_t>(best);
+    }
+    A->K = checkpoint_every;
+    A->nseg = nsteps / checkpoint_every;
     const int64_t nz = A->nz, K = A->K, bytes = A->cap_pad * A->rs;
-    // one allocation, every array 256-byte aligned
+    // one allocation, every array 256-byte aligned (adjoint_bytes adds up the same)
     int64_t o = 0;
     auto take = [&](int64_t b) { const int64_t r = o; o += align256(b); return r; };
     const int64_t o_snap = take(2 * (K + 1) * bytes);
@@ -586,6 +614,12 @@ int adjoint_create(const tube_params* p, int64_t nsteps, int32_t checkpoint_ever
 int adjoint_destroy(adjoint_t a) {
     if (!a) return SCLF_EINVAL;
     free_adjoint(a);
+    return SCLF_OK;
+}
+
+int adjoint_checkpoint_every(adjoint_t a, int32_t* k) {
+    if (!a || !k) return SCLF_EINVAL;
+    *k = static_cast<int32_t>(a->K);
     return SCLF_OK;
 }
 

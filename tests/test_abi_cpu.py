@@ -111,14 +111,16 @@ def test_workspace_grows_with_capacity_and_grid(lib):
 
 def test_adjoint_create_validates_before_touching_the_device():
     """adjoint_create rejects FP64 atomics (the recompute must reproduce the
-    run bit for bit) and bad checkpoint intervals with SCLF_EINVAL before
-    any CUDA call."""
+    run bit for bit), bad checkpoint intervals and odd run lengths with
+    SCLF_EINVAL before any CUDA call (checkpoint_every = 0 asks the library
+    to choose)."""
     import ctypes as C
     lib = B.load()
     h = C.c_void_p()
     for kw, n, k in ((dict(precision=B.SCLF_FP64, accumulate=B.SCLF_ACC_FP64), 100, 10),
                      (dict(accumulate=B.SCLF_ACC_FP64), 100, 10),
-                     (dict(), 100, 7), (dict(), 100, 0), (dict(), 105, 10), (dict(), 0, 10)):
+                     (dict(), 100, 7), (dict(), 100, -2), (dict(), 105, 10), (dict(), 0, 10),
+                     (dict(), 101, 0)):
         p = B.default_params(**kw)
         assert lib.adjoint_create(C.byref(p), n, k, None, C.byref(h)) == -1
     assert lib.adjoint_backward(None, 0, None, None) == -1

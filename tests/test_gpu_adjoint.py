@@ -268,3 +268,23 @@ def test_weighted_ez_profile_gradient_matches_oracle(gpu_lib, prec):
     assert abs(float(np.dot(w, ez)) - v) <= (1e-12 if prec == B.SCLF_FP64 else 1e-6) * scale
     assert rel(g_rho, d_rho) <= TOL[prec] and abs(g_s - d_s) <= TOL[prec] * abs(d_s)
     a.close()
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
+def test_one_segment_chosen_by_the_library_gives_the_same_gradient(gpu_lib, prec):
+    """checkpoint_every = 0: the library keeps the whole run as one segment
+    when its snapshots fit (here they do), so the backward pass replays
+    nothing; the values equal those of the run checkpointed every 10 steps
+    bit for bit (the recompute reproduces the trajectory exactly) and the
+    (rho_GJ, s) gradients to the order of the FP64 atomic grid sums."""
+    kw, z, u, nsteps, K = flat_problem(prec)
+    a10, v10 = gpu_run(kw, z, u, nsteps, K)
+    a1, v1 = gpu_run(kw, z, u, nsteps, 0)
+    assert a10.checkpoint_every == K and a1.checkpoint_every == nsteps
+    assert np.array_equal(v10, v1)
+    for obj in (B.SCLF_OBJ_GAMMA, B.SCLF_OBJ_EZ):
+        g10, s10 = a10.backward(obj)
+        g1, s1 = a1.backward(obj)
+        assert rel(g1, g10) < 1e-12 and abs(s1 - s10) <= 1e-12 * abs(s10), obj
+    a10.close()
+    a1.close()
