@@ -244,7 +244,18 @@ def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=
     z, u = synth.prefilled_beam(n, d["L"] - d["dz"], gfar, seed=seed, order=order,
                                 eta_of_z=eta)
     t.add_particles(z, u)
+    _STATE["last"] = (n, z, u)
     return t, kw, d, z[::stride], u[::stride], stride
+
+
+_STATE = {}
+
+
+def _sample(n, stride):
+    """Every stride-th particle of the last n-particle state build_tube made."""
+    m, z, u = _STATE.pop("last")
+    assert m == n
+    return z[::stride].copy(), u[::stride].copy()
 
 
 def cpu_baseline(zs, us, n_total, kw, d, seconds, stride):
@@ -275,6 +286,129 @@ def cpu_baseline(zs, us, n_total, kw, d, seconds, stride):
             "sample": "%d of the %d particles (every %dth, macro charge x%d), Nz=%d, "
                       "%s particles + fixed-point current, %d steps in %.1f s"
                       % (zs.size, n_total, stride, stride, nz, prec, steps, el)}
+
+
+def _allcore_worker(w, nw, names, shapes, z, u, nz, L, dt, rho0, s, prec, barrier):
+    """One process of the all-core baseline: the oracle's gather, push and
+    deposit on its share of the particles, every step, between barriers."""
+    from multiprocessing import shared_memory
+    import oracle as orc
+    shm = [shared_memory.SharedMemory(name=n) for n in names]
+    ez = np.ndarray(shapes[0], np.float64, buffer=shm[0].buf)
+    acc_all = np.ndarray(shapes[1], np.int64, buffer=shm[1].buf)
+    res = np.ndarray(shapes[2], np.int64, buffer=shm[2].buf)
+    ctl = np.ndarray(shapes[3], np.int64, buffer=shm[3].buf)
+    o = orc.Tube(nz, L, dt, np.full(nz + 1, rho0), s, precision=prec, accumulate="fixed")
+    o.add_particles(z, u)
+    xi, uu = o.xi, o.u
+    fix = o.fix
+    top = (nz << o.fb) if fix else nz
+    while True:
+        barrier.wait()                                   # fields and n_inj are ready
+        if ctl[1]:
+            break
+        if w == 0 and ctl[0] > 0:                        # (a1) injection at the base
+            xi = np.concatenate([xi, np.zeros(int(ctl[0]), xi.dtype)])
+            uu = np.concatenate([uu, np.zeros(int(ctl[0]), uu.dtype)])
+        if fix:
+            ep = orc.gather_fix32(ez, xi, o.fb)
+            xi1, u1, finite = orc.push_fix32(xi, uu, ep, dt, o.dz, o.fb)
+            acc = orc.deposit_fix32(nz, xi[finite], xi1[finite], o.fb)
+        else:
+            ep = orc.gather(ez, xi, o.rt)
+            xi1, u1 = orc.push(xi, uu, ep, dt, o.dz, o.rt)
+            acc = orc.deposit_fractions(nz, xi, xi1, o.rt, "fixed")
+            finite = np.isfinite(xi1) & np.isfinite(u1)
+        alive = finite & (xi1 >= 0) & (xi1 < top)
+        xi, uu = xi1[alive], u1[alive]
+        acc_all[w] = acc
+        w0 = orc.base_weight_fix32(xi, o.fb) if fix else orc.base_weight_fixed(xi, o.rt)
+        res[w] = (xi.size, w0, 0)
+        barrier.wait()                                   # this step's share is written
+    for m in shm:
+        m.close()
+
+
+def cpu_baseline_allcore(zs, us, n_total, kw, d, seconds, stride, workers=None, nsteps=None):
+    """The oracle's step on all host cores: the particle sample split over
+    `workers` spawned processes (gather, push, deposit and removal of their
+    share with the oracle's functions), the integer current sums added in a
+    fixed order and the field leap-frog and injection count done by this
+    process (the oracle's field_update and injection_count), in shared
+    memory. Computes the same fields as the one-process oracle. Runs for
+    ~seconds, or exactly nsteps timed steps when given."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import oracle as orc
+    workers = workers or os.cpu_count() or 1
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    nz, L, dt = kw["Nz"], d["L"], d["dt"]
+    zn = np.arange(nz + 1) * (L / nz)
+    rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"])
+    prec = "fix32" if kw["precision"] == 2 else "f32"
+    s = d["s"] * stride
+    o = orc.Tube(nz, L, dt, rho, s, precision=prec, accumulate="fixed")
+    o.add_particles(zs, us)
+    o.solve_fields()
+    ez, er, b = o.ez, o.er, o.b
+    w0 = o.w0
+    shapes = [(nz,), (workers, nz), (workers, 3), (2,)]
+    shm = [shared_memory.SharedMemory(create=True, size=int(np.prod(sh)) * 8) for sh in shapes]
+    ez_s = np.ndarray(shapes[0], np.float64, buffer=shm[0].buf)
+    acc_all = np.ndarray(shapes[1], np.int64, buffer=shm[1].buf)
+    res = np.ndarray(shapes[2], np.int64, buffer=shm[2].buf)
+    ctl = np.ndarray(shapes[3], np.int64, buffer=shm[3].buf)
+    ctl[:] = 0
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers + 1)
+    parts = np.array_split(np.arange(zs.size), workers)
+    procs = [ctx.Process(target=_allcore_worker,
+                         args=(w, workers, [m.name for m in shm], shapes, zs[parts[w]],
+                               us[parts[w]], nz, L, dt, rho[0], s, prec, barrier))
+             for w in range(workers)]
+    for p in procs:
+        p.start()
+    try:
+        def step():
+            nonlocal ez, er, b, w0
+            n_inj, _ = orc.injection_count(ez[0], w0, s, o.dz, rho[0])
+            ctl[0] = n_inj
+            ez_s[:] = ez
+            barrier.wait()
+            barrier.wait()
+            acc = acc_all[0].copy()
+            for w in range(1, workers):                  # fixed order (exact integers)
+                acc += acc_all[w]
+            w0 = int(res[:, 1].sum())
+            live = int(res[:, 0].sum())
+            j = orc.current_from(acc, s, dt, "fixed")
+            ez, er, b = orc.field_update(ez, er, b, j, dt, o.dz)
+            return live, n_inj
+        n_prev, _ = step()                               # warm-up
+        t0 = time.perf_counter()
+        steps = psteps = 0
+        while (time.perf_counter() - t0 < seconds) if nsteps is None else steps < nsteps:
+            live, inj = step()
+            psteps += n_prev + inj
+            n_prev = live
+            steps += 1
+        el = time.perf_counter() - t0
+        ctl[1] = 1
+        barrier.wait()
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+        for m in shm:
+            m.close()
+            m.unlink()
+    return {"value": psteps / el, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": "%d of the %d particles (every %dth, macro charge x%d), Nz=%d, %s particles + "
+                      "fixed-point current, %d steps in %.1f s; the oracle's particle step on "
+                      "%d processes, integer current sums added in a fixed order, fields and "
+                      "injection in the main process"
+                      % (zs.size, n_total, stride, stride, nz, prec, steps, el, workers),
+            "final_ez": ez}
 
 
 def run_reference(args):
@@ -892,6 +1026,7 @@ def secondary_tube(B, workloads, n, precision, acc, order, seed, steps, warmup):
     precision or current accumulator (same seeded state)."""
     t, kw, d, _, _, _ = build_tube(B, workloads, "gr1e8", n, acc, order, seed,
                                    precision=precision)
+    _STATE.pop("last", None)
     t.solve_fields()
     t.run(warmup)
     t.set_timing(True)
@@ -1066,9 +1201,14 @@ def main():
                "rc": int(rc)}
 
     cpu = None
+    cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(zs, us, n, kw, d, args.cpu_seconds, stride)
         cpu["host"] = host_info()
+        if not large:
+            cpu_all = cpu_baseline_allcore(*_sample(n, 10), n, kw, d, args.cpu_seconds, 10)
+            cpu_all.pop("final_ez")
+            cpu_all["host"] = cpu["host"]
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -1101,6 +1241,7 @@ def main():
                      "compaction_checks": tm["n_compactions"],
                      "bytes_per_launch": BYTES_PER_PARTICLE * slots_per_launch},
         "cpu_baseline": cpu,
+        "cpu_baseline_allcore": cpu_all,
         "e2e": e2e,
         "gpu_launches": int(gpu_launches),
         "clocks": clk,

@@ -30,3 +30,33 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["host"]["nproc"] >= 1 and d["dtype"] == "fix32+f32"
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_all_core_baseline_computes_the_one_process_oracle_fields():
+    """The all-core CPU baseline (the oracle's particle step split over
+    spawned processes, integer current sums added in a fixed order) gives the
+    one-process oracle's E_z bit for bit after the same steps."""
+    sys.path.insert(0, ROOT)
+    import math
+    import numpy as np
+    import bench
+    import oracle as orc
+    from paper_1011_6330_gb300 import binding as B
+    from paper_1011_6330_gb300 import synth, workloads
+    n, nsteps = 20000, 12
+    kw = workloads.gr_tube(n_particles=n, Nz=512, precision=B.SCLF_FIX32)
+    d = B.derive(B.default_params(**kw))
+    gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
+    z, u = synth.prefilled_beam(n, d["L"] - d["dz"], gfar, seed=3,
+                                eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
+    res = bench.cpu_baseline_allcore(z, u, n, kw, d, 0.0, 1, workers=3, nsteps=nsteps)
+    assert res["cores"] == 3 and res["value"] > 0
+    cu = orc.code_units(kw["B_G"], kw["P_s"], kw["Rstar_cm"], kw["incl_rad"], kw["mass_g"])
+    zn = np.arange(kw["Nz"] + 1) * (d["L"] / kw["Nz"])
+    rho = orc.rho_gj_profile(orc.RHO_GR, zn, cu["Lambda0"], kw["incl_rad"], cu["theta_star"],
+                             cu["R_over_Rstar"], cu["kappa"])
+    o = orc.Tube(kw["Nz"], d["L"], d["dt"], rho, d["s"], precision="fix32", accumulate="fixed")
+    o.add_particles(z, u)
+    o.solve_fields()
+    o.run(nsteps + 1)                                  # the baseline's warm-up step too
+    assert np.array_equal(res["final_ez"], o.ez)
