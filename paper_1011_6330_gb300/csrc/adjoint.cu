@@ -341,7 +341,8 @@ __global__ void seed_ez_kernel(const double* ez, int nz, double dz, const double
 
 template <class Real>
 cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s) {
-    adj_field_kernel<Real><<<(a.nz + 255) / 256, 256, 0, s>>>(a);
+    constexpr int kBlock = 128;                // as the forward field kernel
+    adj_field_kernel<Real><<<(a.nz + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
