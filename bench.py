@@ -542,14 +542,15 @@ def run_batch(args, sub=False):
         counts = [x.size for x, _ in saved]
         offs = np.concatenate([[0], np.cumsum(counts)])
         caps = [int(t.params.capacity) for t in batch.tubes]
-        pin_x = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+        xdt = torch.int32 if fix else torch.float32      # raw positions: X (FIX32) or xi
+        pin_x = torch.empty(int(offs[-1]), dtype=xdt, pin_memory=True)
         pin_u = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
         for i, (x, u) in enumerate(saved):
             pin_x.numpy()[offs[i]:offs[i + 1]] = x
             pin_u.numpy()[offs[i]:offs[i + 1]] = u
         del saved
         ocaps = np.concatenate([[0], np.cumsum(caps)])
-        out_x = torch.empty(int(ocaps[-1]), dtype=torch.float32, pin_memory=True)
+        out_x = torch.empty(int(ocaps[-1]), dtype=xdt, pin_memory=True)
         out_u = torch.empty(int(ocaps[-1]), dtype=torch.float32, pin_memory=True)
         nout = C.c_int64()
         ksteps = args.steps

@@ -1044,6 +1044,38 @@ def test_decomposed_frame_dragging_tube_equals_the_whole_tube(gpu_lib, prec):
     dt.close()
 
 
+@pytest.mark.parametrize("n", [1, 16])
+def test_decomposed_tube_with_one_and_sixteen_equal_subdomains(gpu_lib, n):
+    """The degenerate split (one sub-domain: no exchange) and 16 equal
+    sub-domains of 64 cells on config 1 with a prefilled random beam equal the
+    whole tube bit for bit after 300 steps; loading particles into a tube
+    that has stepped is refused; the decomposed Eq. 4 solve (density summed
+    over the sub-domains) agrees with the whole tube's to rounding."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FP32, accumulate=B.SCLF_ACC_FIXED64)
+    z, u = synth.random_particles(30000, kw["L_over_R"] * 0.999, seed=21, u_sigma=3.0)
+    whole = B.Tube(B.default_params(**kw))
+    whole.add_particles(z, u)
+    whole.solve_fields()
+    f0 = whole.read_fields(rho=False)
+    dt = B.DTube(B.default_params(**kw), n=n)
+    dt.load_particles(z, u)
+    dt.solve_fields()
+    fs = dt.read_fields()
+    assert rel(fs["ez"], f0["ez"]) < 1e-12 and rel(fs["er"], f0["er"]) < 1e-12
+    dt.set_fields(f0["ez"], f0["er"], f0["b"])
+    whole.run(300)
+    dt.run(300)
+    _same_run(whole, dt, "%d sub-domains" % n)
+    ex = dt.exchange_stats()
+    assert ex["field_bytes"] == 300 * (n - 1) * (16 + 16 + 8)
+    assert (ex["particles"] > 0) == (n > 1)
+    with pytest.raises(B.SclfError) as e:
+        dt.load_particles(z[:10], u[:10])
+    assert e.value.code == -7
+    whole.close()
+    dt.close()
+
+
 def test_diagnostics_match_the_oracle(gpu_lib):
     """tube_diagnostics (gamma max and mean, kinetic and field energy, Gauss
     residual) against the same quantities from the oracle's state after 150
