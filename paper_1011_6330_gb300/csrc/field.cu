@@ -98,11 +98,11 @@ __device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
     field_store<Real, kAcc>(a, j, in);
 }
 
-template <class Real, int kAcc>
 // 128 threads per block: measured 4-5 % faster than 256 on the 16384-cell
 // adjoint tube (22.99 -> 21.93 ms per 2000-step forward pass), where the
 // kernel is latency-bound and more blocks spread its loads over more SMs.
 constexpr int kFieldBlock = 128;
+template <class Real, int kAcc>
 __global__ void __launch_bounds__(kFieldBlock) field_kernel(const FieldArgs<Real> a) {
     const int j = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.hi) return;
