@@ -252,16 +252,36 @@ __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(c
     long long removed = 0;
     bool nonfinite = false;
     if constexpr (kStages == 1) {
-        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT;
-            int xs[kPPT];
-            float us[kPPT];
+        // the next tile's slots are loaded into registers before this tile's
+        // work, so every warp keeps loads in flight while it computes
+        // (measured on one box: 0.3146 against 0.3171 ms on the 1e8 tube,
+        // 3.487 against 3.572 ms on the 2^30 tube, although ptxas spills
+        // 36 bytes at 4 CTAs per SM; at 3 CTAs per SM, without spills, it
+        // is 0.370 ms)
+        int xs[kPPT], xn[kPPT];
+        float us[kPPT], un[kPPT];
+        const long long t0 = blockIdx.x;
+        if (t0 < ntiles) {
+            const long long i0 = t0 * kTile + static_cast<long long>(threadIdx.x) * kPPT;
 #pragma unroll
             for (int v = 0; v < kPPT; v += kVec) {
                 vload(a.X + i0 + v, xs + v);
                 vload(a.u + i0 + v, us + v);
             }
+        }
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const long long nt = tile + gridDim.x;
+            if (nt < ntiles) {
+                const long long i1 = nt * kTile + static_cast<long long>(threadIdx.x) * kPPT;
+#pragma unroll
+                for (int v = 0; v < kPPT; v += kVec) {
+                    vload(a.X + i1 + v, xn + v);
+                    vload(a.u + i1 + v, un + v);
+                }
+            }
             fix32_tile(c, tile, xs, us, w0_acc, removed, nonfinite);
+#pragma unroll
+            for (int k = 0; k < kPPT; ++k) { xs[k] = xn[k]; us[k] = un[k]; }
         }
     } else {
         extern __shared__ __align__(128) unsigned char ring_smem[];
