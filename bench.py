@@ -41,6 +41,24 @@ KERNEL_SRC = {"gr1e8": ["push.cu", "device_common.cuh", "sclf_internal.h"],
               "batch": ["push.cu", "device_common.cuh", "sclf_internal.h"],
               "batch_fix32": ["push_fix32.cu", "device_common.cuh", "sclf_internal.h"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_kernel_traffic.json")
+# Per-kernel event timing inside the timed region samples every TIME_EVERY-th
+# unit of work (a step launched on its own or a 64-step graph replay): each
+# event-record node adds about 2 us to the run's pace, which the unsampled
+# value would carry on every step.
+TIME_EVERY = 4
+TIMING_SAMPLE = ("CUDA events around the kernels of every %dth unit of work in the timed "
+                 "region (one step or one 64-step graph replay)" % TIME_EVERY)
+
+
+# tube_params.launch_overlap of every tube the run builds (0: the library's
+# default, programmatic dependent launch of a step's kernels; -1: plain
+# stream order)
+LAUNCH_OVERLAP = [0]
+
+
+def tube_params(B, **kw):
+    kw.setdefault("launch_overlap", LAUNCH_OVERLAP[0])
+    return B.default_params(**kw)
 
 
 def parse():
@@ -79,10 +97,15 @@ def parse():
     ap.add_argument("--push-stages", type=int, default=0,
                     help="gr1e8/large: shared-memory stages of the particle kernel's bulk-copy "
                          "ring (1: loads straight into registers; 0: the library's default)")
+    ap.add_argument("--launch-overlap", choices=["on", "off"], default="on",
+                    help="step kernels by programmatic dependent launch (on, the library's "
+                         "default) or in plain stream order (off)")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="adjoint workload: no event-record nodes (for ncu runs, where "
                          "each event node is very slow); no per-kernel times or roofline")
-    return ap.parse_args()
+    args = ap.parse_args()
+    LAUNCH_OVERLAP[0] = 1 if args.launch_overlap == "on" else -1
+    return args
 
 
 def dist_env():
@@ -226,7 +249,7 @@ def build_tube(B, workloads, workload, n, acc, order, seed, sort_interval=0, nz=
                                **({"Nz": nz} if nz else {}))
     kw["sort_interval"] = sort_interval
     kw["push_stages"] = push_stages
-    t = B.Tube(B.default_params(**kw))
+    t = B.Tube(tube_params(B, **kw))
     d = t.derived
     # frame-dragging ramp for the initial momenta: gamma_far = Lambda0^2 kappa cos i
     eta_scale = d["R_over_Rstar"]
@@ -476,7 +499,7 @@ def run_batch(args, sub=False):
     bprec = B.SCLF_FP32 if getattr(args, "batch_precision", "fix32") == "f32" else B.SCLF_FIX32
     fix = bprec == B.SCLF_FIX32
     kws = workloads.death_line_batch(seed=rank_seed(rank), precision=bprec)
-    params = [B.default_params(**kw) for kw in kws]
+    params = [tube_params(B, **kw) for kw in kws]
     batch = B.Batch(params)
     plain = [B.Tube(p) for p in params]
     states = []
@@ -502,7 +525,7 @@ def run_batch(args, sub=False):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    batch.set_timing(True)
+    batch.set_timing(TIME_EVERY)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
@@ -520,7 +543,7 @@ def run_batch(args, sub=False):
     n1 = sum(t.status()["n_particles"] for t in batch.tubes)
     work, el_s = combine_ranks(0.5 * (n0 + n1) * args.steps, el_s, device="cuda")
     push_avg_ms = tm["push_ms"] / max(tm["n_steps"], 1)
-    slots = tm["particle_slots"] / max(tm["n_steps"], 1)
+    slots = tm["particle_slots"] / max(tm["steps_run"], 1)
     achieved = BYTES_PER_PARTICLE * slots / (push_avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
@@ -646,9 +669,12 @@ def run_batch(args, sub=False):
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],
+                     "timed_steps": tm["n_steps"], "timing_sample": TIMING_SAMPLE,
                      "bytes_per_launch": BYTES_PER_PARTICLE * slots},
         "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": int(2 * tm["n_steps"] + tm["n_compactions"] * len(kws)),
+        # per step: descriptor refresh, particle and field kernels; one
+        # compaction kernel per tube per check
+        "gpu_launches": int(3 * tm["steps_run"] + tm["compactions_run"] * len(kws)),
         "clocks": clk,
         "status": {"check": int(max(t.check() for t in batch.tubes))},
     }
@@ -670,7 +696,7 @@ ADJ_STEPS, ADJ_EVERY, ADJ_TIME_EVERY = 2000, 100, 5
 def adjoint_state(B, kw, seed):
     """Seeded prefilled beam of the adjoint workload (as for gr1e8)."""
     from paper_1011_6330_gb300 import synth
-    d = B.derive(B.default_params(**kw))
+    d = B.derive(tube_params(B, **kw))
     gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
     return synth.prefilled_beam(kw["target_particles"], d["L"] - d["dz"], gfar, seed=seed,
                                 eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
@@ -719,9 +745,9 @@ def run_adjoint(args, sub=False):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kw = workloads.adjoint_tube()
-    d = B.derive(B.default_params(**kw))
+    d = B.derive(tube_params(B, **kw))
     z, u = adjoint_state(B, kw, rank_seed(rank))
-    a = B.Adjoint(B.default_params(**kw), ADJ_STEPS, ADJ_EVERY)
+    a = B.Adjoint(tube_params(B, **kw), ADJ_STEPS, ADJ_EVERY)
     a.tube.add_particles(z, u)
     n_eval = max(1, args.steps // ADJ_STEPS)
     timed = not args.no_kernel_timing
@@ -760,7 +786,7 @@ def run_adjoint(args, sub=False):
     work, el_s = combine_ranks(psteps * n_eval, el_s, device="cuda")
     # the plain form: the same tube and particles stepped by tube_run (graphs,
     # no event nodes), timed by events around the whole run
-    t = B.Tube(B.default_params(**dict(kw, track_ids=0)))
+    t = B.Tube(tube_params(B, **dict(kw, track_ids=0)))
     t.add_particles(z, u)
     t.solve_fields()
     t.run(2 * ADJ_EVERY)
@@ -780,7 +806,7 @@ def run_adjoint(args, sub=False):
     # run is one segment when its snapshots fit, so the backward pass
     # replays nothing (one warm-up evaluation, then one timed without event nodes)
     a.close()
-    a1 = B.Adjoint(B.default_params(**kw), ADJ_STEPS, 0)
+    a1 = B.Adjoint(tube_params(B, **kw), ADJ_STEPS, 0)
     a1.tube.add_particles(z, u)
     a1.forward()
     a1.backward(B.SCLF_OBJ_GAMMA)
@@ -795,7 +821,7 @@ def run_adjoint(args, sub=False):
                                            for x, y in zip(g1, grad_gamma)]}
     a1.close()
     # FP32 against FP64: the same run with FP64 particles
-    a64 = B.Adjoint(B.default_params(**dict(kw, precision=B.SCLF_FP64)), ADJ_STEPS, ADJ_EVERY)
+    a64 = B.Adjoint(tube_params(B, **dict(kw, precision=B.SCLF_FP64)), ADJ_STEPS, ADJ_EVERY)
     a64.tube.add_particles(z, u)
     v64 = a64.forward()
     g64 = [a64.param_gradient(*a64.backward(i)) for i in (B.SCLF_OBJ_GAMMA, B.SCLF_OBJ_EZ)]
@@ -805,7 +831,7 @@ def run_adjoint(args, sub=False):
     val_err32 = [float(abs(x - y) / abs(y)) for x, y in zip(vals, v64)]
     # the same run with 32-bit fixed-point positions (SCLF_FIX32): its speed
     # (one untimed-graph evaluation after one warm-up) and its error against FP64
-    ax = B.Adjoint(B.default_params(**dict(kw, precision=B.SCLF_FIX32)), ADJ_STEPS, ADJ_EVERY)
+    ax = B.Adjoint(tube_params(B, **dict(kw, precision=B.SCLF_FIX32)), ADJ_STEPS, ADJ_EVERY)
     ax.tube.add_particles(z, u)
     ax.forward()
     ax.backward(B.SCLF_OBJ_GAMMA)
@@ -861,7 +887,7 @@ def run_adjoint(args, sub=False):
     if not args.no_e2e:
         spec, theta0 = B.adjoint_problem({k: v for k, v in kw.items() if k not in ("dt", "R_cm")},
                                          ADJ_STEPS, ADJ_EVERY, z, u)
-        spec["params"].update(dt=kw["dt"], R_cm=kw["R_cm"])
+        spec["params"].update(dt=kw["dt"], R_cm=kw["R_cm"], launch_overlap=LAUNCH_OVERLAP[0])
         reps = []
         for i in range(3):
             torch.cuda.synchronize()
@@ -953,14 +979,14 @@ def precision_vs_fp64(B, workloads, seed):
     from paper_1011_6330_gb300 import synth
     kw = workloads.gr_tube(n_particles=PREC_N, precision=B.SCLF_FP64,
                            accumulate=B.SCLF_ACC_FIXED64)
-    d = B.derive(B.default_params(**kw))
+    d = B.derive(tube_params(B, **kw))
     L = d["L"]
     gfar = d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"])
     z, u = synth.prefilled_beam(PREC_N, L - d["dz"], gfar, seed=seed,
                                 eta_of_z=lambda zz: 1.0 + zz * d["R_over_Rstar"])
     runs = {}
     for name, prec in (("fp64", B.SCLF_FP64), ("fix32", B.SCLF_FIX32), ("f32", B.SCLF_FP32)):
-        t = B.Tube(B.default_params(**dict(kw, precision=prec)))
+        t = B.Tube(tube_params(B, **dict(kw, precision=prec)))
         t.add_particles(z, u)
         t.solve_fields()
         t.run(PREC_STEPS)
@@ -997,7 +1023,7 @@ def batch_precision_vs_fp64(B, workloads, seed, n_sample=8, steps=2000):
         kw = dict(kws[i], track_ids=0)
         ez = {}
         for name, prec in (("fp64", B.SCLF_FP64), ("fix32", B.SCLF_FIX32), ("f32", B.SCLF_FP32)):
-            t = B.Tube(B.default_params(**dict(kw, precision=prec)))
+            t = B.Tube(tube_params(B, **dict(kw, precision=prec)))
             d = t.derived
             gr = kw["rho_gj_mode"] == B.SCLF_RHO_GR
             gfar = (d["Lambda0"] ** 2 * d["kappa"] * math.cos(kw["incl_rad"]) if gr
@@ -1035,7 +1061,7 @@ def secondary_tube(B, workloads, n, precision, acc, order, seed, steps, warmup):
     tm = t.timing()
     t.close()
     push_ms = tm["push_ms"] / max(tm["n_steps"], 1)
-    slots = tm["particle_slots"] / max(tm["n_steps"], 1)
+    slots = tm["particle_slots"] / max(tm["steps_run"], 1)
     peak, kind = measured_peaks()
     achieved = BYTES_PER_PARTICLE * slots / (push_ms * 1e-3) / 1e9
     return {"positions": precision, "current_accumulator": "fp64" if acc == B.SCLF_ACC_FP64
@@ -1116,7 +1142,7 @@ def main():
     time.sleep(0.4)
     barrier(ws)
     torch.cuda.synchronize()
-    t.set_timing(True)
+    t.set_timing(TIME_EVERY)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -1136,7 +1162,7 @@ def main():
 
     # roofline of the dominant kernel (the particle kernel)
     push_avg_ms = tm["push_ms"] / max(tm["n_steps"], 1)
-    slots_per_launch = tm["particle_slots"] / max(tm["n_steps"], 1)
+    slots_per_launch = tm["particle_slots"] / max(tm["steps_run"], 1)
     achieved = BYTES_PER_PARTICLE * slots_per_launch / (push_avg_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
@@ -1150,7 +1176,7 @@ def main():
                 and ent.get("accumulate", "fixed64") == args.accumulate \
                 and ent.get("order", "descending") == args.order and ent.get("particles") == n:
             traffic = ent["bytes_per_launch"]
-    gpu_launches = 2 * tm["n_steps"] + tm["n_compactions"]
+    gpu_launches = 2 * tm["steps_run"] + tm["compactions_run"]
     check = t.check()
 
     # end to end through the C ABI with pinned host buffers
@@ -1226,6 +1252,7 @@ def main():
                    "dt_R_over_c": d["dt"], "order": args.order,
                    "current_accumulator": args.accumulate,
                    "push_stages": args.push_stages or "default",
+                   "launch_overlap": getattr(args, "launch_overlap", "on"),
                    "sort_by_cell": ({"interval_steps": args.sort_interval,
                                      "first_sort_ms_wall": sort_ms}
                                     if args.sort_interval > 0 else None),
@@ -1239,7 +1266,8 @@ def main():
                      "peak_source": peak_kind, "push_ms_avg": push_avg_ms,
                      "field_ms_avg": tm["field_ms"] / max(tm["n_steps"], 1),
                      "compact_ms_total": tm["compact_ms"],
-                     "compaction_checks": tm["n_compactions"],
+                     "compaction_checks": tm["compactions_run"],
+                     "timed_steps": tm["n_steps"], "timing_sample": TIMING_SAMPLE,
                      "bytes_per_launch": BYTES_PER_PARTICLE * slots_per_launch},
         "cpu_baseline": cpu,
         "cpu_baseline_allcore": cpu_all,

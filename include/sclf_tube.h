@@ -144,6 +144,17 @@ typedef struct tube_params {
                               bound by instruction issue, not by load
                               latency). Results do not depend on it (bit
                               for bit); < 0 or > 4 is EINVAL              */
+    int32_t launch_overlap;/* consecutive kernels of a step (particles, fields;
+                              in batches and adjoint passes too): 0 -> the
+                              library's default (1); 1: programmatic
+                              dependent launch, each kernel launched as the
+                              CTAs of the one before it exit and waiting for
+                              it on the device before its first memory
+                              access (hides the launch: +10 % on a 1e6-
+                              particle tube, neutral on 1e8); -1: plain
+                              stream order. Results do not depend on it
+                              (bit for bit); other values are EINVAL. A
+                              batch takes its first tube's setting        */
 } tube_params;
 
 /* Code-unit quantities derived from tube_params (all FP64). */
@@ -180,14 +191,20 @@ typedef struct tube_stats {
     uint32_t reserved;
 } tube_stats;
 
-/* Kernel timings accumulated while timing is enabled. */
+/* Kernel timings accumulated while timing is enabled. With a sampling
+ * period n > 1 (tube_set_timing) the times cover the sampled steps only;
+ * per-launch averages are push_ms / n_steps and particle_slots / steps_run. */
 typedef struct tube_timing {
     double push_ms;            /* summed device time of the particle kernel  */
     double field_ms;           /* summed device time of the field kernel     */
     double compact_ms;         /* summed device time of compactions          */
     int64_t n_steps;           /* steps timed                                */
     int64_t n_compactions;     /* compactions timed                          */
-    int64_t particle_slots;    /* sum over timed steps of slots processed    */
+    int64_t particle_slots;    /* slots processed by the particle kernel, all
+                                  steps since timing was enabled            */
+    int64_t steps_run;         /* steps run since timing was enabled (timed
+                                  or not)                                    */
+    int64_t compactions_run;   /* compaction checks launched since then      */
 } tube_timing;
 
 /* Fill p with the standard pulsar of Sec. 3 (P = 1 s, B = 1e12 G,
@@ -371,10 +388,15 @@ int tube_selftest_velocity(uint32_t first, uint64_t count, uint64_t* n_mismatch,
  * capacity (plus 8 with IDs). Synchronises. */
 int tube_sort(tube_t t);
 
-/* Enable (1) or disable (0) per-kernel CUDA-event timing of steps; enabling
- * clears the accumulated numbers. Graph replays then carry event-record
- * nodes around each kernel; reading them back waits for the replay two
- * chunks earlier. */
+/* Per-kernel CUDA-event timing of steps: enable = n >= 1 times every n-th
+ * unit of work, a unit being one step launched on its own or one graph
+ * replay of a compaction interval's steps (every step: n = 1); 0 disables;
+ * < 0 is EINVAL. Enabling clears the accumulated numbers. A timed graph
+ * replay carries an event-record node before each kernel (and one after the
+ * last); each such node adds a few microseconds to the run, so a sampling
+ * period keeps the run's own pace close to the untimed one. Compaction
+ * checks are timed whenever timing is enabled. Reading a timed replay back
+ * waits for the replay two timed chunks earlier. */
 int tube_set_timing(tube_t t, int enable);
 
 /* Accumulated timings since timing was enabled. Synchronises. */
@@ -497,7 +519,10 @@ int batch_step(batch_t b);
  * Asynchronous. */
 int batch_run(batch_t b, int64_t nsteps);
 
-/* Per-kernel event timing of the batched launches (as tube_set_timing). */
+/* Per-kernel event timing of the batched launches: enable = n >= 1 times
+ * every n-th step (each timed step is launched on its own, with event
+ * records around its kernels); with n > 1 the other steps run as graph
+ * replays where the step count allows; 0 disables; < 0 is EINVAL. */
 int batch_set_timing(batch_t b, int enable);
 
 /* Accumulated timings; particle_slots sums over all tubes. Synchronises. */

@@ -43,6 +43,7 @@ class TubeParams(C.Structure):
         ("gr_variant", C.c_int32), ("gr_alpha", C.c_int32),
         ("gr_f", C.POINTER(C.c_double)), ("gr_H", C.POINTER(C.c_double)),
         ("sort_interval", C.c_int32), ("push_stages", C.c_int32),
+        ("launch_overlap", C.c_int32),
     ]
 
 
@@ -70,7 +71,8 @@ class TubeTiming(C.Structure):
     _fields_ = [
         ("push_ms", C.c_double), ("field_ms", C.c_double), ("compact_ms", C.c_double),
         ("n_steps", C.c_int64), ("n_compactions", C.c_int64),
-        ("particle_slots", C.c_int64),
+        ("particle_slots", C.c_int64), ("steps_run", C.c_int64),
+        ("compactions_run", C.c_int64),
     ]
 
 
@@ -392,7 +394,9 @@ class Tube:
         return {n: getattr(d, n) for n, _ in TubeDiag._fields_}
 
     def set_timing(self, enable):
-        _check(self.lib.tube_set_timing(self.h, 1 if enable else 0), "tube_set_timing")
+        """True or 1: time every step; n > 1: every n-th unit of work (a
+        single step or a graph replay); False or 0: off."""
+        _check(self.lib.tube_set_timing(self.h, int(enable)), "tube_set_timing")
 
     def timing(self):
         t = TubeTiming()
@@ -547,7 +551,8 @@ class Batch:
         _check(self.lib.batch_run(self.h, int(n)), "batch_run")
 
     def set_timing(self, enable):
-        _check(self.lib.batch_set_timing(self.h, 1 if enable else 0), "batch_set_timing")
+        """True or 1: time every step; n > 1: every n-th step; 0: off."""
+        _check(self.lib.batch_set_timing(self.h, int(enable)), "batch_set_timing")
 
     def timing(self):
         t = TubeTiming()

@@ -28,6 +28,7 @@ template <> struct PairT<double> { using T = double2; };
 // ---------------------------------------------------------------------------
 template <class Real>
 __global__ void __launch_bounds__(256) adj_field_kernel(const AdjFieldArgs<Real> a) {
+    grid_dependency_wait();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int nz = a.nz;
     if (j >= nz) return;
@@ -153,6 +154,7 @@ __device__ __forceinline__ void adj_push_tile(const AdjPushArgs<Real>& a, long l
 template <class Real>
 __global__ void __launch_bounds__(kThreads) adj_push_kernel(const AdjPushArgs<Real> a) {
     constexpr int kTile = Layout<Real>::kTile;
+    grid_dependency_wait();
     const long long n_slots = a.log[kLogSlots];
     const long long n_tot = n_slots + a.log[kLogInjected];
     const long long ntiles = (n_tot + kTile - 1) / kTile;
@@ -251,6 +253,7 @@ __device__ __forceinline__ void adj_push_fix32_tile(const AdjPushFixArgs& a, lon
 
 __global__ void __launch_bounds__(kThreads) adj_push_fix32_kernel(const AdjPushFixArgs a) {
     constexpr int kTile = Layout<int>::kTile;
+    grid_dependency_wait();
     const long long n_slots = a.log[kLogSlots];
     const long long n_tot = n_slots + a.log[kLogInjected];
     const long long ntiles = (n_tot + kTile - 1) / kTile;
@@ -340,10 +343,10 @@ __global__ void seed_ez_kernel(const double* ez, int nz, double dz, const double
 }  // namespace
 
 template <class Real>
-cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s) {
+cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s, bool overlap) {
     constexpr int kBlock = 128;                // as the forward field kernel
-    adj_field_kernel<Real><<<(a.nz + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(adj_field_kernel<Real>, (a.nz + kBlock - 1) / kBlock, kBlock, 0, s,
+                         overlap, a);
 }
 
 template <class Real>
@@ -355,9 +358,8 @@ int adj_push_grid_size(int device_sms) {
 }
 
 template <class Real>
-cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s) {
-    adj_push_kernel<Real><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s, bool overlap) {
+    return launch_kernel(adj_push_kernel<Real>, grid, kThreads, 0, s, overlap, a);
 }
 
 template <class Pos, class Mom>
@@ -383,9 +385,9 @@ int adj_push_fix32_grid_size(int device_sms) {
     return per_sm * device_sms;
 }
 
-cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s) {
-    adj_push_fix32_kernel<<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s,
+                                  bool overlap) {
+    return launch_kernel(adj_push_fix32_kernel, grid, kThreads, 0, s, overlap, a);
 }
 
 cudaError_t launch_seed_ez(const double* ez, int nz, double dz, const double* values,
@@ -394,10 +396,10 @@ cudaError_t launch_seed_ez(const double* ez, int nz, double dz, const double* va
     return cudaGetLastError();
 }
 
-template cudaError_t launch_adj_field<float>(const AdjFieldArgs<float>&, cudaStream_t);
-template cudaError_t launch_adj_field<double>(const AdjFieldArgs<double>&, cudaStream_t);
-template cudaError_t launch_adj_push<float>(const AdjPushArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_adj_push<double>(const AdjPushArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_adj_field<float>(const AdjFieldArgs<float>&, cudaStream_t, bool);
+template cudaError_t launch_adj_field<double>(const AdjFieldArgs<double>&, cudaStream_t, bool);
+template cudaError_t launch_adj_push<float>(const AdjPushArgs<float>&, int, cudaStream_t, bool);
+template cudaError_t launch_adj_push<double>(const AdjPushArgs<double>&, int, cudaStream_t, bool);
 template int adj_push_grid_size<float>(int);
 template int adj_push_grid_size<double>(int);
 template cudaError_t launch_objectives<float, float>(const float*, const float*, const DevState*,

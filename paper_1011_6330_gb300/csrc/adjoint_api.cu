@@ -114,7 +114,7 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
             pa.ez2 = reinterpret_cast<const float*>(tab_of(A, k));
             pa.evlog = evlog;
             pa.replay = replay;
-            e = launch_push_fix32(pa, t->push_stages, t->push_grid, s);
+            e = launch_push_fix32(pa, t->push_stages, t->push_grid, s, t->overlap);
         } else {
             PushArgs<Real> pa = push_args<Real>(t);
             pa.xi = reinterpret_cast<Real*>(A->sx[k]);
@@ -125,7 +125,8 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
             pa.ez2 = reinterpret_cast<const Real*>(tab_of(A, k));
             pa.evlog = evlog;
             pa.replay = replay;
-            e = launch_push<Real>(pa, t->p.accumulate, t->push_stages, t->push_grid, s);
+            e = launch_push<Real>(pa, t->p.accumulate, t->push_stages, t->push_grid, s,
+                                  t->overlap);
         }
         if (e == cudaSuccess) e = mark(A, timed, 2 * k + 1);
         if (e != cudaSuccess) break;
@@ -133,7 +134,7 @@ int capture_forward(sclf_adjoint* A, long long* evlog, const long long* replay,
         fa.jlast = A->jlog + static_cast<int64_t>(k) * A->nz;
         fa.ez2 = reinterpret_cast<Real*>(tab_of(A, k + 1));
         fa.evlog = evlog;
-        e = launch_field<Real>(fa, t->p.accumulate, s);
+        e = launch_field<Real>(fa, t->p.accumulate, s, t->overlap);
         if (e == cudaSuccess) e = mark(A, timed, 2 * k + 2);
     }
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -171,7 +172,7 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
         fa.cdt = t->fc.cdt;
         fa.fourpi_dt = t->fc.fourpi_dt;
         fa.s_over_dt = t->fc.s_over_dt;
-        e = launch_adj_field<Real>(fa, s);
+        e = launch_adj_field<Real>(fa, s, t->overlap);
         if (e == cudaSuccess) e = mark(A, timed, 2 * i + 1);
         if (e != cudaSuccess) break;
         if constexpr (std::is_same<Pos, int>::value) {
@@ -191,7 +192,7 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
             pa.cfl = static_cast<float>(t->d.dt / t->d.dz);
             pa.scale = std::ldexp(1.0f, -t->fb);
             pa.two_fb = std::ldexp(1.0f, t->fb);
-            e = launch_adj_push_fix32(pa, A->adj_grid, s);
+            e = launch_adj_push_fix32(pa, A->adj_grid, s, t->overlap);
         } else {
             AdjPushArgs<Real> pa;
             pa.xi = reinterpret_cast<const Real*>(A->sx[k]);
@@ -207,7 +208,7 @@ int capture_reverse(sclf_adjoint* A, const std::vector<cudaEvent_t>* timed,
             pa.nzf = static_cast<Real>(A->nz);
             pa.dt = static_cast<Real>(t->d.dt);
             pa.cfl = static_cast<Real>(t->d.dt / t->d.dz);
-            e = launch_adj_push<Real>(pa, A->adj_grid, s);
+            e = launch_adj_push<Real>(pa, A->adj_grid, s, t->overlap);
         }
         if (e == cudaSuccess) e = mark(A, timed, 2 * i + 2);
     }

@@ -104,6 +104,7 @@ __device__ __forceinline__ void field_cell(const FieldArgs<Real>& a, int j) {
 constexpr int kFieldBlock = 128;
 template <class Real, int kAcc>
 __global__ void __launch_bounds__(kFieldBlock) field_kernel(const FieldArgs<Real> a) {
+    grid_dependency_wait();
     const int j = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.hi) return;
     field_cell<Real, kAcc>(a, j);
@@ -136,6 +137,7 @@ __device__ __forceinline__ FieldArgs<float> batch_field_args(const BatchTube& d,
 __global__ void __launch_bounds__(256)
 batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ cell_tube,
                    int n_cells, int parity) {
+    grid_dependency_wait();
     const long long base = static_cast<long long>(blockIdx.x) * blockDim.x * kBatchCells +
                            threadIdx.x;
     int ti[kBatchCells];
@@ -169,21 +171,20 @@ batch_field_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ 
 }  // namespace
 
 template <class Real>
-cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate, cudaStream_t s) {
+cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate, cudaStream_t s, bool overlap) {
     const int grid = (a.hi - a.lo + kFieldBlock - 1) / kFieldBlock;
-    if (accumulate == kAccFixed) field_kernel<Real, kAccFixed><<<grid, kFieldBlock, 0, s>>>(a);
-    else field_kernel<Real, kAccF64><<<grid, kFieldBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    return accumulate == kAccFixed
+               ? launch_kernel(field_kernel<Real, kAccFixed>, grid, kFieldBlock, 0, s, overlap, a)
+               : launch_kernel(field_kernel<Real, kAccF64>, grid, kFieldBlock, 0, s, overlap, a);
 }
 
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
-                               int parity, cudaStream_t s) {
+                               int parity, cudaStream_t s, bool overlap) {
     const int per_block = 256 * kBatchCells;
-    batch_field_kernel<<<(n_cells + per_block - 1) / per_block, 256, 0, s>>>(tubes, cell_tube,
-                                                                            n_cells, parity);
-    return cudaGetLastError();
+    return launch_kernel(batch_field_kernel, (n_cells + per_block - 1) / per_block, 256, 0, s,
+                         overlap, tubes, cell_tube, n_cells, parity);
 }
 
-template cudaError_t launch_field<float>(const FieldArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_field<double>(const FieldArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_field<float>(const FieldArgs<float>&, int, cudaStream_t, bool);
+template cudaError_t launch_field<double>(const FieldArgs<double>&, int, cudaStream_t, bool);
 }  // namespace sclf

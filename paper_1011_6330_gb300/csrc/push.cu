@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, kPushMinBlocks)
 push_kernel(const PushArgs<Real> a) {
     constexpr int kTile = Layout<Real>::kTile;
     using AccT = typename AccType<kAcc>::T;
+    grid_dependency_wait();
     DevState* st = a.st;
     const long long n_req = requested_injection(st, a.replay);
     const long long n_inj = clipped_injection(st, a.capacity, n_req);
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
                   long long n_tiles) {
     constexpr int kTile = kThreads * kPPT;
+    grid_dependency_wait();
     long long w0 = 0, removed = 0;
     bool nonfinite = false;
     // The tube of the next tile is loaded one tile ahead; the tube's step
@@ -405,6 +407,7 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
                         const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
                         long long n_tiles) {
     constexpr int kTile = kThreads * kPPT;
+    grid_dependency_wait();
     long long w0 = 0, removed = 0;
     bool nonfinite = false;
     int ti = blockIdx.x < n_tiles ? tile_tube[blockIdx.x] : 0;
@@ -443,6 +446,7 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
 }
 
 __global__ void batch_refresh_kernel(BatchTube* tubes, int n_tubes) {
+    grid_dependency_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tubes) return;
     BatchTube& d = tubes[i];
@@ -532,13 +536,14 @@ int push_grid_acc(int stages, int device_sms) {
 }
 
 template <class Real, int kAcc>
-void launch_push_acc(const PushArgs<Real>& a, int stages, int grid, cudaStream_t s) {
+cudaError_t launch_push_acc(const PushArgs<Real>& a, int stages, int grid, cudaStream_t s,
+                            bool overlap) {
     const size_t smem = push_smem_bytes<Real>(stages);
     switch (stages) {
-        case 1: push_kernel<Real, kAcc, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case 3: push_kernel<Real, kAcc, 3><<<grid, kThreads, smem, s>>>(a); break;
-        case 4: push_kernel<Real, kAcc, 4><<<grid, kThreads, smem, s>>>(a); break;
-        default: push_kernel<Real, kAcc, 2><<<grid, kThreads, smem, s>>>(a); break;
+        case 1: return launch_kernel(push_kernel<Real, kAcc, 1>, grid, kThreads, 0, s, overlap, a);
+        case 3: return launch_kernel(push_kernel<Real, kAcc, 3>, grid, kThreads, smem, s, overlap, a);
+        case 4: return launch_kernel(push_kernel<Real, kAcc, 4>, grid, kThreads, smem, s, overlap, a);
+        default: return launch_kernel(push_kernel<Real, kAcc, 2>, grid, kThreads, smem, s, overlap, a);
     }
 }
 
@@ -552,15 +557,14 @@ int push_grid_size(int accumulate, int stages, int device_sms) {
 
 template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int stages, int grid,
-                        cudaStream_t s) {
-    if (accumulate == kAccFixed) launch_push_acc<Real, kAccFixed>(a, stages, grid, s);
-    else launch_push_acc<Real, kAccF64>(a, stages, grid, s);
-    return cudaGetLastError();
+                        cudaStream_t s, bool overlap) {
+    return accumulate == kAccFixed ? launch_push_acc<Real, kAccFixed>(a, stages, grid, s, overlap)
+                                   : launch_push_acc<Real, kAccF64>(a, stages, grid, s, overlap);
 }
 
-cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s) {
-    batch_refresh_kernel<<<(n_tubes + 127) / 128, 128, 0, s>>>(tubes, n_tubes);
-    return cudaGetLastError();
+cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s, bool overlap) {
+    return launch_kernel(batch_refresh_kernel, (n_tubes + 127) / 128, 128, 0, s, overlap, tubes,
+                         n_tubes);
 }
 
 cudaError_t launch_batch_status(const BatchTube* tubes, int n_tubes, tube_stats* out,
@@ -581,19 +585,19 @@ int batch_push_grid_size(int variant, int device_sms) {
 }
 
 cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
-                              int grid, int variant, cudaStream_t s) {
+                              int grid, int variant, cudaStream_t s, bool overlap) {
 #define SCLF_BATCH_LAUNCH(P, M, T) \
-    batch_push_kernel<P, M, T><<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles)
+    return launch_kernel(batch_push_kernel<P, M, T>, grid, kThreads, 0, s, overlap, tubes, \
+                         tile_tube, n_tiles)
     switch (variant) {
-        case 1: SCLF_BATCH_LAUNCH(8, 3, false); break;
-        case 2: SCLF_BATCH_LAUNCH(4, 4, false); break;
-        case 3: SCLF_BATCH_LAUNCH(8, 4, true); break;
-        case 4: SCLF_BATCH_LAUNCH(8, 3, true); break;
-        case 5: SCLF_BATCH_LAUNCH(16, 2, true); break;
-        default: SCLF_BATCH_LAUNCH(8, 4, false); break;
+        case 1: SCLF_BATCH_LAUNCH(8, 3, false);
+        case 2: SCLF_BATCH_LAUNCH(4, 4, false);
+        case 3: SCLF_BATCH_LAUNCH(8, 4, true);
+        case 4: SCLF_BATCH_LAUNCH(8, 3, true);
+        case 5: SCLF_BATCH_LAUNCH(16, 2, true);
+        default: SCLF_BATCH_LAUNCH(8, 4, false);
     }
 #undef SCLF_BATCH_LAUNCH
-    return cudaGetLastError();
 }
 
 int batch_push_const_grid_size(int variant, int device_sms) {
@@ -609,23 +613,25 @@ int batch_push_const_grid_size(int variant, int device_sms) {
 
 cudaError_t launch_batch_push_const(const BatchConstTable& k, const BatchTube* tubes,
                                     const int* tile_tube, long long n_tiles, int grid,
-                                    int variant, cudaStream_t s) {
+                                    int variant, cudaStream_t s, bool overlap) {
 #define SCLF_BATCH_LAUNCH(P, M, T) \
-    batch_push_const_kernel<P, M, T><<<grid, kThreads, 0, s>>>(k, tubes, tile_tube, n_tiles)
+    return launch_kernel(batch_push_const_kernel<P, M, T>, grid, kThreads, 0, s, overlap, k, \
+                         tubes, tile_tube, n_tiles)
     switch (variant) {
-        case 1: SCLF_BATCH_LAUNCH(8, 3, false); break;
-        case 2: SCLF_BATCH_LAUNCH(4, 4, false); break;
-        case 3: SCLF_BATCH_LAUNCH(8, 4, true); break;
-        case 4: SCLF_BATCH_LAUNCH(8, 3, true); break;
-        case 5: SCLF_BATCH_LAUNCH(16, 2, true); break;
-        default: SCLF_BATCH_LAUNCH(8, 4, false); break;
+        case 1: SCLF_BATCH_LAUNCH(8, 3, false);
+        case 2: SCLF_BATCH_LAUNCH(4, 4, false);
+        case 3: SCLF_BATCH_LAUNCH(8, 4, true);
+        case 4: SCLF_BATCH_LAUNCH(8, 3, true);
+        case 5: SCLF_BATCH_LAUNCH(16, 2, true);
+        default: SCLF_BATCH_LAUNCH(8, 4, false);
     }
 #undef SCLF_BATCH_LAUNCH
-    return cudaGetLastError();
 }
 
 template int push_grid_size<float>(int, int, int);
 template int push_grid_size<double>(int, int, int);
-template cudaError_t launch_push<float>(const PushArgs<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_push<double>(const PushArgs<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_push<float>(const PushArgs<float>&, int, int, int, cudaStream_t,
+                                       bool);
+template cudaError_t launch_push<double>(const PushArgs<double>&, int, int, int, cudaStream_t,
+                                        bool);
 }  // namespace sclf

@@ -207,6 +207,7 @@ constexpr int kFix32MinBlocks = 4;
 template <int kStages>
 __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(const PushFixArgs a) {
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
+    grid_dependency_wait();
     DevState* st = a.st;
     const long long n_slots = st->n_slots;
     const long long n_req = a.replay ? a.replay[kLogStride * st->step + kLogInjected] : st->n_inj;
@@ -321,6 +322,7 @@ __global__ void __launch_bounds__(kThreads, kFix32MinBlocks)
 batch_push_fix32_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ tile_tube,
                         long long n_tiles) {
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
+    grid_dependency_wait();
     long long w0 = 0, removed = 0;
     bool nonfinite = false;
     int ti = blockIdx.x < n_tiles ? tile_tube[blockIdx.x] : 0;
@@ -412,20 +414,20 @@ int batch_push_fix32_grid_size(int device_sms) {
 }
 
 cudaError_t launch_batch_push_fix32(const BatchTube* tubes, const int* tile_tube,
-                                    long long n_tiles, int grid, cudaStream_t s) {
-    batch_push_fix32_kernel<<<grid, kThreads, 0, s>>>(tubes, tile_tube, n_tiles);
-    return cudaGetLastError();
+                                    long long n_tiles, int grid, cudaStream_t s, bool overlap) {
+    return launch_kernel(batch_push_fix32_kernel, grid, kThreads, 0, s, overlap, tubes, tile_tube,
+                         n_tiles);
 }
 
-cudaError_t launch_push_fix32(const PushFixArgs& a, int stages, int grid, cudaStream_t s) {
+cudaError_t launch_push_fix32(const PushFixArgs& a, int stages, int grid, cudaStream_t s,
+                              bool overlap) {
     const size_t smem = fix32_smem_bytes(stages);
     switch (stages) {
-        case 1: push_fix32_kernel<1><<<grid, kThreads, 0, s>>>(a); break;
-        case 3: push_fix32_kernel<3><<<grid, kThreads, smem, s>>>(a); break;
-        case 4: push_fix32_kernel<4><<<grid, kThreads, smem, s>>>(a); break;
-        default: push_fix32_kernel<2><<<grid, kThreads, smem, s>>>(a); break;
+        case 1: return launch_kernel(push_fix32_kernel<1>, grid, kThreads, 0, s, overlap, a);
+        case 3: return launch_kernel(push_fix32_kernel<3>, grid, kThreads, smem, s, overlap, a);
+        case 4: return launch_kernel(push_fix32_kernel<4>, grid, kThreads, smem, s, overlap, a);
+        default: return launch_kernel(push_fix32_kernel<2>, grid, kThreads, smem, s, overlap, a);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace sclf

@@ -254,7 +254,31 @@ struct AdjPushFixArgs {
     float dt, cfl, scale, two_fb;
 };
 
-// Launchers. All return cudaGetLastError() after the launch.
+// Launch of `kernel` on `grid` x `block` threads. With `overlap` the launch
+// carries programmatic stream serialisation: the grid may be launched while
+// the kernel before it in the stream is finishing (as that kernel's CTAs
+// exit). Such a kernel begins with grid_dependency_wait(), which returns once
+// that kernel has completed and its writes are visible, so the two kernels'
+// memory accesses keep stream order; what overlaps is the launch. A preceding
+// operation that is not a kernel (a copy, an event) is waited for in full.
+template <class... P, class... A>
+inline cudaError_t launch_kernel(void (*kernel)(P...), int grid, int block, size_t smem,
+                                 cudaStream_t s, bool overlap, const A&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(block));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1u : 0u;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Launchers. All return the launch's error (cudaGetLastError() after <<<>>>).
+// Those with `overlap` pass it to launch_kernel.
 // The single-tube particle kernels take `stages`: 1 loads each tile straight
 // into registers, 2..kMaxPushStages stream the next tiles through a ring of
 // that many shared-memory stages by bulk asynchronous copies (TMA).
@@ -262,13 +286,14 @@ constexpr int kMaxPushStages = 4;
 constexpr int kDefaultPushStages = 1;
 template <class Real>
 cudaError_t launch_push(const PushArgs<Real>& a, int accumulate, int stages, int grid,
-                        cudaStream_t s);
+                        cudaStream_t s, bool overlap = false);
 template <class Real>
 int push_grid_size(int accumulate, int stages, int device_sms);
 template <class Real>
 cudaError_t launch_field(const FieldArgs<Real>& a, int accumulate,
-                         cudaStream_t s);
-cudaError_t launch_push_fix32(const PushFixArgs& a, int stages, int grid, cudaStream_t s);
+                         cudaStream_t s, bool overlap = false);
+cudaError_t launch_push_fix32(const PushFixArgs& a, int stages, int grid, cudaStream_t s,
+                              bool overlap = false);
 // Shapes of the batched particle kernel: particles per thread (the tile is
 // kThreads times that), CTAs per SM in its launch bounds and per-thread
 // current runs (1: the first particle's cell; 2: also the last one's).
@@ -277,7 +302,7 @@ constexpr int kBatchPPT[kBatchVariants] = {8, 8, 4, 8, 8, 16};
 constexpr int kBatchMinBlocks[kBatchVariants] = {4, 3, 4, 4, 3, 2};
 constexpr int kBatchRuns[kBatchVariants] = {1, 1, 1, 2, 2, 2};
 cudaError_t launch_batch_push(const BatchTube* tubes, const int* tile_tube, long long n_tiles,
-                              int grid, int variant, cudaStream_t s);
+                              int grid, int variant, cudaStream_t s, bool overlap = false);
 // A tube's constants for the batched particle kernel, passed by value in the
 // kernel's parameter space (the constant bank, 32 KB at most): the compiler
 // reloads them instead of holding them in registers across a tile. Batches
@@ -301,20 +326,22 @@ static_assert(sizeof(BatchConstTable) + 3 * sizeof(void*) <= 32764,
               "kernel parameters are limited to 32764 bytes");
 cudaError_t launch_batch_push_const(const BatchConstTable& k, const BatchTube* tubes,
                                     const int* tile_tube, long long n_tiles, int grid,
-                                    int variant, cudaStream_t s);
+                                    int variant, cudaStream_t s, bool overlap = false);
 int batch_push_const_grid_size(int variant, int device_sms);
 // Copies each tube's step counters (slots, clipped injection, first ID) into
 // its descriptor before the particle launch.
-cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s);
+cudaError_t launch_batch_refresh(BatchTube* tubes, int n_tubes, cudaStream_t s,
+                                 bool overlap = false);
 cudaError_t launch_batch_status(const BatchTube* tubes, int n_tubes, tube_stats* out,
                                 cudaStream_t s);
 int batch_push_grid_size(int variant, int device_sms);
 cudaError_t launch_batch_field(const BatchTube* tubes, const int* cell_tube, int n_cells,
-                               int parity, cudaStream_t s);
+                               int parity, cudaStream_t s, bool overlap = false);
 int push_fix32_grid_size(int stages, int device_sms);
 // The SCLF_FIX32 batch's particle kernel (one shape: 8 slots per thread).
 cudaError_t launch_batch_push_fix32(const BatchTube* tubes, const int* tile_tube,
-                                    long long n_tiles, int grid, cudaStream_t s);
+                                    long long n_tiles, int grid, cudaStream_t s,
+                                    bool overlap = false);
 int batch_push_fix32_grid_size(int device_sms);
 template <class Pos, class Mom>
 cudaError_t launch_compact(const CompactArgs<Pos, Mom>& a, int grid, cudaStream_t s);
@@ -353,12 +380,14 @@ cudaError_t launch_rho(const Pos* xi, long long n_slots, double* rho_acc,
                        int nz, double scale, cudaStream_t s);
 
 template <class Real>
-cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s);
+cudaError_t launch_adj_field(const AdjFieldArgs<Real>& a, cudaStream_t s, bool overlap = false);
 template <class Real>
-cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_push(const AdjPushArgs<Real>& a, int grid, cudaStream_t s,
+                            bool overlap = false);
 template <class Real>
 int adj_push_grid_size(int device_sms);
-cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_push_fix32(const AdjPushFixArgs& a, int grid, cudaStream_t s,
+                                  bool overlap = false);
 int adj_push_fix32_grid_size(int device_sms);
 // Sums over the final state of a recorded run: out[0] = mean gamma of the
 // live slots, out[1] = ||E_z||_2 = sqrt(sum E_z^2 dz). part holds

@@ -60,6 +60,7 @@ int derive(const tube_params* p, tube_derived* d) {
     if (p->compact_interval < 0) return SCLF_EINVAL;
     if (p->sort_interval < 0) return SCLF_EINVAL;
     if (p->push_stages < 0 || p->push_stages > kMaxPushStages) return SCLF_EINVAL;
+    if (p->launch_overlap < -1 || p->launch_overlap > 1) return SCLF_EINVAL;
     if (p->gr_variant != SCLF_GR_COS && p->gr_variant != SCLF_GR_BOTH) return SCLF_EINVAL;
     if (p->gr_alpha != 0 && p->gr_alpha != 1) return SCLF_EINVAL;
     if (p->rho_gj_mode == SCLF_RHO_GR) {

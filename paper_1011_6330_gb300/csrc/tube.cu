@@ -113,15 +113,18 @@ double raw_mom(const sclf_tube* t, const void* raw, int64_t i) {
 }
 
 cudaError_t enqueue_push(sclf_tube* t, cudaStream_t s) {
-    if (fix32(t)) return launch_push_fix32(push_fix_args(t), t->push_stages, t->push_grid, s);
+    if (fix32(t))
+        return launch_push_fix32(push_fix_args(t), t->push_stages, t->push_grid, s, t->overlap);
     return fp64(t) ? launch_push<double>(push_args<double>(t), t->p.accumulate, t->push_stages,
-                                         t->push_grid, s)
+                                         t->push_grid, s, t->overlap)
                    : launch_push<float>(push_args<float>(t), t->p.accumulate, t->push_stages,
-                                        t->push_grid, s);
+                                        t->push_grid, s, t->overlap);
 }
 cudaError_t enqueue_field(sclf_tube* t, int parity, cudaStream_t s) {
-    return fp64(t) ? launch_field<double>(field_args<double>(t, parity), t->p.accumulate, s)
-                   : launch_field<float>(field_args<float>(t, parity), t->p.accumulate, s);
+    return fp64(t) ? launch_field<double>(field_args<double>(t, parity), t->p.accumulate, s,
+                                          t->overlap)
+                   : launch_field<float>(field_args<float>(t, parity), t->p.accumulate, s,
+                                         t->overlap);
 }
 // The compaction follows a field kernel, whose commit resets the tile
 // ticket; a compaction outside the step sequence resets it first.
@@ -156,7 +159,8 @@ int reserve_events(sclf_tube* t, int k) {
 
 int one_step(sclf_tube* t) {
     const int parity = static_cast<int>(t->host_step & 1);
-    if (t->timing) {
+    const bool timed = t->timing && (t->timing_tick++ % t->timing_every) == 0;
+    if (timed) {
         const int e0 = reserve_events(t, 3);
         if (e0 < 0) return SCLF_ECUDA;
         CK(cudaEventRecord(t->ev[e0], t->stream));
@@ -171,7 +175,9 @@ int one_step(sclf_tube* t) {
     }
     t->host_step += 1;
     t->steps_since_compact += 1;
+    if (t->timing) t->acc.steps_run += 1;
     if (t->steps_since_compact >= t->compact_every) {
+        if (t->timing) t->acc.compactions_run += 1;
         if (t->timing) {
             const int e0 = reserve_events(t, 2);
             if (e0 < 0) return SCLF_ECUDA;
@@ -189,9 +195,10 @@ int one_step(sclf_tube* t) {
 
 // One captured graph = chunk_steps steps starting at even parity, then a
 // compaction check (chunk_steps == compact interval, rounded up to even).
-// With ev != nullptr, event-record nodes bracket every kernel: ev[3k],
-// ev[3k+1], ev[3k+2] around step k's particle and field kernels and the last
-// two around the compaction.
+// With ev != nullptr, an event-record node precedes every kernel: ev[2k]
+// step k's particle kernel, ev[2k+1] its field kernel, ev[2n] the
+// compaction, and ev[2n+1] follows it (step k's field kernel ends at
+// ev[2k+2]).
 int capture_chunk(sclf_tube* t, cudaGraphExec_t* out, const std::vector<cudaEvent_t>* ev) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
@@ -202,15 +209,14 @@ int capture_chunk(sclf_tube* t, cudaGraphExec_t* out, const std::vector<cudaEven
     };
     const int n = t->chunk_steps;
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
-        mark(3 * k);
+        mark(2 * k);
         if (e == cudaSuccess) e = enqueue_push(t, t->gstream);
-        mark(3 * k + 1);
+        mark(2 * k + 1);
         if (e == cudaSuccess) e = enqueue_field(t, k & 1, t->gstream);
-        mark(3 * k + 2);
     }
-    mark(3 * n);
+    mark(2 * n);
     if (e == cudaSuccess) e = enqueue_compact(t, t->gstream, 0);
-    mark(3 * n + 1);
+    mark(2 * n + 1);
     const cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e); }
     CK(e2);
@@ -230,16 +236,16 @@ int collect_chunk(sclf_tube* t, int which) {
     auto& c = t->tchunk[which];
     if (!c.pending) return SCLF_OK;
     const int n = t->chunk_steps;
-    CK(cudaEventSynchronize(c.ev[3 * n + 1]));
+    CK(cudaEventSynchronize(c.ev[2 * n + 1]));
     for (int k = 0; k < n; ++k) {
         float a = 0.f, b = 0.f;
-        CK(cudaEventElapsedTime(&a, c.ev[3 * k], c.ev[3 * k + 1]));
-        CK(cudaEventElapsedTime(&b, c.ev[3 * k + 1], c.ev[3 * k + 2]));
+        CK(cudaEventElapsedTime(&a, c.ev[2 * k], c.ev[2 * k + 1]));
+        CK(cudaEventElapsedTime(&b, c.ev[2 * k + 1], c.ev[2 * k + 2]));
         t->acc.push_ms += a;
         t->acc.field_ms += b;
     }
     float cm = 0.f;
-    CK(cudaEventElapsedTime(&cm, c.ev[3 * n], c.ev[3 * n + 1]));
+    CK(cudaEventElapsedTime(&cm, c.ev[2 * n], c.ev[2 * n + 1]));
     t->acc.compact_ms += cm;
     t->acc.n_compactions += 1;
     t->acc.n_steps += n;
@@ -268,7 +274,7 @@ int launch_timed_chunk(sclf_tube* t) {
     int rc = collect_chunk(t, w);
     if (rc) return rc;
     if (!c.exec) {
-        c.ev.resize(3 * t->chunk_steps + 2, nullptr);
+        c.ev.resize(2 * t->chunk_steps + 2, nullptr);
         for (auto& e : c.ev) CK(cudaEventCreate(&e));
         rc = capture_chunk(t, &c.exec, &c.ev);
         if (rc) return rc;
@@ -555,6 +561,7 @@ int tube_create(const tube_params* p, void* dev_workspace, int64_t ws_bytes, voi
     if (cudaStreamSynchronize(t->stream) != cudaSuccess) return fail(SCLF_ECUDA);
 
     t->push_stages = p->push_stages > 0 ? p->push_stages : kDefaultPushStages;
+    t->overlap = p->launch_overlap >= 0;
     t->push_grid = fix32(t) ? push_fix32_grid_size(t->push_stages, t->sms)
                  : fp64(t) ? push_grid_size<double>(p->accumulate, t->push_stages, t->sms)
                            : push_grid_size<float>(p->accumulate, t->push_stages, t->sms);
@@ -650,13 +657,17 @@ int tube_run(tube_t t, int64_t nsteps) {
         if (t->p.use_graphs && (t->host_step & 1) == 0 &&
             t->steps_since_compact == 0 && nsteps >= t->chunk_steps) {
             int rc;
-            if (t->timing) {
+            if (t->timing && (t->timing_tick++ % t->timing_every) == 0) {
                 rc = launch_timed_chunk(t);
             } else {
                 rc = build_chunk(t);
                 if (!rc) rc = launch_chunk(t);
             }
             if (rc) return rc;
+            if (t->timing) {
+                t->acc.steps_run += t->chunk_steps;
+                t->acc.compactions_run += 1;
+            }
             nsteps -= t->chunk_steps;
             t->steps_since_sort += t->chunk_steps;
             continue;
@@ -1032,7 +1043,7 @@ int tube_compact(tube_t t) {
 }
 
 int tube_set_timing(tube_t t, int enable) {
-    if (!t) return SCLF_EINVAL;
+    if (!t || enable < 0) return SCLF_EINVAL;
     if (enable) {
         if (t->ev.empty()) {
             t->ev.resize(3 * 2048 + 8, nullptr);
@@ -1049,6 +1060,8 @@ int tube_set_timing(tube_t t, int enable) {
         if (rc) return rc;
         t->slots_base = h.slots_processed;
         t->timing = true;
+        t->timing_every = enable;
+        t->timing_tick = 0;
     } else {
         const int rc = drain_timing(t);
         t->timing = false;
@@ -1120,12 +1133,15 @@ struct sclf_batch {
     int variant = 0;                   // particle kernel shape (batch_autotune)
     bool fix32 = false;                // SCLF_FIX32 tubes: one particle-kernel shape
     int fix_grid = 0;
+    bool overlap = true;               // step kernels by programmatic dependent launch
     int64_t host_step = 0;
     int steps_since_compact = 0;
     int compact_every = 64;
     int chunk_steps = 64;
     cudaGraphExec_t chunk = nullptr;
     bool timing = false;
+    int timing_every = 1;              // sampling period (steps)
+    int64_t timing_tick = 0;
     std::vector<cudaEvent_t> ev;       // 3 per step, 2 per compaction round
     std::vector<std::pair<int, int>> recs;
     int ev_next = 0;
@@ -1146,23 +1162,26 @@ int tile_class(int variant) {
 
 cudaError_t batch_launch_push(sclf_batch* b, cudaStream_t s) {
     if (b->fix32) {
-        const cudaError_t e = launch_batch_refresh(b->d_desc[0], static_cast<int>(b->tubes.size()), s);
+        const cudaError_t e = launch_batch_refresh(b->d_desc[0], static_cast<int>(b->tubes.size()),
+                                                   s, b->overlap);
         if (e != cudaSuccess) return e;
-        return launch_batch_push_fix32(b->d_desc[0], b->d_tile_tube[0], b->n_tiles[0], b->fix_grid, s);
+        return launch_batch_push_fix32(b->d_desc[0], b->d_tile_tube[0], b->n_tiles[0], b->fix_grid,
+                                       s, b->overlap);
     }
     const int c = tile_class(b->variant);
-    const cudaError_t e = launch_batch_refresh(b->d_desc[c], static_cast<int>(b->tubes.size()), s);
+    const cudaError_t e = launch_batch_refresh(b->d_desc[c], static_cast<int>(b->tubes.size()), s,
+                                               b->overlap);
     if (e != cudaSuccess) return e;
     if (!b->ctab.empty())
         return launch_batch_push_const(b->ctab[c], b->d_desc[c], b->d_tile_tube[c], b->n_tiles[c],
-                                       b->const_grid[b->variant], b->variant, s);
+                                       b->const_grid[b->variant], b->variant, s, b->overlap);
     return launch_batch_push(b->d_desc[c], b->d_tile_tube[c], b->n_tiles[c],
-                             b->push_grid[b->variant], b->variant, s);
+                             b->push_grid[b->variant], b->variant, s, b->overlap);
 }
 
 int batch_enqueue_step(sclf_batch* b, cudaStream_t s, int parity) {
     CK(batch_launch_push(b, s));
-    CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, s));
+    CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, s, b->overlap));
     return SCLF_OK;
 }
 
@@ -1208,13 +1227,15 @@ int batch_reserve(sclf_batch* b, int k) {
 
 int batch_one_step(sclf_batch* b) {
     const int parity = static_cast<int>(b->host_step & 1);
-    if (b->timing) {
+    const bool timed = b->timing && (b->timing_tick++ % b->timing_every) == 0;
+    if (timed) {
         const int e0 = batch_reserve(b, 3);
         if (e0 < 0) return SCLF_ECUDA;
         CK(cudaEventRecord(b->ev[e0], b->stream));
         CK(batch_launch_push(b, b->stream));
         CK(cudaEventRecord(b->ev[e0 + 1], b->stream));
-        CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, b->stream));
+        CK(launch_batch_field(b->d_desc[0], b->d_cell_tube, b->n_cells, parity, b->stream,
+                              b->overlap));
         CK(cudaEventRecord(b->ev[e0 + 2], b->stream));
         b->recs.push_back({0, e0});
     } else {
@@ -1222,7 +1243,9 @@ int batch_one_step(sclf_batch* b) {
         if (rc) return rc;
     }
     batch_advance(b, 1);
+    if (b->timing) b->acc.steps_run += 1;
     if (++b->steps_since_compact >= b->compact_every) {
+        if (b->timing) b->acc.compactions_run += 1;
         int e0 = -1;
         if (b->timing) {
             e0 = batch_reserve(b, 2);
@@ -1272,6 +1295,7 @@ int batch_create(int32_t n, const tube_params* params, void* stream, batch_t* ou
     if (!b) return SCLF_ENOMEM;
     b->stream = static_cast<cudaStream_t>(stream);
     b->fix32 = params[0].precision == SCLF_FIX32;
+    b->overlap = params[0].launch_overlap >= 0;
     auto fail = [&](int code) { batch_destroy(b); return code; };
     std::vector<BatchTube> desc(n);
     std::vector<int> tile_tube[kTileClasses], cell_tube;
@@ -1432,7 +1456,10 @@ int batch_run(batch_t b, int64_t nsteps) {
     NvtxRange nvtx_range("batch_run");
     if (!b || nsteps < 0) return SCLF_EINVAL;
     while (nsteps > 0) {
-        if (!b->timing && (b->host_step & 1) == 0 && b->steps_since_compact == 0 &&
+        // timed steps are launched on their own; with a sampling period the
+        // others may replay the graph
+        const bool graph_ok = !b->timing || b->timing_every > 1;
+        if (graph_ok && (b->host_step & 1) == 0 && b->steps_since_compact == 0 &&
             nsteps >= b->chunk_steps && b->tubes[0]->p.use_graphs) {
             int rc = batch_build_chunk(b);
             if (rc) return rc;
@@ -1446,6 +1473,11 @@ int batch_run(batch_t b, int64_t nsteps) {
                 CK(cudaStreamWaitEvent(b->stream, b->join, 0));
             }
             batch_advance(b, b->chunk_steps);
+            if (b->timing) {
+                b->acc.steps_run += b->chunk_steps;
+                b->acc.compactions_run += 1;
+                b->timing_tick += b->chunk_steps;
+            }
             nsteps -= b->chunk_steps;
             continue;
         }
@@ -1457,7 +1489,7 @@ int batch_run(batch_t b, int64_t nsteps) {
 }
 
 int batch_set_timing(batch_t b, int enable) {
-    if (!b) return SCLF_EINVAL;
+    if (!b || enable < 0) return SCLF_EINVAL;
     if (enable) {
         if (b->ev.empty()) {
             b->ev.resize(3 * 2048 + 8, nullptr);
@@ -1476,6 +1508,8 @@ int batch_set_timing(batch_t b, int enable) {
             b->slots_base.push_back(h.slots_processed);
         }
         b->timing = true;
+        b->timing_every = enable;
+        b->timing_tick = 0;
         return SCLF_OK;
     }
     const int rc = batch_drain(b);

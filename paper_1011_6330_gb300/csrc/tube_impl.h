@@ -50,6 +50,7 @@ struct sclf_tube {
     sclf::FieldConsts fc{};
     int push_grid = 0, compact_grid = 0;
     int push_stages = 1;               // the particle kernel's TMA ring (1: none)
+    bool overlap = true;               // step kernels by programmatic dependent launch
     int fb = 0;                        // fractional bits of SCLF_FIX32 positions
     int64_t host_step = 0;             // steps launched (== device step count)
     int steps_since_compact = 0;
@@ -68,6 +69,8 @@ struct sclf_tube {
     int tnext = 0;
     // timing
     bool timing = false;
+    int timing_every = 1;              // sampling period (units of work)
+    int64_t timing_tick = 0;
     std::vector<cudaEvent_t> ev;       // pool, 3 per step, 2 per compaction
     struct Rec { int kind; int e0; };  // kind 0 step (e0, e0+1, e0+2), 1 compaction
     std::vector<Rec> recs;

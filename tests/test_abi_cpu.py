@@ -90,7 +90,8 @@ def test_invalid_parameters_are_rejected(lib):
     for bad in (dict(dt=kw["L_over_R"] / kw["Nz"]),       # c dt = dz
                 dict(Nz=1), dict(capacity=-1), dict(precision=7),
                 dict(accumulate=3), dict(rho_gj_mode=9), dict(L_over_R=0.0),
-                dict(push_stages=-1), dict(push_stages=5)):
+                dict(push_stages=-1), dict(push_stages=5),
+                dict(launch_overlap=-2), dict(launch_overlap=2)):
         p = B.default_params(**{**kw, **bad})
         with pytest.raises(B.SclfError) as e:
             B.derive(p)

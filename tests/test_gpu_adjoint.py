@@ -271,6 +271,23 @@ def test_weighted_ez_profile_gradient_matches_oracle(gpu_lib, prec):
 
 
 @pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
+def test_launch_overlap_gives_the_same_gradient(gpu_lib, prec):
+    """The forward, recompute and reverse kernels by programmatic dependent
+    launch give the same values bit for bit as plain stream order, and the
+    same (rho_GJ, s) gradients to the order of the FP64 atomic grid sums."""
+    kw, z, u, nsteps, K = flat_problem(prec)
+    plain, vp = gpu_run(dict(kw, launch_overlap=-1), z, u, nsteps, K)
+    over, vo = gpu_run(dict(kw, launch_overlap=1), z, u, nsteps, K)
+    assert np.array_equal(vp, vo)
+    for obj in (B.SCLF_OBJ_GAMMA, B.SCLF_OBJ_EZ):
+        gp, sp = plain.backward(obj)
+        go, so = over.backward(obj)
+        assert rel(go, gp) < 1e-12 and abs(so - sp) <= 1e-12 * abs(sp), obj
+    plain.close()
+    over.close()
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
 def test_one_segment_chosen_by_the_library_gives_the_same_gradient(gpu_lib, prec):
     """checkpoint_every = 0: the library keeps the whole run as one segment
     when its snapshots fit (here they do), so the backward pass replays

@@ -933,6 +933,119 @@ def test_push_stages_change_no_result(gpu_lib, prec):
             assert np.array_equal(got[2][k], ref[2][k]), (stages, k)
 
 
+def _run_state(t):
+    st = t.status()
+    return st, t.read_particles(), t.read_fields(rho=False)
+
+
+def _same_run_state(a, b, what):
+    for k in ("step", "n_particles", "n_slots", "total_injected", "last_removed",
+              "pending_injection", "flags"):
+        assert a[0][k] == b[0][k], (what, k)
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y), what
+    for k in ("ez", "er", "b", "j"):
+        assert np.array_equal(a[2][k], b[2][k]), (what, k)
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FP64, B.SCLF_FIX32])
+def test_launch_overlap_changes_no_result(gpu_lib, prec):
+    """The step kernels launched with programmatic dependent launch (each
+    scheduled while the one before it finishes, waiting for it on the device
+    before its first memory access) give the same run bit for bit as plain
+    stream order: stepped one call at a time, in captured graphs with their
+    compaction checks, and in the timed graphs, whose event nodes sit between
+    the kernels. Injection every step, removals at both ends, a ragged last
+    tile."""
+    kw = workloads.flat_sclf_small(precision=prec, accumulate=B.SCLF_ACC_FIXED64,
+                                   capacity=1 << 22)
+    z, u = synth.random_particles(2 * 10 ** 6 + 77, kw["L_over_R"], seed=12, u_sigma=2.0)
+    got = {}
+    for ov in (-1, 1):
+        t = B.Tube(B.default_params(**kw, launch_overlap=ov))
+        t.add_particles(z, u)
+        for _ in range(5):
+            t.step()
+        t.run(130)
+        t.set_timing(True)
+        t.run(64)
+        t.set_timing(False)
+        got[ov] = _run_state(t)
+        assert got[ov][0]["flags"] == 0, ov
+        assert got[ov][0]["last_removed"] > 0, ov
+        t.close()
+    _same_run_state(got[-1], got[1], prec)
+
+
+@pytest.mark.parametrize("prec", [B.SCLF_FIX32, B.SCLF_FP32])
+def test_batch_launch_overlap_changes_no_result(gpu_lib, prec):
+    """A batch's refresh, particle and field kernels by programmatic dependent
+    launch equal the same batch in plain stream order, bit for bit, over
+    graph chunks and single steps."""
+    kws = _small_batch_params(prec)
+    states = {}
+    for ov in (-1, 1):
+        batch = B.Batch([B.default_params(**kw, launch_overlap=ov) for kw in kws])
+        for i, kw in enumerate(kws):
+            _fill(batch.tubes[i], kw, seed=i)
+        batch.run(70)
+        batch.step()
+        states[ov] = _batch_state(batch)
+        batch.close()
+    _same_state(states[-1], states[1])
+
+
+def test_sampled_timing_counts_the_run_and_keeps_its_results(gpu_lib):
+    """tube_set_timing(3) times every third unit of work (a step launched on
+    its own, or a 64-step graph replay); steps_run and compactions_run count
+    every step and compaction check, and the run equals an untimed one bit
+    for bit. batch_set_timing(2) times every second step and lets the others
+    replay the graph. The counts follow from the schedules (graph replays
+    start at an even step right after a compaction check)."""
+    kw = workloads.flat_sclf_small(precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64,
+                                   capacity=1 << 21)
+    z, u = synth.random_particles(5 * 10 ** 5 + 3, kw["L_over_R"], seed=13, u_sigma=2.0)
+    a, b = (B.Tube(B.default_params(**kw)) for _ in range(2))
+    for t in (a, b):
+        t.add_particles(z, u)
+        t.run(10)
+    a.set_timing(3)
+    a.run(300)              # 54 single steps, 3 graph replays, 54 single steps
+    tm = a.timing()
+    a.set_timing(0)
+    b.run(300)
+    _same_run_state(_run_state(a), _run_state(b), "sampled timing")
+    assert tm["steps_run"] == 300 and tm["compactions_run"] == 4
+    assert tm["n_steps"] == 18 + 64 + 18 and tm["n_compactions"] == 2
+    assert tm["push_ms"] > 0 and tm["field_ms"] > 0
+    n = a.status()["n_slots"]
+    assert 0.8 * 300 * n < tm["particle_slots"] < 1.25 * 300 * n
+    a.close()
+    b.close()
+
+    kws = _small_batch_params(B.SCLF_FIX32)
+    ba, bb = (B.Batch([B.default_params(**kw) for kw in kws]) for _ in range(2))
+    for batch in (ba, bb):
+        for i, kw in enumerate(kws):
+            _fill(batch.tubes[i], kw, seed=i)
+        batch.run(10)
+    # compaction checks every 7 steps, graph replays of 8: the 10 warm-up
+    # steps are a replay and 2 single steps; then 5 single steps (units 0-4,
+    # a check after the last), one more to reach an even step (unit 5), 6
+    # (units 6-11, a check), 17 replays (units 12-147) and 2 single steps
+    # (units 148-149); every second unit is timed
+    ba.set_timing(2)
+    ba.run(150)
+    tb = ba.timing()
+    ba.set_timing(0)
+    bb.run(150)
+    _same_state(_batch_state(ba), _batch_state(bb))
+    assert tb["steps_run"] == 150 and tb["compactions_run"] == 2 + 17
+    assert tb["n_steps"] == 3 + 3 + 1 and tb["n_compactions"] == 2
+    ba.close()
+    bb.close()
+
+
 @pytest.mark.parametrize("prec", [B.SCLF_FP32, B.SCLF_FIX32])
 def test_sort_by_cell_changes_no_result(gpu_lib, prec):
     """A shuffled beam stepped with a stable re-sort by cell every 10 steps
