@@ -278,8 +278,25 @@ template <class Real, int kAcc, int kStages>
 __global__ void __launch_bounds__(kThreads, kPushMinBlocks)
 push_kernel(const PushArgs<Real> a) {
     constexpr int kTile = Layout<Real>::kTile;
+    constexpr int kPPT1 = Layout<Real>::kPPT, kVec1 = Layout<Real>::kVec;
     using AccT = typename AccType<kAcc>::T;
     grid_dependency_wait();
+    // The CTA's first tile is loaded before the step's counters are read (the
+    // slot arrays are padded to whole tiles, and the counters only decide
+    // which of the tile's slots are live): in small tubes, where a CTA has one
+    // tile, the two loads' latencies overlap.
+    Real xs[kPPT1], us[kPPT1];
+    if constexpr (kStages == 1) {
+        if (static_cast<long long>(blockIdx.x) * kTile < a.capacity) {
+            const long long i0 = static_cast<long long>(blockIdx.x) * kTile +
+                                 static_cast<long long>(threadIdx.x) * kPPT1;
+#pragma unroll
+            for (int v = 0; v < kPPT1; v += kVec1) {
+                vload(a.xi + i0 + v, xs + v);
+                vload(a.u + i0 + v, us + v);
+            }
+        }
+    }
     DevState* st = a.st;
     const long long n_req = requested_injection(st, a.replay);
     const long long n_inj = clipped_injection(st, a.capacity, n_req);
@@ -310,7 +327,15 @@ push_kernel(const PushArgs<Real> a) {
     bool nonfinite = false;
     if constexpr (kStages == 1) {
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            push_tile<Real, kAcc>(c, tile, w0_acc, removed, nonfinite);
+            if (tile != blockIdx.x) {
+                const long long i0 = tile * kTile + static_cast<long long>(threadIdx.x) * kPPT1;
+#pragma unroll
+                for (int v = 0; v < kPPT1; v += kVec1) {
+                    vload(a.xi + i0 + v, xs + v);
+                    vload(a.u + i0 + v, us + v);
+                }
+            }
+            push_tile_body<Real, kAcc>(c, tile, xs, us, w0_acc, removed, nonfinite);
         }
     } else {
         constexpr int kPPT = Layout<Real>::kPPT, kVec = Layout<Real>::kVec;

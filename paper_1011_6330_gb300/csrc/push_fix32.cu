@@ -208,6 +208,24 @@ template <int kStages>
 __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(const PushFixArgs a) {
     constexpr int kPPT = Layout<int>::kPPT, kVec = Layout<int>::kVec, kTile = Layout<int>::kTile;
     grid_dependency_wait();
+    // The CTA's first tile is loaded before the step's counters are read: the
+    // slot arrays are padded to whole tiles, so a tile that starts below the
+    // capacity lies inside them, and the counters only decide which of its
+    // slots are live. In small tubes, where a CTA has one tile, the two
+    // loads' latencies overlap.
+    int xs[kPPT], xn[kPPT];
+    float us[kPPT], un[kPPT];
+    if constexpr (kStages == 1) {
+        if (static_cast<long long>(blockIdx.x) * kTile < a.capacity) {
+            const long long i0 = static_cast<long long>(blockIdx.x) * kTile +
+                                 static_cast<long long>(threadIdx.x) * kPPT;
+#pragma unroll
+            for (int v = 0; v < kPPT; v += kVec) {
+                vload(a.X + i0 + v, xs + v);
+                vload(a.u + i0 + v, us + v);
+            }
+        }
+    }
     DevState* st = a.st;
     const long long n_slots = st->n_slots;
     const long long n_req = a.replay ? a.replay[kLogStride * st->step + kLogInjected] : st->n_inj;
@@ -259,17 +277,6 @@ __global__ void __launch_bounds__(kThreads, kFix32MinBlocks) push_fix32_kernel(c
         // 3.487 against 3.572 ms on the 2^30 tube, although ptxas spills
         // 36 bytes at 4 CTAs per SM; at 3 CTAs per SM, without spills, it
         // is 0.370 ms)
-        int xs[kPPT], xn[kPPT];
-        float us[kPPT], un[kPPT];
-        const long long t0 = blockIdx.x;
-        if (t0 < ntiles) {
-            const long long i0 = t0 * kTile + static_cast<long long>(threadIdx.x) * kPPT;
-#pragma unroll
-            for (int v = 0; v < kPPT; v += kVec) {
-                vload(a.X + i0 + v, xs + v);
-                vload(a.u + i0 + v, us + v);
-            }
-        }
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const long long nt = tile + gridDim.x;
             if (nt < ntiles) {
