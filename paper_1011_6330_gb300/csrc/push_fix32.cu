@@ -84,28 +84,33 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
     // Runs on two cells, c_r and c_r + 1: c_r is the lower of the cells of
     // the thread's first and last slots (sorted slots at ~100 particles per
     // cell often span two cells), when it lies in [1, hi - 2] (hi = Nz for a
-    // whole tube, else the sub-domain's end); A = c_r 2^fb, else A =
-    // 0xc0000000, which puts U - A at or above 2^30 >= 2^fb for every
-    // position U < 2^31 (no particle is common). A common particle starts and
-    // ends in c_r or c_r + 1 (U - A and U1 - A below 2^(fb+1): live, cell >= 1,
-    // inside the tube and the sub-domain); in 2^-fb units its current on c_r
-    // is F_cr(X1) - F_cr(X) = min(U1 - A, 2^fb) - min(U - A, 2^fb) and the
-    // rest of its increment falls on c_r + 1, so the runs keep the sum of the
-    // increments and the sum of the parts on c_r. (Measured: 0.308 against 0.323 ms
-    // for the run on the first slot's cell alone on the 1e8-particle tube,
-    // 0.677 against 0.896 ms on the death-line batch.)
+    // whole tube, else the sub-domain's end; so Nz >= 3 and fb <= 29). With
+    // A = c_r 2^fb, a particle is common when U - A and U1 - A are both below
+    // 2^(fb+1): it starts and ends in c_r or c_r + 1 (live, cell >= 1, inside
+    // the tube and the sub-domain). In 2^-fb units its current on c_r is
+    // F_cr(X1) - F_cr(X) = min(U1 - A, 2^fb) - min(U - A, 2^fb) and the rest
+    // of its increment falls on c_r + 1, so the runs keep the sum of the
+    // increments and the sum of the parts on c_r. Without a run the bound is
+    // 0 and no particle is common. (Measured: 0.308 against 0.323 ms for the
+    // run on the first slot's cell alone on the 1e8-particle tube, 0.677
+    // against 0.896 ms on the death-line batch.)
+    // A hole carries X = -1 (removals and padding write exactly that; loaded
+    // slots have no holes), so U = 2^32 - 1: its gather index wraps to 0 and
+    // U - A >= 2^32 - 2^31 > 2^(fb+1), so it is never common and needs no
+    // test of its own on the common path.
     int xr = xs[0];
     const int xl = xs[kPPT - 1];
     xr = (xr < 0 || (xl >= 0 && xl < xr)) ? xl : xr;
     const bool has_run = xr >= static_cast<int>(one) && xr < c.hi_x - one;
-    const unsigned A = has_run ? (static_cast<unsigned>(xr) & ~mask) : 0xc0000000u;
-    const unsigned one_u = 1u << fb, two_u = 2u << fb;
-    int s_inc = 0, s_low = 0;
+    const unsigned A = static_cast<unsigned>(xr) & ~mask;
+    const unsigned one_u = 1u << fb, bound = has_run ? 2u << fb : 0u;
+    // The runs are summed modulo 2^32: every particle's increment and part on
+    // c_r are added, and those of particles that are not common are taken
+    // back out on their own path (exact, and cheaper than a select each).
+    unsigned s_inc = 0, s_low = 0;
 #pragma unroll
     for (int k = 0; k < kPPT; ++k) {
-        const int X = xs[k];
-        const bool lv = X >= 0;                  // holes and padding carry X < 0
-        const unsigned U = lv ? static_cast<unsigned>(X) : 0u;
+        const unsigned U = static_cast<unsigned>(xs[k]);
         // (a2) h = X + 2^(fb-1): m = h >> fb, f = (h mod 2^fb) 2^-fb
         const unsigned h = U + half;
         const float f = __uint2float_rn(h & mask) * scale;
@@ -124,52 +129,60 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
         // (a4) the common particle's current joins the runs
         // both offsets below 2^(fb+1), a power of two: so is their OR
         const unsigned t0 = U - A, t1 = U1 - A;
-        const bool common = fin & ((t0 | t1) < two_u);
+        const bool common = fin & ((t0 | t1) < bound);
         const int low = static_cast<int>(min(t1, one_u)) - static_cast<int>(min(t0, one_u));
-        s_inc += common ? inc : 0;
-        s_low += common ? low : 0;
-        if (lv & !common) {
-            const int XX = static_cast<int>(U);
-            const long long X1 = static_cast<long long>(XX) + inc;
-            const long long c1 = X1 >> fb;
-            const unsigned c0 = U >> fb;
-            if (!fin) {
-                nonfinite = true;
-                ++removed;
-                xs[k] = -1;
-                us[k] = 0.0f;
-            } else {
-                const long long b0 = static_cast<long long>(c0) << fb;
-                const long long f0a = min(max(static_cast<long long>(XX) - b0, 0LL), one);
-                const long long f1a = min(max(X1 - b0, 0LL), one);
-                const long long qa = shl_signed(f1a - f0a, sh);
-                if (qa && checked_index(c0, nz, c.flags)) acc_add(jacc + c0, qa);
-                if (c1 != static_cast<long long>(c0) && c1 >= 0 && c1 < nz) {
-                    const long long b1 = c1 << fb;
-                    const long long f0b = min(max(static_cast<long long>(XX) - b1, 0LL), one);
-                    const long long f1b = min(max(X1 - b1, 0LL), one);
-                    const long long qb = shl_signed(f1b - f0b, sh);
-                    if (qb) acc_add(jacc + static_cast<int>(c1), qb);
-                }
-                // (a5) removal at the ends; base-cell weight for the next injection
-                if (X1 >= c.lo_x && X1 < c.hi_x) {
-                    xs[k] = static_cast<int>(X1);
-                    us[k] = u1;
-                    if (c1 == 0) w0_acc += shl_signed(one - X1, sh);
-                } else if (X1 >= 0 && X1 < top) {         // to a neighbouring sub-domain
-                    emigrate_fix(c.out, X1 < c.lo_x ? 0 : 1, static_cast<int>(X1), u1,
-                                 c.ids ? c.ids[i0 + k] : -1LL, c.flags);
-                    xs[k] = -1;
-                    us[k] = 0.0f;
-                } else {
-                    ++removed;
-                    xs[k] = -1;
-                    us[k] = 0.0f;
-                }
+        s_inc += static_cast<unsigned>(inc);
+        s_low += static_cast<unsigned>(low);
+        if (common) {
+            xs[k] = static_cast<int>(U1);
+            us[k] = u1;
+            continue;
+        }
+        s_inc -= static_cast<unsigned>(inc);     // not in the runs: taken back out
+        s_low -= static_cast<unsigned>(low);
+        const int XX = xs[k];
+        if (XX < 0) {                            // a hole stays one
+            if constexpr (kChecked) {
+                if (XX != -1) atomicOr(c.flags, SCLF_FLAG_BOUNDS);
             }
+            continue;
+        }
+        const long long X1 = static_cast<long long>(XX) + inc;
+        const long long c1 = X1 >> fb;
+        const unsigned c0 = U >> fb;
+        if (!fin) {
+            nonfinite = true;
+            ++removed;
+            xs[k] = -1;
+            us[k] = 0.0f;
+            continue;
+        }
+        const long long b0 = static_cast<long long>(c0) << fb;
+        const long long f0a = min(max(static_cast<long long>(XX) - b0, 0LL), one);
+        const long long f1a = min(max(X1 - b0, 0LL), one);
+        const long long qa = shl_signed(f1a - f0a, sh);
+        if (qa && checked_index(c0, nz, c.flags)) acc_add(jacc + c0, qa);
+        if (c1 != static_cast<long long>(c0) && c1 >= 0 && c1 < nz) {
+            const long long b1 = c1 << fb;
+            const long long f0b = min(max(static_cast<long long>(XX) - b1, 0LL), one);
+            const long long f1b = min(max(X1 - b1, 0LL), one);
+            const long long qb = shl_signed(f1b - f0b, sh);
+            if (qb) acc_add(jacc + static_cast<int>(c1), qb);
+        }
+        // (a5) removal at the ends; base-cell weight for the next injection
+        if (X1 >= c.lo_x && X1 < c.hi_x) {
+            xs[k] = static_cast<int>(X1);
+            us[k] = u1;
+            if (c1 == 0) w0_acc += shl_signed(one - X1, sh);
+        } else if (X1 >= 0 && X1 < top) {         // to a neighbouring sub-domain
+            emigrate_fix(c.out, X1 < c.lo_x ? 0 : 1, static_cast<int>(X1), u1,
+                         c.ids ? c.ids[i0 + k] : -1LL, c.flags);
+            xs[k] = -1;
+            us[k] = 0.0f;
         } else {
-            xs[k] = common ? static_cast<int>(U1) : xs[k];
-            us[k] = common ? u1 : us[k];
+            ++removed;
+            xs[k] = -1;
+            us[k] = 0.0f;
         }
     }
 #pragma unroll
@@ -181,7 +194,7 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
     }
     const int key = has_run ? static_cast<int>(A >> fb) : -1;
     const int key2 = has_run ? key + 1 : -1;
-    int ra = s_low, rb = s_inc - s_low;
+    int ra = static_cast<int>(s_low), rb = static_cast<int>(s_inc - s_low);
     if constexpr (kChecked) {
         if (ra != 0 && !checked_index(key, nz, c.flags)) ra = 0;
         if (rb != 0 && !checked_index(key2, nz, c.flags)) rb = 0;

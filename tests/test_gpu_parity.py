@@ -393,6 +393,32 @@ def test_fix32_ragged_tiles_with_forced_compaction(gpu_lib):
     t.close()
 
 
+@pytest.mark.parametrize("nz", [16, 17, 33])
+def test_fix32_smallest_grids_match_oracle(gpu_lib, nz):
+    """FIX32 tubes of the fewest cells allowed (16: 27 fractional bits, the
+    most; 17: 26; 33: 25), particles in every cell, exits at both ends,
+    holes left between compactions and injection every step, against the
+    FIX32 oracle every step."""
+    L = 8.0
+    kw = dict(workloads.flat_sclf_small(precision=B.SCLF_FIX32, accumulate=B.SCLF_ACC_FIXED64,
+                                        capacity=1 << 21),
+              Nz=nz, dt=0.4 * L / nz, rho_gj_user=-np.ones(nz + 1), compact_interval=8)
+    z, u = synth.random_particles(3000, L * (1 - 1e-3), seed=20 + nz, u_sigma=2.0)
+    t, o = pair(gpu_lib, kw, "fix32", "fixed")
+    assert t.derived["pos_unit"] == 2.0 ** -o.fb
+    t.add_particles(z, u)
+    o.add_particles(z, u)
+    for n in range(60):
+        t.step()
+        o.step()
+        compare(t, o, TOL[B.SCLF_FP32], "Nz %d step %d" % (nz, n))
+    assert t.status()["flags"] == 0
+    assert o.total_injected > 0 and o.last_removed >= 0
+    X, uu, ids = t.save_particles()
+    assert np.array_equal(X.astype(np.int64), o.xi) and np.array_equal(uu, o.u)
+    t.close()
+
+
 def test_large_fix32_tube_against_oracle_on_all_particles(gpu_lib):
     """The large tube's configuration (B = 3e12 G, P = 0.1 s, Nz = 2^20,
     fixed-point positions) with 2^27 particles, and the oracle, both from the
