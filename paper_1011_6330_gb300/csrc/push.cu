@@ -36,14 +36,18 @@ __device__ __forceinline__ typename AccType<kAcc>::T common_frac(double x0, doub
 // converted to 2^-20 units exactly (below 2^24); the segmented sums of up to
 // 32 lanes then stay below 2^29 and are scanned in 32-bit integers, and
 // each segment's total goes to the 2^-32-unit accumulator shifted by 12.
-template <bool kFloatRun, class AccT, class RunT>
+// kWarpReduce: a warp whose lanes share one key takes one warp reduction
+// (dense sorted tubes); without it every flush is the segmented scan (the
+// batches' sparser tubes, where such warps are rare and the test costs).
+template <bool kFloatRun, bool kWarpReduce, class AccT, class RunT>
 __device__ __forceinline__ void flush_run(int key, RunT r, int nz, unsigned int* flags,
                                           AccT* jacc) {
     if constexpr (kFloatRun) {
         int q = __float2int_rn(r * 1048576.0f);
         if constexpr (kChecked)
             if (q != 0 && !checked_index(key, nz, flags)) q = 0;
-        warp_flush_i32(key, q, jacc, 12);
+        if constexpr (kWarpReduce) warp_flush_i32(key, q, jacc, 12);
+        else warp_scan_flush_i32(key, q, jacc, 12);
     } else {
         if constexpr (kChecked)
             if (r != AccT(0) && !checked_index(key, nz, flags)) r = AccT(0);
@@ -94,7 +98,8 @@ __device__ __forceinline__ void emigrate(const Outbox* out, int side, P x, M u, 
 // Adds the tile's base weight, removals and non-finite flag to the caller's
 // counters.
 // The tile body: the thread's kPPT slots are already in xs, us.
-template <class Real, int kAcc, int kPPT = Layout<Real>::kPPT, bool kTwoRuns = false>
+template <class Real, int kAcc, int kPPT = Layout<Real>::kPPT, bool kTwoRuns = false,
+          bool kWarpReduce = true>
 __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccType<kAcc>::T>& c,
                                                long long tile, Real (&xs)[kPPT],
                                                Real (&us)[kPPT], long long& w0_acc,
@@ -228,15 +233,16 @@ __device__ __forceinline__ void push_tile_body(const TileCtx<Real, typename AccT
         }
     }
     const int key = rkey >= Real(0) ? static_cast<int>(rkey) : -1;
-    flush_run<kFloatRun, AccT>(key, ra, nz, c.flags, jacc);
+    flush_run<kFloatRun, kWarpReduce, AccT>(key, ra, nz, c.flags, jacc);
     if constexpr (kTwoRuns) {
         const int key2 = rkey2 >= Real(0) && rkey2 != rkey ? static_cast<int>(rkey2) : -1;
-        flush_run<kFloatRun, AccT>(key2, rb, nz, c.flags, jacc);
+        flush_run<kFloatRun, kWarpReduce, AccT>(key2, rb, nz, c.flags, jacc);
     }
 }
 
 // A tile with its slots loaded straight from global memory into registers.
-template <class Real, int kAcc, int kPPT = Layout<Real>::kPPT, bool kTwoRuns = false>
+template <class Real, int kAcc, int kPPT = Layout<Real>::kPPT, bool kTwoRuns = false,
+          bool kWarpReduce = true>
 __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<kAcc>::T>& c,
                                           long long tile, long long& w0_acc, long long& removed,
                                           bool& nonfinite) {
@@ -248,7 +254,8 @@ __device__ __forceinline__ void push_tile(const TileCtx<Real, typename AccType<k
         vload(c.xi + i0 + v, xs + v);
         vload(c.u + i0 + v, us + v);
     }
-    push_tile_body<Real, kAcc, kPPT, kTwoRuns>(c, tile, xs, us, w0_acc, removed, nonfinite);
+    push_tile_body<Real, kAcc, kPPT, kTwoRuns, kWarpReduce>(c, tile, xs, us, w0_acc, removed,
+                                                            nonfinite);
 }
 
 // Injection bookkeeping of a step: the requested count (the tube's own, or
@@ -419,7 +426,7 @@ batch_push_kernel(const BatchTube* __restrict__ tubes, const int* __restrict__ t
         c.out = nullptr;
         // the next tile's descriptor line into L1 while this tile computes
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
-        push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
+        push_tile<float, kAccFixed, kPPT, kTwoRuns, false>(c, local, w0, removed, nonfinite);
         flush_tube_counters(d.st, w0, removed, nonfinite);
     }
 }
@@ -465,7 +472,7 @@ batch_push_const_kernel(const __grid_constant__ BatchConstTable k,
         c.hif = kc.nzf;
         c.out = nullptr;
         asm volatile("prefetch.global.L1 [%0];" ::"l"(tubes + ti));
-        push_tile<float, kAccFixed, kPPT, kTwoRuns>(c, local, w0, removed, nonfinite);
+        push_tile<float, kAccFixed, kPPT, kTwoRuns, false>(c, local, w0, removed, nonfinite);
         flush_tube_counters(kc.st, w0, removed, nonfinite);
     }
 }
