@@ -51,11 +51,6 @@ __device__ __forceinline__ void emigrate_fix(const Outbox* out, int side, int X,
 }
 
 // One tile of kThreads * kPPT slots whose thread's slots are in xs, us.
-// kWarpReduce: the runs of a warp whose lanes share one run cell are two
-// warp reductions (dense sorted tubes: most warps; 0.3019 -> 0.2902 ms on
-// the 1e8-particle tube); the batch kernel, whose tubes hold ~100 particles
-// per cell, always takes the segmented scans (the test alone cost it 0.8 %).
-template <bool kWarpReduce = true>
 __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
                                            int (&xs)[Layout<int>::kPPT],
                                            float (&us)[Layout<int>::kPPT], long long& w0_acc,
@@ -206,12 +201,7 @@ __device__ __forceinline__ void fix32_tile(const FixCtx& c, long long tile,
     }
     // |ra|, |rb| <= 8 2^fb per lane: 32-lane segment sums fit 32 bits up to fb = 22
     if (fb <= 22) {
-        if constexpr (kWarpReduce) {
-            warp_flush2_i32(key, ra, rb, jacc, sh);
-        } else {
-            warp_scan_flush_i32(key, ra, jacc, sh);
-            warp_scan_flush_i32(key2, rb, jacc, sh);
-        }
+        warp_flush2_i32(key, ra, rb, jacc, sh);
     } else {
         warp_flush<long long>(key, shl_signed(ra, sh), jacc);
         warp_flush<long long>(key2, shl_signed(rb, sh), jacc);
@@ -397,7 +387,7 @@ batch_push_fix32_kernel(const BatchTube* __restrict__ tubes, const int* __restri
             vload(c.Xo + i0 + v, xs + v);
             vload(d.u + i0 + v, us + v);
         }
-        fix32_tile<false>(c, local, xs, us, w0, removed, nonfinite);
+        fix32_tile(c, local, xs, us, w0, removed, nonfinite);
         flush_tube_counters(d.st, w0, removed, nonfinite);
     }
 }
