@@ -67,13 +67,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["gr1e8", "large", "batch", "adjoint"], default="gr1e8",
+    ap.add_argument("--workload", choices=["gr1e8", "large", "batch", "adjoint", "dtube"],
+                    default="gr1e8",
                     help="gr1e8: P = 0.5 s frame-dragging tube, Nz = 65536, FP32 particles "
                          "(default); large: P = 0.1 s, B = 3e12 G, Nz = 2^20, 2^30 "
                          "fixed-point particles; batch: 256 pulsar tubes; adjoint: "
                          "gradients of a 2000-step run of a P = 0.3 s tube, Nz = 16384, "
-                         "1e6 FP32 particles")
+                         "1e6 FP32 particles; dtube: the gr1e8 tube cut into --domains "
+                         "z-domains on one GPU")
     ap.add_argument("--particles", type=float, default=None)
+    ap.add_argument("--domains", type=int, default=4,
+                    help="dtube workload: equal z-ranges the gr1e8 tube is cut into")
     ap.add_argument("--nz", type=int, default=None,
                     help="gr1e8/large: grid cells (default 65536 / 2^20), e.g. for a smaller "
                          "profiling case with the same particles per cell")
@@ -1100,6 +1104,69 @@ def sub_args(args, **kw):
     return argparse.Namespace(**d)
 
 
+def run_dtube(args):
+    """One tube split into z-domains on one GPU, as virtual sub-domains of a
+    multi-GPU run (dtube_*): the gr1e8 tube (FIX32 by default) cut into
+    args.domains equal cell ranges, each with its own slots, stream and grid
+    copy, stepped by dtube_run with the per-step exchanges (boundary current,
+    crossing particles, B_phi / E_z halos); reported next to the same seeded
+    tube stepped whole by tube_run. Both are timed by the wall clock around
+    the run with the device synchronised on both sides (dtube_run launches on
+    several streams)."""
+    import torch
+    from paper_1011_6330_gb300 import binding as B
+    from paper_1011_6330_gb300 import workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    n = int(args.particles or 1e8)
+    t, kw, d, _, _, _ = build_tube(B, workloads, "gr1e8", n, B.SCLF_ACC_FIXED64, args.order,
+                                   seed=rank_seed(rank), nz=args.nz, precision=args.precision)
+    _, z, u = _STATE.pop("last")
+
+    def timed(obj):
+        obj.run(args.warmup)
+        torch.cuda.synchronize()
+        s0 = obj.status()
+        w0 = time.perf_counter()
+        obj.run(args.steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - w0
+        s1 = obj.status()
+        return 0.5 * (s0["n_particles"] + s1["n_particles"]) * args.steps / el, el, s1
+
+    t.solve_fields()
+    whole, el_whole, _ = timed(t)
+    t.close()
+    dtb = B.DTube(tube_params(B, **kw), n=args.domains)
+    dtb.load_particles(z, u)
+    del z, u
+    dtb.solve_fields()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    value, el, st = timed(dtb)
+    clk = clocks.stop()
+    xs = dtb.exchange_stats()
+    per = max(xs["steps"], 1)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fix32+f32" if args.precision == "fix32" else "f32", "data": "synthetic",
+            "config": {"workload": gr_workload_name(n, kw["Nz"], args.precision)
+                       + "_zdomains%d" % args.domains,
+                       "domains": args.domains, "Nz": kw["Nz"], "particles_per_gpu": n,
+                       "parallelism": "one tube in %d z-domains on one GPU" % args.domains,
+                       "timing": "wall clock around dtube_run / tube_run, device "
+                                 "synchronised on both sides"},
+            "whole_tube": {"value": whole, "ms_per_step": 1e3 * el_whole / args.steps},
+            "vs_whole": value / whole,
+            "exchange_per_step": {"field_bytes": xs["field_bytes"] / per,
+                                  "particles": xs["particles"] / per,
+                                  "particle_bytes": xs["particle_bytes"] / per},
+            "clocks": clk, "status": {"flags": st["flags"], "n_particles": st["n_particles"]}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1108,6 +1175,8 @@ def main():
         return run_batch(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "dtube":
+        return run_dtube(args)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
