@@ -151,6 +151,7 @@ struct sclf_dtube {
     int compact_every = 64;
     int64_t part_bytes = 0;                // bytes per handed-over particle
     int64_t halo_bytes = 0;                // field bytes exchanged per step
+    cudaGraphExec_t chunk = nullptr;       // compact_every steps, captured once
 };
 
 namespace sclf {
@@ -228,6 +229,52 @@ int dstep(sclf_dtube* D) {
     return SCLF_OK;
 }
 
+// compact_every steps from an even step right after a compaction check,
+// captured once from the exchange stream (the sub-domain streams join the
+// capture through its event and rejoin it at the end; the events between the
+// streams become graph edges) and replayed by dtube_run. The host's step
+// counters are restored after the capture and advanced per replay.
+int capture_dchunk(sclf_dtube* D) {
+    const int64_t hs = D->host_step;
+    std::vector<int64_t> ths(D->n);
+    for (int k = 0; k < D->n; ++k) ths[k] = D->dom[k]->host_step;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(D->xs, cudaStreamCaptureModeThreadLocal));
+    int rc = release_domains(D);
+    for (int s = 0; s < D->compact_every && rc == SCLF_OK; ++s) rc = dstep(D);
+    if (rc == SCLF_OK) rc = join_domains(D);
+    const cudaError_t e2 = cudaStreamEndCapture(D->xs, &g);
+    D->host_step = hs;
+    for (int k = 0; k < D->n; ++k) {
+        D->dom[k]->host_step = ths[k];
+        D->dom[k]->steps_since_compact = 0;
+    }
+    D->steps_since_compact = 0;
+    if (rc != SCLF_OK || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != SCLF_OK ? rc : cuda_fail(e2);
+    }
+    const cudaError_t e = cudaGraphInstantiate(&D->chunk, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return SCLF_OK;
+}
+
+int launch_dchunk(sclf_dtube* D) {
+    int rc = join_domains(D);
+    if (rc) return rc;
+    CK(cudaGraphLaunch(D->chunk, D->xs));
+    rc = release_domains(D);
+    if (rc) return rc;
+    D->host_step += D->compact_every;
+    for (int k = 0; k < D->n; ++k) {
+        D->dom[k]->host_step += D->compact_every;
+        D->dom[k]->steps_since_compact = 0;
+    }
+    D->steps_since_compact = 0;
+    return SCLF_OK;
+}
+
 int sync_all(sclf_dtube* D) {
     for (int k = 0; k < D->n; ++k) CK(cudaStreamSynchronize(D->streams[k]));
     CK(cudaStreamSynchronize(D->xs));
@@ -245,6 +292,7 @@ int clear_injection(sclf_dtube* D) {
 }
 
 void destroy(sclf_dtube* D) {
+    if (D->chunk) cudaGraphExecDestroy(D->chunk);
     for (tube_t t : D->dom)
         if (t) {
             t->owned = false;
@@ -480,9 +528,18 @@ int dtube_step(dtube_t dt) {
 int dtube_run(dtube_t dt, int64_t nsteps) {
     NvtxRange nvtx_range("dtube_run");
     if (!dt || nsteps < 0) return SCLF_EINVAL;
-    for (int64_t s = 0; s < nsteps; ++s) {
-        const int rc = dstep(dt);
-        if (rc) return rc;
+    sclf_dtube* D = dt;
+    while (nsteps > 0) {
+        int rc;
+        if (D->p.use_graphs && D->compact_every % 2 == 0 && (D->host_step & 1) == 0 &&
+            D->steps_since_compact == 0 && nsteps >= D->compact_every) {
+            if (!D->chunk && (rc = capture_dchunk(D)) != SCLF_OK) return rc;
+            if ((rc = launch_dchunk(D)) != SCLF_OK) return rc;
+            nsteps -= D->compact_every;
+            continue;
+        }
+        if ((rc = dstep(D)) != SCLF_OK) return rc;
+        nsteps -= 1;
     }
     return SCLF_OK;
 }
