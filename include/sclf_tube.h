@@ -460,6 +460,10 @@ int dtube_solve_fields(dtube_t dt);
 
 /* One step (Figure A) of every sub-domain with its exchanges. Async. */
 int dtube_step(dtube_t dt);
+/* nsteps such steps. With use_graphs and an even compaction interval, runs of
+ * that many steps starting at an even step right after a compaction check
+ * replay one CUDA graph captured on first use (the same kernels and
+ * exchanges, bit for bit); the other steps are launched one by one. Async. */
 int dtube_run(dtube_t dt, int64_t nsteps);
 
 /* The whole tube's counters: live particles, slots, removals and flags
